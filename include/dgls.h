@@ -1,0 +1,193 @@
+/*
+ * dgls.h -- C ABI of libdgls.so: matrix-free DG0/DG1 residual, Jacobian-vector product,
+ * Newton-GMRES implicit Euler step and adaptive discharge of the coarse-grained Li-S cathode
+ * model of Okraschevski et al., "Structure Matters" (arXiv 2511.05233), on one NVIDIA GB300.
+ *
+ * Model: Tab. 4 (coarse-grained PDE system) with the Tradeoff Chemistry of Tab. 3, the
+ * constitutive laws of Eqs. 2-6 and 18-24, Eq. 57 localisation, boundary conditions Eqs. 25-27;
+ * discretisation Eqs. 43-48 (DG0 = two-point harmonic flux, DG1 = Q1 interior penalty);
+ * time stepping Eq. 50; controllers Fig. 4 (naive) and Eqs. 51-54 (H211b); initial state
+ * Tab. 6 and the parabolic relaxation of Sec. 2.8; cell voltage Eq. A1.
+ *
+ * Conventions for every call
+ *  - All state vectors are FP64 arrays in device memory ("_dev") owned by the caller, laid out
+ *    as dg_layout() reports: fields one after another; liquid fields and Phi^L have one value
+ *    per voxel (index i + nx*(j + ny*k), x fastest), solid fields and Phi^S one value per
+ *    structure voxel in increasing voxel index; DG1 stores 8 nodal values per voxel node-major
+ *    (offset + node*len + voxel, node = a + 2b + 4c for the x, y, z Gauss-node indices).
+ *  - Device calls are issued on the stream given to dg_setup and are asynchronous unless the
+ *    comment says "synchronous".  No call aborts the process: errors are returned as a
+ *    dg_status and described by dg_last_error().
+ *  - The context owns its Krylov, preconditioner and scratch workspaces (allocated in
+ *    dg_setup, freed in dg_destroy); it never takes ownership of caller buffers.
+ */
+#ifndef DGLS_H
+#define DGLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DG_OK = 0,
+    DG_ERR_ARG = -1,        /* invalid argument or structure */
+    DG_ERR_OOM = -2,        /* workspace exceeds hbm_budget_bytes or cudaMalloc failed */
+    DG_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    DG_ERR_NOCONV = -4,     /* Newton did not converge (iteration limit or line search) */
+    DG_ERR_NONFINITE = -5,  /* NaN/Inf in a residual or update */
+    DG_ERR_TIMEOUT = -6,    /* a bounded device-side wait gave up */
+    DG_ERR_ABORTED = -7     /* time-step controller gave up (31st consecutive halving) */
+} dg_status;
+
+typedef struct dg_ctx dg_ctx;
+
+/* Voxel structure (Sec. 2.1): phase per voxel, 0 macro-pore, 1 coarse-grained active
+ * structure, 2 homogeneous separator.  x is the transport direction: the current collector is
+ * the x = 0 face, the lithium anode the x = nx face.  dg_setup copies the array. */
+typedef struct {
+    int32_t nx, ny, nz;
+    double h;                  /* voxel width in m */
+    const uint8_t* phase;      /* host pointer, nx*ny*nz bytes, x fastest */
+} dg_structure;
+
+typedef enum { DG_CHEM_REDUCED3 = 0, DG_CHEM_TRADEOFF = 1 } dg_chemistry;
+typedef enum { DG_PREC_FP64 = 0, DG_PREC_MIXED = 1 } dg_precision;
+
+typedef struct {
+    int32_t order;             /* 0: DG0 (Eq. 48), 1: DG1 tensor-product Q1 (Eqs. 43-47) */
+    int32_t chemistry;         /* dg_chemistry: three-species (Li+, S8(L), S8^2-, E1 only, solids
+                                  frozen) or the paper's Tradeoff Chemistry (Tab. 3) */
+    double T;                  /* K; 298.15 reproduces Tab. 5.2 */
+    double f_C;                /* discharge rate in 1/h (App. B, Eq. 18) */
+    double j_el;               /* A/m^2; <= 0 derives j_el = f_C c_theo m_A,S8 (App. B) */
+    double eps_struct;         /* structure fraction of the cathode, 1 - macro-porosity (Eq. 57) */
+    double penalty;            /* DG1 interior-penalty factor (Eq. 46: 1) */
+    int32_t smooth;            /* 1: rates of C2 and E4 multiplied by T_H(t) (Sec. 2.8, Eq. 56) */
+    /* Newton-Krylov solver (the role of PETSc newtonls + gmres, Sec. 2.7) */
+    int32_t precision;         /* dg_precision: FP64 Krylov, or FP32 JVP/basis/preconditioner
+                                  inside the FP64 Newton iteration */
+    int32_t gmres_restart;     /* Krylov subspace size m (30) */
+    int32_t gmres_max_it;      /* total GMRES iterations per linear solve */
+    double newton_rtol;        /* ||S R|| <= rtol ||S R(z^n)|| (1e-10) */
+    int32_t newton_max_it;     /* 25 */
+    double eta_max;            /* Eisenstat-Walker forcing-term cap (1e-2) */
+    double eta_min;            /* forcing-term floor */
+    int64_t hbm_budget_bytes;  /* workspace cap checked in dg_setup (0: no cap) */
+} dg_params;
+
+typedef struct {
+    int32_t converged;         /* 1 if Newton converged */
+    int32_t newton_iterations;
+    int32_t gmres_iterations;  /* summed over Newton iterations */
+    int32_t residual_evals;
+    int32_t jvp_evals;
+    double norm0, norm;        /* scaled residual norms ||S R|| at start and end */
+} dg_step_info;
+
+typedef enum { DG_CTRL_NAIVE = 0, DG_CTRL_H211B = 1, DG_CTRL_FIXED = 2 } dg_controller;
+
+typedef struct {
+    int32_t controller;        /* dg_controller */
+    double t0, dt0, dt_min, dt_max;
+    double tol;                /* H211b tolerance (Eq. 51) */
+    double cutoff_V;           /* stop at the first accepted step with U_cell <= cutoff (1.9 V) */
+    double t_end;              /* stop when t >= t_end (<= 0: no limit) */
+    int32_t max_steps;         /* accepted-step limit */
+    int32_t max_halvings;      /* consecutive halvings before DG_ERR_ABORTED (30) */
+    const double* replay_dt;   /* host array: if non-NULL take these step sizes (n_replay) */
+    int32_t n_replay;
+} dg_discharge_opts;
+
+typedef struct {               /* caller-allocated host arrays of length n_max */
+    int32_t n_max;
+    int32_t n;                 /* accepted steps written */
+    double* t;                 /* time after the step, s */
+    double* dt;                /* accepted step size, s */
+    double* U_cell;            /* Eq. A1, V */
+    double* c_m;               /* c_m = t f_C c_theo, Ah/kg (App. B) */
+    int32_t* newton_its;       /* per accepted step */
+    int32_t* gmres_its;
+    int32_t status;            /* dg_status of the run: DG_OK (cut-off, t_end or max_steps) */
+    int32_t attempts, failures;
+} dg_curve;
+
+/* Default parameters of the paper (Tabs. 1, 2, 5) for a chemistry and DG order. */
+dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t order);
+
+/* Copy the structure, build the compacted structure list and neighbour data, upload the
+ * parameters and allocate the workspaces on `cuda_stream` (NULL: legacy default stream).
+ * DG_ERR_ARG if no structure voxel touches the current collector or the anode layer is not
+ * liquid; DG_ERR_OOM if the workspace exceeds hbm_budget_bytes.  Synchronous. */
+dg_status dg_setup(const dg_structure* s, const dg_params* p, void* cuda_stream, dg_ctx** out);
+dg_status dg_destroy(dg_ctx* ctx);
+const char* dg_last_error(const dg_ctx* ctx);
+
+/* Number of unknowns and per-field offset/length (lengths include the 8 DG1 nodes).
+ * Arrays hold up to 10 entries; *n_fields receives 10 (Tradeoff) or 5 (three-species). */
+dg_status dg_layout(const dg_ctx* ctx, int64_t* n_dof, int32_t* n_fields,
+                    int64_t field_offset[10], int64_t field_len[10]);
+
+/* Tab. 6 equilibrium written into z_dev (Phi^L = 0, Phi^S = Delta Phi_0; three-species:
+ * 1000/10/100 mol/m^3 and the Nernst potential of E1).  Asynchronous. */
+dg_status dg_equilibrium_state(dg_ctx* ctx, double* z_dev);
+
+/* Parabolic relaxation of Sec. 2.8 applied to z_dev in place: n_steps implicit Euler steps of
+ * size dt with concentrations frozen, d_t Phi terms and the current ramped by T_H.  Synchronous. */
+dg_status dg_relax(dg_ctx* ctx, double* z_dev, double dt, int32_t n_steps);
+
+/* Residual R(z; z^n, t, dt) of the implicit Euler step (Eq. 50) in the DG weak form,
+ * volume-integrated, unscaled.  t is the time at which T_H is evaluated (t^{n+1}).
+ * z_dev, zold_dev, r_dev: n_dof doubles; r_dev must not alias the inputs.  Asynchronous. */
+dg_status dg_residual(dg_ctx* ctx, const double* z_dev, const double* zold_dev,
+                      double t, double dt, double* r_dev);
+
+/* Jacobian-vector product J(z) v with J = dR/dz at fixed z^n, t, dt (exact forward-mode
+ * linearisation of dg_residual).  Asynchronous. */
+dg_status dg_jvp(dg_ctx* ctx, const double* z_dev, double t, double dt,
+                 const double* v_dev, double* jv_dev);
+
+/* Apply the cell-block-Jacobi preconditioner built at z: out = B(z)^{-1} v, where B holds the
+ * diagonal blocks of S J (S the Newton row scales; DG0 full voxel blocks, DG1 per-node field
+ * blocks).  Asynchronous. */
+dg_status dg_block_jacobi(dg_ctx* ctx, const double* z_dev, double t, double dt,
+                          const double* v_dev, double* out_dev);
+
+/* Newton row scale of every unknown (dt/(M c_ref) for species and solids, dt/(M F c_ref) for
+ * the potentials, M the voxel or node volume) written to s_dev.  Asynchronous. */
+dg_status dg_row_scales(dg_ctx* ctx, double dt, double* s_dev);
+
+/* One implicit Euler step (Eq. 50) from z^n at time t to t + dt by Newton-GMRES with
+ * block-Jacobi right preconditioning.  zn_dev is read, z_dev receives z^{n+1} (they may be
+ * the same buffer).  On DG_ERR_NOCONV z_dev holds the last Newton iterate.  Synchronous. */
+dg_status dg_step(dg_ctx* ctx, const double* zn_dev, double* z_dev, double t, double dt,
+                  dg_step_info* info);
+
+/* Same step with host buffers: copies zn_host to the device, steps, copies z^{n+1} back to
+ * z_host.  Synchronous. */
+dg_status dg_step_host(dg_ctx* ctx, const double* zn_host, double* z_host, double t, double dt,
+                       dg_step_info* info);
+
+/* Cell voltage U_cell (Eq. A1): mean of Phi^S over the structure faces at x = 0. Synchronous. */
+dg_status dg_cell_voltage(dg_ctx* ctx, const double* z_dev, double* U_cell);
+
+/* Ledger (Eq. A3 numerators and Sec. 3.2 conservation): out[0] total dissolved + solid sulfur
+ * (mol), out[1] total lithium (mol), out[2] liquid charge (C), out[3] Phi^L mean over the anode
+ * face, out[4] Phi^L mean over the x = 0 face.  Synchronous. */
+dg_status dg_ledger(dg_ctx* ctx, const double* z_dev, double out[5]);
+
+/* Galvanostatic discharge from z_dev (in place) under the chosen controller until the
+ * cut-off voltage, t_end or max_steps; one curve point per accepted step.  Synchronous. */
+dg_status dg_discharge(dg_ctx* ctx, double* z_dev, const dg_discharge_opts* opts, dg_curve* out);
+
+/* Number of CUDA kernels this context has launched (monotone counter). */
+int64_t dg_launch_count(const dg_ctx* ctx);
+
+/* Workspace bytes held by the context on the device. */
+int64_t dg_workspace_bytes(const dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGLS_H */

@@ -193,32 +193,55 @@ def transport_factor(epsL, c):
     return _pos(epsL) ** 1.5 * np.exp(-K.VISC_EXP * cS)
 
 
-def sources(chem, c, eps_solid, phiL, phiS, tH, aV, T=K.T_DEFAULT):
+def rates_magnitude(chem, c, phiL, phiS, T=K.T_DEFAULT):
+    """|forward| + |backward| term of each mass-action rate (size of the terms that cancel)."""
+    a = activities(chem, c)
+    out = {}
+    for rx in chem.reactions:
+        ar, ap = net_activities(rx, a)
+        if rx.kind == "C":
+            s = np.sqrt(rx.K_sp)
+            out[rx.name] = np.abs(ar * s) + np.abs(ap / s)
+        else:
+            x = K.F * (phiS - phiL - rx.U0) / (2.0 * K.R_GAS * T)
+            out[rx.name] = np.abs(ar * np.exp(-x)) + np.abs(ap * np.exp(x))
+    return out
+
+
+def sources(chem, c, eps_solid, phiL, phiS, tH, aV, T=K.T_DEFAULT, mag=False):
     """Volumetric sources (mol m^-3 s^-1) and charge sources (A m^-3) at structure points.
 
     Species i:  k_C R_C,i + a_V k_E R_E,i / F = sum_C nu_ik eps_s(k) k_C,k r_k + a_V sum_E nu_ik k_E,k r_k  (Eqs. 5, 6, 16, 17)
     Liquid charge:  sum_j z_j a_V k_E R_E,j  (Tab. 4 row 2);  solid charge: z_e a_V k_E R_E,e (Eq. 17b).
     Reactions flagged ``smooth`` are multiplied by T_H (Sec. 2.8)."""
-    r = rates_mass_action(chem, c, phiL, phiS, T)
+    r = rates_magnitude(chem, c, phiL, phiS, T) if mag else rates_mass_action(chem, c, phiL, phiS, T)
     names = list(chem.liquid) + list(chem.solid)
     S = {m: 0.0 for m in names}
     SE = {m: 0.0 for m in chem.liquid}
     e_rate = 0.0                                  # sum_E k_E,k r_k T_k
     for rx in chem.reactions:
         rate = r[rx.name] * (tH if rx.smooth else 1.0)
+        sg = (lambda v: abs(float(v))) if mag else float
         if rx.kind == "C":
             w = eps_solid[rx.solid] * rx.k * rate
+            if mag:
+                w = np.abs(w)
             for m, nu in rx.nu.items():
                 if m in S:
-                    S[m] = S[m] + float(nu) * w
+                    S[m] = S[m] + sg(nu) * w
         else:
             w = aV * rx.k * rate
+            if mag:
+                w = np.abs(w)
             for m, nu in rx.nu.items():
                 if m in S:
-                    S[m] = S[m] + float(nu) * w
+                    S[m] = S[m] + sg(nu) * w
                 if m in SE:
-                    SE[m] = SE[m] + float(nu) * w
+                    SE[m] = SE[m] + sg(nu) * w
             e_rate = e_rate + rx.k * rate
+    if mag:
+        q_liquid = K.F * sum(abs(K.Z[m]) * SE[m] for m in chem.liquid)
+        return S, q_liquid, np.abs(aV) * K.F * e_rate
     q_liquid = K.F * sum(K.Z[m] * SE[m] for m in chem.liquid)
     nu_e, z_e = -1.0, -1.0
     q_solid = z_e * aV * K.F * nu_e * e_rate

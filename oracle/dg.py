@@ -50,10 +50,11 @@ def _sl(ndim, axis, s):
 
 # ------------------------------------------------------------------------------------ DG0
 
-def dg0_faces(Kc, psi, h):
+def dg0_faces(Kc, psi, h, mag=False):
     """Interior-face part of Eq. 48 per cell: sum_Q A {K}_H (psi_P - psi_Q) / h, A = h^2.
 
-    Kc, psi: (nz, ny, nx).  Each face is evaluated once and added to both cells."""
+    Kc, psi: (nz, ny, nx).  Each face is evaluated once and added to both cells.
+    mag=True sums |flux| instead (the size of the terms, used for rounding tolerances)."""
     out = np.zeros(np.broadcast(Kc, psi).shape, dtype=np.result_type(Kc, psi, float))
     for d in ("x", "y", "z"):
         ax = AXES[d][0]
@@ -62,8 +63,10 @@ def dg0_faces(Kc, psi, h):
             continue
         lo, hi = _sl(3, ax, slice(0, n - 1)), _sl(3, ax, slice(1, n))
         flux = h * harmonic(Kc[lo], Kc[hi]) * (psi[lo] - psi[hi])
+        if mag:
+            flux = np.abs(flux)
         out[lo] += flux
-        out[hi] -= flux
+        out[hi] -= -flux if mag else flux
     return out
 
 
@@ -99,7 +102,7 @@ def _scatter_nodes(out, d, val_at_1, val_at_0):
     out[_sl(out.ndim, na, 0)] += val_at_0
 
 
-def dg1_volume(Kn, psi, h):
+def dg1_volume(Kn, psi, h, mag=False):
     """int K grad psi . grad phi_m over each cell with 2x2x2 Gauss quadrature (collocated K).
 
     Per direction the term factorises into lines of two nodes:
@@ -107,11 +110,13 @@ def dg1_volume(Kn, psi, h):
     out = np.zeros(np.broadcast(Kn, psi).shape, dtype=np.result_type(Kn, psi, float))
     for d in ("x", "y", "z"):
         flux = (3.0 * h / 8.0) * (node(Kn, d, 0) + node(Kn, d, 1)) * (node(psi, d, 1) - node(psi, d, 0))
-        _scatter_nodes(out, d, flux, -flux)
+        if mag:
+            flux = np.abs(flux)
+        _scatter_nodes(out, d, flux, flux if mag else -flux)
     return out
 
 
-def dg1_faces(Kf, psi, h, penalty=1.0):
+def dg1_faces(Kf, psi, h, penalty=1.0, mag=False):
     """Interior-face terms of Eq. 46 on every interior face, 2x2 Gauss points per face.
 
     Kf[d] = (K_plus_side, K_minus_side): the coefficient evaluated from the traced fields on
@@ -135,20 +140,30 @@ def dg1_faces(Kf, psi, h, penalty=1.0):
         pen = penalty * H * (tp[L] - tm[Rr]) / h
         fP = wf * (-avg + pen)           # enters cell P (left) as f * v-
         fQ = wf * (avg - pen)            # enters cell Q (right) as f * v+
+        if mag:
+            fP = wf * (np.abs(avg) + np.abs(pen))
+            fQ = fP
         accP = np.zeros_like(tp, dtype=out.dtype)
         accQ = np.zeros_like(tp, dtype=out.dtype)
         accP[L] = fP
         accQ[Rr] = fQ
         # P: near node is a=1, far node a=0; Q: near node a=0, far node a=1
-        _scatter_nodes(out, d, ALPHA * accP + BETA * accQ, BETA * accP + ALPHA * accQ)
+        if mag:
+            _scatter_nodes(out, d, ALPHA * accP + abs(BETA) * accQ, abs(BETA) * accP + ALPHA * accQ)
+        else:
+            _scatter_nodes(out, d, ALPHA * accP + BETA * accQ, BETA * accP + ALPHA * accQ)
     return out
 
 
-def dg1_boundary_flux(shape_like, d, side, fN, h, dtype=float):
+def dg1_boundary_flux(shape_like, d, side, fN, h, dtype=float, mag=False):
     """int_{face} f^N v for the face xi = side of direction d (f^N given at the face points,
     zero where the face is not a boundary face)."""
     out = np.zeros(shape_like, dtype=dtype)
     wf = 0.25 * h * h
+    if mag:
+        fN = np.abs(fN)
+        _scatter_nodes(out, d, ALPHA * wf * fN, ALPHA * wf * fN)
+        return out
     if side > 0:
         _scatter_nodes(out, d, ALPHA * wf * fN, BETA * wf * fN)
     else:

@@ -358,3 +358,69 @@ def cell_means(model, grid, z):
         (8 * out["S8s"] if "S8s" in out else 0.0) + (out["Li2Ss"] if "Li2Ss" in out else 0.0)
     out["lithium"] = out["Li"] + (2 * out["Li2Ss"] if "Li2Ss" in out else 0.0)
     return out
+
+
+# --------------------------------------------------------------------------- rounding scale
+
+def residual_magnitude(model, grid, z, zn, t, dt):
+    """Per-row sum of the absolute values of the terms that make up ``residual`` (storage parts,
+    every face flux, forward and backward reaction terms, boundary terms): the size against
+    which rounding differences between two implementations of the residual are measured."""
+    chem = model.chem
+    h = grid.h
+    dg1 = model.order == 1
+    Mw = h ** 3 / 8.0 if dg1 else h ** 3
+    U, Un = unpack(model, grid, z), unpack(model, grid, zn)
+    phase = np.broadcast_to(grid.phase, U["PhiL"].shape) if dg1 else grid.phase
+    eps_s, eps_sn = _solid_fractions(model, U), _solid_fractions(model, Un)
+    epsL, epsLn = liquid_fraction(model, phase, eps_s), liquid_fraction(model, phase, eps_sn)
+    R = {}
+    for m in chem.liquid:
+        R[m] = Mw * (np.abs(epsL * U[m]) + np.abs(epsLn * Un[m])) / dt
+    rho_M = {"S8s": K.RHO_S8 / K.M_S8, "Li2Ss": K.RHO_LI2S / K.M_LI2S}
+    for s in chem.solid:
+        f = "eps_" + s
+        R[f] = Mw * rho_M[s] * (np.abs(U[f]) + np.abs(Un[f])) / dt * (phase == STRUCT)
+    R["PhiL"] = 0.0 * np.abs(U["PhiL"])
+    R["PhiS"] = 0.0 * np.abs(U["PhiS"])
+    terms, _ = coefficients(model, phase, U)
+    if dg1:
+        fterms = _face_coefficients(model, grid, U)
+    for e in list(chem.liquid) + ["PhiL", "PhiS"]:
+        for it, (Kn, f) in enumerate(terms[e]):
+            if dg1:
+                Kf = {d: (fterms[d][+1][e][it][0], fterms[d][-1][e][it][0]) for d in ("x", "y", "z")}
+                R[e] = R[e] + dg.dg1_volume(Kn, U[f], h, mag=True) + dg.dg1_faces(Kf, U[f], h, model.penalty, mag=True)
+            else:
+                R[e] = R[e] + dg.dg0_faces(Kn, U[f], h, mag=True)
+    eps = _solid_fractions(model, U)
+    aV = ch.specific_surface(eps["S8s"], eps["Li2Ss"], model.f_C, model.eps_struct)
+    c = {m: U[m] for m in chem.liquid}
+    S, qL, qS = ch.sources(chem, c, eps, U["PhiL"], U["PhiS"], _smooth_factor(model, t), aV, model.T, mag=True)
+    st = phase == STRUCT
+    for m in chem.liquid:
+        R[m] = R[m] + Mw * np.where(st, S[m], 0.0)
+    for s in chem.solid:
+        R["eps_" + s] = R["eps_" + s] + Mw * np.where(st, S[s], 0.0)
+    R["PhiL"] = R["PhiL"] + Mw * np.where(st, qL, 0.0)
+    R["PhiS"] = R["PhiS"] + Mw * np.where(st, qS, 0.0)
+    x = lambda phiL: K.F * (0.0 - phiL) / (2.0 * K.R_GAS * model.T)
+    A = h * h
+    if dg1:
+        cLi_t, phiL_t = dg.trace(U["Li"], "x", +1), dg.trace(U["PhiL"], "x", +1)
+        last = np.zeros((grid.nz, grid.ny, grid.nx), dtype=bool)
+        last[:, :, -1] = True
+        rm = np.where(last, np.abs(cLi_t) / K.C_REF * np.exp(-x(phiL_t)) + np.exp(x(phiL_t)), 0.0)
+        R["Li"] = R["Li"] + dg.dg1_boundary_flux(U["Li"].shape, "x", +1, K.K_ANO * rm, h, mag=True)
+        R["PhiL"] = R["PhiL"] + dg.dg1_boundary_flux(U["Li"].shape, "x", +1, K.F * K.K_ANO * rm, h, mag=True)
+        first = np.zeros((grid.nz, grid.ny, grid.nx), dtype=bool)
+        first[:, :, 0] = True
+        fN = np.where(first & grid.struct, abs(_cc_current(model, grid, t, False)), 0.0)
+        R["PhiS"] = R["PhiS"] + dg.dg1_boundary_flux(U["PhiS"].shape, "x", -1, fN, h, mag=True)
+    else:
+        cL, pL = U["Li"][:, :, -1], U["PhiL"][:, :, -1]
+        rm = np.abs(cL) / K.C_REF * np.exp(-x(pL)) + np.exp(x(pL))
+        R["Li"][:, :, -1] += A * K.K_ANO * rm
+        R["PhiL"][:, :, -1] += A * K.F * K.K_ANO * rm
+        R["PhiS"][:, :, 0] += np.where(grid.cc, A * abs(_cc_current(model, grid, t, False)), 0.0)
+    return pack(model, grid, R)

@@ -1,0 +1,812 @@
+// C-ABI layer of libdgls: context setup, parameters of the paper, Newton-GMRES implicit Euler
+// steps, time-step controllers and the discharge loop.  Kernels live in dg0.cu, dg1.cu, la.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dgls.h"
+#include "internal.h"
+
+using namespace dgls;
+
+struct dg_ctx {
+    dg_params prm;
+    DevParams P;
+    Geo G;
+    LaunchCtx L;
+    int64_t launches = 0;
+    int64_t ndof = 0;
+    int64_t nblk = 0;              // preconditioner blocks
+    int64_t ws_bytes = 0;
+    int n_cc = 0;
+    std::string err;
+    std::vector<void*> allocs;
+    // geometry
+    uint8_t* d_phase = nullptr;
+    int32_t* d_cmap = nullptr;
+    int32_t* d_sidx = nullptr;
+    // model scratch (transport factors or DG1 face data)
+    double* gb = nullptr;
+    double* gbd = nullptr;
+    float* gb32 = nullptr;
+    float* gbd32 = nullptr;
+    // preconditioner
+    double* blk = nullptr;
+    float* blk32 = nullptr;
+    int* d_bad = nullptr;
+    // Newton vectors
+    double *zc = nullptr, *zt = nullptr, *R = nullptr, *Rt = nullptr, *dz = nullptr, *zn = nullptr;
+    // Krylov (FP64 or FP32 by precision)
+    void* V = nullptr;
+    void* w = nullptr;
+    void* u = nullptr;
+    void* x = nullptr;             // Krylov combination sum y_k V_k
+    float* z32 = nullptr;
+    // discharge work states
+    double *za = nullptr, *zb = nullptr, *zC = nullptr, *zF = nullptr;
+    // reductions
+    double* partial = nullptr;
+    double* dres = nullptr;
+    double* hres = nullptr;        // pinned host mirror
+    double* d_vals = nullptr;      // equilibrium field values
+    // statistics of the last step
+    int gmres_its = 0, res_evals = 0, jvp_evals = 0;
+};
+
+static dg_status fail(dg_ctx* c, dg_status s, const std::string& m) {
+    if (c) c->err = m;
+    return s;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e__ = (call);                                                       \
+        if (e__ != cudaSuccess)                                                         \
+            return fail(ctx, DG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+// ------------------------------------------------------------------ paper constants
+namespace {
+const double F_ = 96485.332, R_ = 8.3145, CREF = 1000.0;
+// Tab. 5.1
+const double KSP1 = 0.006, KC1 = 120.0, KSP2 = 8e-15, KC2 = 3e-3;
+const double U01 = 2.41, U02 = 2.32, U03 = 2.31, U04 = 1.985;
+const double KE[6] = {2.53e-6, 3.54e-8, 1.49e-10, 2.05e-7, 9.11e-10, 1.37e-15};
+const double AV0 = 94.908e6, RHO_S8 = 2070.4, M_S8 = 0.2565, EPS_S8_0 = 0.095;
+const double RHO_LI2S = 1659.0, M_LI2S = 0.0459, EPS_LI2S_0 = 2.77e-6;
+const double AV_A = 0.1392, AV_B = 3.310, KAPPA_S = 1.0, K_ANO = 5.0e-3;
+// Tab. 5.2 (order: Li+, S8(L), S8^2-, S6^2-, S4^2-, S^2-) and the anion
+const double D0_TO[6] = {9.3e-10, 10.0e-10, 5.3e-10, 5.3e-10, 7.6e-10, 0.6e-10};
+const double Z_TO[6] = {1, 0, -2, -2, -2, -2};
+const double WS_TO[6] = {0, 8, 8, 6, 4, 1};
+const double D0_A = 9.3e-10, C_LI_0 = 1500.0;
+// Tab. 2 and Sec. 2.1
+const double X_CATHODE = 0.168, X_SULFUR = 0.0956, EPS_SEP = 0.4;
+const double VISC = 7.76e-4;
+
+// Tab. 6 equilibrium: concentrations (Li+, S8(L), S8^2-, S6^2-, S4^2-, S^2-), Delta Phi_0, U5, U6.
+void tab6(double T, double out_c[6], double* dphi0, double* U5, double* U6) {
+    const double rtf = R_ * T / F_;
+    const double cS8 = KSP1 * CREF;
+    const double cS2 = KSP2 * CREF * CREF * CREF / (C_LI_0 * C_LI_0);
+    const double d0 = (0.75 * U01 + 0.25 * U02) / 6.0 + U03 / 12.0 + 0.75 * U04 +
+                      rtf * (std::log(cS8 / CREF) / 16.0 - 0.5 * std::log(cS2 / CREF));
+    const double cS8_2 = cS8 * std::exp(-2.0 * (d0 - U01) / rtf);
+    const double cS6_2 = CREF * std::pow(cS8 / CREF, 0.75) * std::exp(-2.0 * (d0 - (0.75 * U01 + 0.25 * U02)) / rtf);
+    const double cS4_2 = CREF * std::pow(cS2 / CREF, 4.0) * std::exp(6.0 * (d0 - U04) / rtf);
+    *U5 = d0 - rtf * (0.5 * std::log(cS8_2 / CREF) - std::log(cS4_2 / CREF));
+    *U6 = d0 - rtf * (std::log(cS4_2 / CREF) / 6.0 + 4.0 / 3.0 * std::log(C_LI_0 / CREF));
+    *dphi0 = d0;
+    out_c[0] = C_LI_0; out_c[1] = cS8; out_c[2] = cS8_2; out_c[3] = cS6_2; out_c[4] = cS4_2; out_c[5] = cS2;
+}
+}  // namespace
+
+extern "C" dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t order) {
+    if (!p || (chemistry != 0 && chemistry != 1) || (order != 0 && order != 1)) return DG_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->order = order;
+    p->chemistry = chemistry;
+    p->T = 298.15;
+    p->f_C = 0.5;
+    p->j_el = 0.0;
+    p->eps_struct = 0.4;
+    p->penalty = 1.0;
+    p->smooth = 1;
+    p->precision = DG_PREC_FP64;
+    p->gmres_restart = 30;
+    p->gmres_max_it = 600;
+    p->newton_rtol = 1e-10;
+    p->newton_max_it = 25;
+    p->eta_max = 1e-2;
+    p->eta_min = 1e-12;
+    p->hbm_budget_bytes = 0;
+    return DG_OK;
+}
+
+// ------------------------------------------------------------------ setup
+template <class T>
+static cudaError_t dalloc(dg_ctx* ctx, T** ptr, int64_t n) {
+    if (n <= 0) n = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (size_t)n * sizeof(T));
+    if (e != cudaSuccess) return e;
+    ctx->allocs.push_back(q);
+    ctx->ws_bytes += n * (int64_t)sizeof(T);
+    *ptr = (T*)q;
+    return cudaSuccess;
+}
+
+static void free_all(dg_ctx* ctx) {
+    for (void* q : ctx->allocs) cudaFree(q);
+    ctx->allocs.clear();
+    if (ctx->hres) cudaFreeHost(ctx->hres);
+    ctx->hres = nullptr;
+}
+
+extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void* stream, dg_ctx** out) {
+    if (!out) return DG_ERR_ARG;
+    *out = nullptr;
+    if (!s || !prm || !s->phase || s->nx < 2 || s->ny < 1 || s->nz < 1 || !(s->h > 0)) return DG_ERR_ARG;
+    if ((prm->order != 0 && prm->order != 1) || (prm->chemistry != 0 && prm->chemistry != 1)) return DG_ERR_ARG;
+    if (!(prm->eps_struct > 0 && prm->eps_struct <= 1) || prm->gmres_restart < 1 || prm->gmres_restart > MAXK - 1)
+        return DG_ERR_ARG;
+    const int64_t ncell64 = (int64_t)s->nx * s->ny * s->nz;
+    if (ncell64 > 2000000000LL) return DG_ERR_ARG;
+    dg_ctx* ctx = new dg_ctx();
+    ctx->prm = *prm;
+    ctx->L.st = (cudaStream_t)stream;
+    ctx->L.counter = &ctx->launches;
+    const int nx = s->nx, ny = s->ny, nz = s->nz, ncell = (int)ncell64;
+    // ---- host geometry: phases, compacted structure list
+    std::vector<int32_t> cmap(ncell, -1), sidx;
+    sidx.reserve(ncell / 2);
+    for (int c = 0; c < ncell; ++c) {
+        uint8_t ph = s->phase[c];
+        if (ph > 2) { delete ctx; return DG_ERR_ARG; }
+        if (ph == 1) { cmap[c] = (int32_t)sidx.size(); sidx.push_back(c); }
+    }
+    int n_cc = 0;
+    for (int q = 0; q < ny * nz; ++q)
+        if (s->phase[(int64_t)q * nx] == 1) ++n_cc;
+    if (n_cc == 0) {
+        dg_status st = fail(ctx, DG_ERR_ARG, "no structure voxel touches the current collector");
+        delete ctx;
+        return st;
+    }
+    int n_sep = 0;
+    for (int i = nx - 1; i >= 0; --i) {
+        bool all = true;
+        for (int q = 0; q < ny * nz && all; ++q) all = s->phase[(int64_t)q * nx + i] == 2;
+        if (!all) break;
+        ++n_sep;
+    }
+    ctx->n_cc = n_cc;
+    // ---- device parameters
+    DevParams& P = ctx->P;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = nx; P.ny = ny; P.nz = nz;
+    P.n_cell = ncell;
+    P.n_struct = (int)sidx.size();
+    const bool to = prm->chemistry == DG_CHEM_TRADEOFF;
+    P.nl = to ? 6 : 3;
+    P.ns = to ? 2 : 0;
+    P.nf = P.nl + P.ns + 2;
+    P.order = prm->order;
+    P.h = s->h;
+    P.V = s->h * s->h * s->h;
+    P.A = s->h * s->h;
+    P.F = F_;
+    P.RT = R_ * prm->T;
+    P.F_RT = F_ / P.RT;
+    P.F_2RT = 0.5 * P.F_RT;
+    P.cref = CREF;
+    const int spec_to[6] = {0, 1, 2, 3, 4, 5};
+    const int spec_r3[3] = {0, 1, 2};
+    for (int m = 0; m < P.nl; ++m) {
+        int q = to ? spec_to[m] : spec_r3[m];
+        P.D0[m] = D0_TO[q];
+        P.zc[m] = Z_TO[q];
+        P.wS[m] = WS_TO[q];
+        P.kappa_m[m] = P.zc[m] * P.F_RT * P.D0[m];
+        P.Kd[m] = P.zc[m] * F_ * (P.D0[m] - D0_A);
+        P.Km[m] = P.zc[m] * F_ * P.F_RT * (P.zc[m] * P.D0[m] + D0_A);
+    }
+    P.D0A = D0_A;
+    P.visc = VISC;
+    const double es = prm->eps_struct;
+    P.eps_sep = EPS_SEP;
+    P.cbd = (X_CATHODE - X_SULFUR) / es;
+    P.eps_frozen[0] = EPS_S8_0 / es;
+    P.eps_frozen[1] = EPS_LI2S_0 / es;
+    P.aV0p = AV0 / es;
+    P.s8ref = 1.2 * EPS_S8_0 / es;
+    P.li2sref = AV_A * std::exp(-AV_B * prm->f_C) / es;
+    P.rhoM[0] = RHO_S8 / M_S8;
+    P.rhoM[1] = RHO_LI2S / M_LI2S;
+    P.kappa_s = KAPPA_S;
+    P.kAno = K_ANO;
+    double j_el = prm->j_el;
+    if (!(j_el > 0)) {
+        const double c_theo = 16.0 * F_ / M_S8;                       // C/kg (App. B)
+        const double L_cat = (nx - n_sep) * s->h;
+        j_el = prm->f_C / 3600.0 * c_theo * RHO_S8 * EPS_S8_0 * L_cat;
+    }
+    P.j_cc = j_el * (double)ny * nz / n_cc;
+    P.kC[0] = KC1; P.kC[1] = KC2;
+    P.sqK[0] = std::sqrt(KSP1); P.sqK[1] = std::sqrt(KSP2);
+    double ceq[6], d0, U5, U6;
+    tab6(prm->T, ceq, &d0, &U5, &U6);
+    const double U0s[6] = {U01, U02, U03, U04, U5, U6};
+    for (int k = 0; k < 6; ++k) { P.kE[k] = KE[k]; P.U0[k] = U0s[k]; }
+    P.penalty = prm->penalty;
+    P.smooth = prm->smooth;
+    const int nn = prm->order == 1 ? 8 : 1;
+    const double M = prm->order == 1 ? P.V / 8.0 : P.V;
+    int64_t off = 0;
+    for (int f = 0; f < P.nf; ++f) {
+        bool st = (f >= P.nl && f < P.nl + P.ns) || f == P.nf - 1;
+        P.is_struct[f] = st ? 1 : 0;
+        P.flen[f] = st ? P.n_struct : P.n_cell;
+        P.off[f] = off;
+        off += P.flen[f] * nn;
+        bool pot = f >= P.nf - 2;
+        P.rscale[f] = pot ? 1.0 / (M * F_ * CREF) : 1.0 / (M * CREF);
+    }
+    ctx->ndof = off;
+    // equilibrium field values
+    double vals[DG_MAXF];
+    if (to) {
+        for (int m = 0; m < 6; ++m) vals[m] = ceq[m];
+        vals[6] = EPS_S8_0 / es;
+        vals[7] = EPS_LI2S_0 / es;
+        vals[8] = 0.0;
+        vals[9] = d0;
+    } else {
+        vals[0] = 1000.0; vals[1] = 10.0; vals[2] = 100.0;
+        vals[3] = 0.0;
+        // Nernst potential of E1 (Eq. 24): U0 - RT/F ln(a_S8^2-^{1/2} / a_S8(L)^{1/2})
+        vals[4] = U01 - P.RT / F_ * (0.5 * std::log(vals[2] / CREF) - 0.5 * std::log(vals[1] / CREF));
+    }
+    // ---- allocations
+    const bool mixed = prm->precision == DG_PREC_MIXED;
+    const int m = prm->gmres_restart;
+    ctx->nblk = (int64_t)ncell * nn;
+    const int64_t N = ctx->ndof;
+    int64_t scratch = prm->order == 1 ? dg1_face_buffer_len(P) : (int64_t)ncell;
+    int64_t need = ncell * (1 + 4 + 4) + N * 8 * (6 + 4) + scratch * 8 * 2 +
+                   ctx->nblk * P.nf * P.nf * 8 + (int64_t)(m + 1) * N * (mixed ? 4 : 8) + 3 * N * (mixed ? 4 : 8) +
+                   N * 8 + (mixed ? (N * 4 + scratch * 4 * 2 + ctx->nblk * P.nf * P.nf * 4) : 0);
+    if (prm->hbm_budget_bytes > 0 && need > prm->hbm_budget_bytes) {
+        dg_status st = fail(ctx, DG_ERR_OOM, "workspace of " + std::to_string(need) + " bytes exceeds hbm_budget_bytes");
+        delete ctx;
+        return st;
+    }
+#define AL(ptr, n)                                                        \
+    do {                                                                  \
+        if (dalloc(ctx, &(ptr), (n)) != cudaSuccess) {                    \
+            free_all(ctx);                                                \
+            delete ctx;                                                   \
+            return DG_ERR_OOM;                                            \
+        }                                                                 \
+    } while (0)
+    AL(ctx->d_phase, ncell);
+    AL(ctx->d_cmap, ncell);
+    AL(ctx->d_sidx, (int64_t)sidx.size());
+    AL(ctx->gb, scratch);
+    AL(ctx->gbd, scratch);
+    AL(ctx->blk, ctx->nblk * P.nf * P.nf);
+    AL(ctx->d_bad, 4);
+    AL(ctx->zc, N); AL(ctx->zt, N); AL(ctx->R, N); AL(ctx->Rt, N); AL(ctx->dz, N); AL(ctx->zn, N);
+    AL(ctx->za, N); AL(ctx->zb, N); AL(ctx->zC, N); AL(ctx->zF, N);
+    AL(ctx->partial, (int64_t)RED_BLOCKS * MAXK + 64);
+    AL(ctx->dres, 256);
+    AL(ctx->d_vals, DG_MAXF);
+    if (mixed) {
+        float *V, *w, *u, *x;
+        AL(V, (int64_t)(m + 1) * N); AL(w, N); AL(u, N); AL(x, N);
+        ctx->V = V; ctx->w = w; ctx->u = u; ctx->x = x;
+        AL(ctx->z32, N);
+        AL(ctx->gb32, scratch);
+        AL(ctx->gbd32, scratch);
+        AL(ctx->blk32, ctx->nblk * P.nf * P.nf);
+    } else {
+        double *V, *w, *u, *x;
+        AL(V, (int64_t)(m + 1) * N); AL(w, N); AL(u, N); AL(x, N);
+        ctx->V = V; ctx->w = w; ctx->u = u; ctx->x = x;
+    }
+#undef AL
+    if (cudaMallocHost(&ctx->hres, 256 * sizeof(double)) != cudaSuccess) {
+        free_all(ctx);
+        delete ctx;
+        return DG_ERR_OOM;
+    }
+    cudaStream_t st = ctx->L.st;
+    if (cudaMemcpyAsync(ctx->d_phase, s->phase, ncell, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->d_cmap, cmap.data(), ncell * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        (!sidx.empty() && cudaMemcpyAsync(ctx->d_sidx, sidx.data(), sidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+        cudaMemcpyAsync(ctx->d_vals, vals, sizeof(vals), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        free_all(ctx);
+        delete ctx;
+        return DG_ERR_CUDA;
+    }
+    ctx->G.phase = ctx->d_phase;
+    ctx->G.cmap = ctx->d_cmap;
+    ctx->G.sidx = ctx->d_sidx;
+    *out = ctx;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_destroy(dg_ctx* ctx) {
+    if (!ctx) return DG_ERR_ARG;
+    if (ctx->L.st) cudaStreamSynchronize(ctx->L.st);
+    else cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+    return DG_OK;
+}
+
+extern "C" const char* dg_last_error(const dg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+extern "C" int64_t dg_launch_count(const dg_ctx* ctx) { return ctx ? ctx->launches : 0; }
+extern "C" int64_t dg_workspace_bytes(const dg_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+extern "C" dg_status dg_layout(const dg_ctx* ctx, int64_t* n_dof, int32_t* n_fields, int64_t off[10], int64_t len[10]) {
+    if (!ctx) return DG_ERR_ARG;
+    const int nn = ctx->P.order == 1 ? 8 : 1;
+    if (n_dof) *n_dof = ctx->ndof;
+    if (n_fields) *n_fields = ctx->P.nf;
+    for (int f = 0; f < ctx->P.nf; ++f) {
+        if (off) off[f] = ctx->P.off[f];
+        if (len) len[f] = ctx->P.flen[f] * nn;
+    }
+    return DG_OK;
+}
+
+// ------------------------------------------------------------------ model calls
+static dg_status residual_(dg_ctx* ctx, const double* z, const double* zn, double t, double dt, int relax, double* r) {
+    cudaError_t e = ctx->P.order == 0 ? dg0_residual(ctx->L, ctx->P, ctx->G, z, zn, t, dt, relax, r, ctx->gb)
+                                      : dg1_residual(ctx->L, ctx->P, ctx->G, z, zn, t, dt, relax, r, ctx->gb);
+    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("residual: ") + cudaGetErrorString(e));
+    ctx->res_evals++;
+    return DG_OK;
+}
+
+template <class S>
+static dg_status jvp_(dg_ctx* ctx, const S* z, const S* v, double t, double dt, int relax, double sc_dt, S* out,
+                      S* gb, S* gbd) {
+    cudaError_t e = ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd)
+                                      : dg1_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd);
+    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("jvp: ") + cudaGetErrorString(e));
+    ctx->jvp_evals++;
+    return DG_OK;
+}
+
+static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt, int relax) {
+    cudaError_t e = ctx->P.order == 0 ? dg0_blocks(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb)
+                                      : dg1_blocks(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb);
+    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("blocks: ") + cudaGetErrorString(e));
+    e = cudaMemsetAsync(ctx->d_bad, 0, sizeof(int), ctx->L.st);
+    if (e == cudaSuccess) e = block_invert(ctx->L, ctx->blk, ctx->nblk, ctx->P.nf, ctx->blk32, ctx->d_bad);
+    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
+    return DG_OK;
+}
+
+static dg_status sync_(dg_ctx* ctx) {
+    cudaError_t e = cudaStreamSynchronize(ctx->L.st);
+    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+    return DG_OK;
+}
+
+static dg_status scaled_norm_(dg_ctx* ctx, const double* r, double dt, double* out) {
+    cudaError_t e = scaled_norm2(ctx->L, ctx->P, r, dt, ctx->partial, ctx->dres + 200);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->hres + 200, ctx->dres + 200, sizeof(double), cudaMemcpyDeviceToHost, ctx->L.st);
+    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("norm: ") + cudaGetErrorString(e));
+    dg_status s = sync_(ctx);
+    if (s != DG_OK) return s;
+    *out = std::sqrt(ctx->hres[200]);
+    return DG_OK;
+}
+
+extern "C" dg_status dg_residual(dg_ctx* ctx, const double* z, const double* zold, double t, double dt, double* r) {
+    if (!ctx || !z || !zold || !r || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_residual: bad argument");
+    return residual_(ctx, z, zold, t, dt, 0, r);
+}
+
+extern "C" dg_status dg_jvp(dg_ctx* ctx, const double* z, double t, double dt, const double* v, double* jv) {
+    if (!ctx || !z || !v || !jv || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_jvp: bad argument");
+    return jvp_<double>(ctx, z, v, t, dt, 0, 0.0, jv, ctx->gb, ctx->gbd);
+}
+
+extern "C" dg_status dg_block_jacobi(dg_ctx* ctx, const double* z, double t, double dt, const double* v, double* out) {
+    if (!ctx || !z || !v || !out || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_block_jacobi: bad argument");
+    dg_status s = build_precond(ctx, z, t, dt, 0);
+    if (s != DG_OK) return s;
+    CK(block_apply<double>(ctx->L, ctx->P, ctx->G, ctx->blk, v, out));
+    return DG_OK;
+}
+
+extern "C" dg_status dg_row_scales(dg_ctx* ctx, double dt, double* s) {
+    if (!ctx || !s || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_row_scales: bad argument");
+    CK(row_scales(ctx->L, ctx->P, dt, s));
+    return DG_OK;
+}
+
+extern "C" dg_status dg_equilibrium_state(dg_ctx* ctx, double* z) {
+    if (!ctx || !z) return fail(ctx, DG_ERR_ARG, "dg_equilibrium_state: bad argument");
+    CK(fill_equilibrium(ctx->L, ctx->P, ctx->d_vals, z));
+    return DG_OK;
+}
+
+extern "C" dg_status dg_cell_voltage(dg_ctx* ctx, const double* z, double* U) {
+    if (!ctx || !z || !U) return fail(ctx, DG_ERR_ARG, "dg_cell_voltage: bad argument");
+    CK(cell_voltage(ctx->L, ctx->P, ctx->G, z, ctx->partial, ctx->dres + 210));
+    CK(cudaMemcpyAsync(ctx->hres + 210, ctx->dres + 210, sizeof(double), cudaMemcpyDeviceToHost, ctx->L.st));
+    dg_status s = sync_(ctx);
+    if (s != DG_OK) return s;
+    *U = ctx->hres[210];
+    return DG_OK;
+}
+
+extern "C" dg_status dg_ledger(dg_ctx* ctx, const double* z, double out[5]) {
+    if (!ctx || !z || !out) return fail(ctx, DG_ERR_ARG, "dg_ledger: bad argument");
+    CK(ledger(ctx->L, ctx->P, ctx->G, z, ctx->partial, ctx->dres + 220));
+    CK(cudaMemcpyAsync(ctx->hres + 220, ctx->dres + 220, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->L.st));
+    dg_status s = sync_(ctx);
+    if (s != DG_OK) return s;
+    for (int k = 0; k < 5; ++k) out[k] = ctx->hres[220 + k];
+    return DG_OK;
+}
+
+// ------------------------------------------------------------------ GMRES
+// Right-preconditioned restarted GMRES(m) for (S J) d = b with classical Gram-Schmidt and one
+// re-orthogonalisation pass; S the Newton row scales, preconditioner the inverted diagonal
+// blocks of S J.  b = -S R(z) is formed from ctx->R.  The correction is accumulated in ctx->dz.
+template <class S>
+static dg_status gmres_(dg_ctx* ctx, const double* z, double t, double dt, int relax, double eta, int* its_out) {
+    const int64_t N = ctx->ndof;
+    const int m = ctx->prm.gmres_restart;
+    const LaunchCtx& L = ctx->L;
+    S* V = (S*)ctx->V;
+    S* w = (S*)ctx->w;
+    S* u = (S*)ctx->u;
+    S* x = (S*)ctx->x;
+    const bool mixed = std::is_same<S, float>::value;
+    const S* zS = mixed ? (const S*)ctx->z32 : (const S*)z;
+    S* gbS = mixed ? (S*)ctx->gb32 : (S*)ctx->gb;
+    S* gbdS = mixed ? (S*)ctx->gbd32 : (S*)ctx->gbd;
+    const void* blkS = mixed ? (const void*)ctx->blk32 : (const void*)ctx->blk;
+    if (mixed) CK(to_f32(L, ctx->z32, z, N));
+    CK(cudaMemsetAsync(ctx->dz, 0, N * sizeof(double), L.st));
+    ctx->hres[100] = 1.0;
+    CK(cudaMemcpyAsync(ctx->dres + 100, ctx->hres + 100, sizeof(double), cudaMemcpyHostToDevice, L.st));
+    double beta0 = -1.0;
+    int total = 0;
+    std::vector<double> H((m + 1) * m), cs(m), sn(m), gvec(m + 1), y(m);
+    const int max_it = ctx->prm.gmres_max_it;
+    bool converged = false;
+    for (int cycle = 0; total < max_it && !converged; ++cycle) {
+        // residual of the current correction: r = b - A dz = -S R - S J dz
+        if (cycle == 0) {
+            CK(neg_scaled<S>(L, ctx->P, ctx->R, dt, w));
+        } else {
+            if (mixed) CK(to_f32(L, (float*)u, ctx->dz, N));
+            else CK(cudaMemcpyAsync(u, ctx->dz, N * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+            dg_status s = jvp_<S>(ctx, zS, u, t, dt, relax, dt, x, gbS, gbdS);
+            if (s != DG_OK) return s;
+            CK(neg_scaled<S>(L, ctx->P, ctx->R, dt, w));
+            CK(maxpy<S>(L, w, x, N, N, 1, ctx->dres + 100, -1.0));   // dres[100] = 1
+        }
+        CK(mdot<S>(L, w, N, N, 1, w, ctx->partial, ctx->dres + 64));
+        CK(scale_copy<S>(L, V, w, N, ctx->dres + 64, 1.0));
+        CK(cudaMemcpyAsync(ctx->hres + 64, ctx->dres + 64, sizeof(double), cudaMemcpyDeviceToHost, L.st));
+        dg_status s = sync_(ctx);
+        if (s != DG_OK) return s;
+        double beta = std::sqrt(ctx->hres[64]);
+        if (!std::isfinite(beta)) return fail(ctx, DG_ERR_NONFINITE, "GMRES: non-finite residual");
+        if (beta0 < 0) beta0 = beta;
+        if (beta <= eta * beta0 || beta == 0.0) { converged = true; break; }
+        std::fill(gvec.begin(), gvec.end(), 0.0);
+        gvec[0] = beta;
+        int j = 0;
+        for (; j < m && total < max_it; ++j) {
+            S* vj = V + (int64_t)j * N;
+            CK(block_apply<S>(L, ctx->P, ctx->G, blkS, vj, u));
+            s = jvp_<S>(ctx, zS, u, t, dt, relax, dt, w, gbS, gbdS);
+            if (s != DG_OK) return s;
+            CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres));
+            CK(maxpy<S>(L, w, V, N, N, j + 1, ctx->dres, -1.0));
+            CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres + 32));
+            CK(maxpy<S>(L, w, V, N, N, j + 1, ctx->dres + 32, -1.0));
+            CK(mdot<S>(L, w, N, N, 1, w, ctx->partial, ctx->dres + 64));
+            CK(scale_copy<S>(L, V + (int64_t)(j + 1) * N, w, N, ctx->dres + 64, 1.0));
+            CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 65 * sizeof(double), cudaMemcpyDeviceToHost, L.st));
+            s = sync_(ctx);
+            if (s != DG_OK) return s;
+            ++total;
+            for (int i = 0; i <= j; ++i) H[i * m + j] = ctx->hres[i] + ctx->hres[32 + i];
+            double hn = std::sqrt(ctx->hres[64]);
+            if (!std::isfinite(hn)) return fail(ctx, DG_ERR_NONFINITE, "GMRES: non-finite Krylov vector");
+            H[(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; ++i) {
+                double a = H[i * m + j], b = H[(i + 1) * m + j];
+                H[i * m + j] = cs[i] * a + sn[i] * b;
+                H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+            }
+            double a = H[j * m + j], b = H[(j + 1) * m + j];
+            double r = std::hypot(a, b);
+            cs[j] = r > 0 ? a / r : 1.0;
+            sn[j] = r > 0 ? b / r : 0.0;
+            H[j * m + j] = r;
+            H[(j + 1) * m + j] = 0.0;
+            gvec[j + 1] = -sn[j] * gvec[j];
+            gvec[j] = cs[j] * gvec[j];
+            if (std::fabs(gvec[j + 1]) <= eta * beta0 || hn == 0.0) { ++j; converged = true; break; }
+        }
+        // y = H^{-1} g (upper triangular j x j), x = sum y_k V_k, dz += M^{-1} x
+        for (int i = j - 1; i >= 0; --i) {
+            double acc = gvec[i];
+            for (int k = i + 1; k < j; ++k) acc -= H[i * m + k] * y[k];
+            y[i] = H[i * m + i] != 0.0 ? acc / H[i * m + i] : 0.0;
+        }
+        for (int i = 0; i < j; ++i) ctx->hres[100 + i] = y[i];
+        CK(cudaMemcpyAsync(ctx->dres + 100, ctx->hres + 100, j * sizeof(double), cudaMemcpyHostToDevice, L.st));
+        CK(cudaMemsetAsync(x, 0, N * sizeof(S), L.st));
+        CK(maxpy<S>(L, x, V, N, N, j, ctx->dres + 100, 1.0));
+        CK(block_apply<S>(L, ctx->P, ctx->G, blkS, x, u));
+        if (mixed) CK(to_f64_add(L, ctx->dz, (const float*)u, 1.0, N));
+        else CK(axpby(L, ctx->dz, 1.0, (const double*)u, 1.0, N));
+        // restore dres[100] = 1 for the restart residual update
+        ctx->hres[100] = 1.0;
+        CK(cudaMemcpyAsync(ctx->dres + 100, ctx->hres + 100, sizeof(double), cudaMemcpyHostToDevice, L.st));
+        s = sync_(ctx);
+        if (s != DG_OK) return s;
+    }
+    *its_out = total;
+    return DG_OK;
+}
+
+// ------------------------------------------------------------------ Newton
+// Solve R(z; z^n, t1, dt) = 0 starting from z = zstart (ctx->zc holds the iterate).
+static dg_status newton_(dg_ctx* ctx, const double* zn, double t1, double dt, int relax, dg_step_info* info) {
+    const int64_t N = ctx->ndof;
+    const LaunchCtx& L = ctx->L;
+    ctx->gmres_its = 0;
+    ctx->res_evals = 0;
+    ctx->jvp_evals = 0;
+    dg_status s = residual_(ctx, ctx->zc, zn, t1, dt, relax, ctx->R);
+    if (s != DG_OK) return s;
+    double nrm;
+    s = scaled_norm_(ctx, ctx->R, dt, &nrm);
+    if (s != DG_OK) return s;
+    const double n0 = nrm;
+    if (info) { info->norm0 = n0; info->norm = n0; info->converged = 0; info->newton_iterations = 0; }
+    if (!std::isfinite(nrm)) return fail(ctx, DG_ERR_NONFINITE, "non-finite initial residual");
+    double eta = ctx->prm.eta_max;
+    const bool mixed = ctx->prm.precision == DG_PREC_MIXED;
+    int it = 0;
+    dg_status result = DG_OK;
+    for (;;) {
+        if (nrm <= ctx->prm.newton_rtol * n0 || nrm == 0.0) break;
+        if (it >= ctx->prm.newton_max_it) { result = fail(ctx, DG_ERR_NOCONV, "Newton: iteration limit"); break; }
+        s = build_precond(ctx, ctx->zc, t1, dt, relax);
+        if (s != DG_OK) return s;
+        int its = 0;
+        // forcing term never asks for more than the Newton tolerance needs
+        double eta_eff = std::max(eta, 0.5 * ctx->prm.newton_rtol * n0 / nrm);
+        eta_eff = std::min(eta_eff, ctx->prm.eta_max);
+        s = mixed ? gmres_<float>(ctx, ctx->zc, t1, dt, relax, std::max(eta_eff, 1e-6), &its)
+                  : gmres_<double>(ctx, ctx->zc, t1, dt, relax, eta_eff, &its);
+        if (s != DG_OK) return s;
+        ctx->gmres_its += its;
+        // backtracking line search on ||S R||
+        double lam = 1.0, nt = 0.0;
+        bool ok = false;
+        for (int cut = 0; cut <= 10; ++cut) {
+            CK(cudaMemcpyAsync(ctx->zt, ctx->zc, N * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+            CK(axpby(L, ctx->zt, 1.0, ctx->dz, lam, N));
+            s = residual_(ctx, ctx->zt, zn, t1, dt, relax, ctx->Rt);
+            if (s != DG_OK) return s;
+            s = scaled_norm_(ctx, ctx->Rt, dt, &nt);
+            if (s != DG_OK) return s;
+            if (std::isfinite(nt) && nt <= (1.0 - 1e-4 * lam) * nrm) { ok = true; break; }
+            lam *= 0.5;
+        }
+        if (!ok) { result = fail(ctx, DG_ERR_NOCONV, "Newton: line search failed"); break; }
+        std::swap(ctx->zc, ctx->zt);
+        std::swap(ctx->R, ctx->Rt);
+        // Eisenstat-Walker choice 2 (gamma 0.9, alpha 2) with the usual safeguard
+        double eta_new = 0.9 * (nt / nrm) * (nt / nrm);
+        double safe = 0.9 * eta * eta;
+        if (safe > 0.1) eta_new = std::max(eta_new, safe);
+        eta = std::min(ctx->prm.eta_max, std::max(ctx->prm.eta_min, eta_new));
+        nrm = nt;
+        ++it;
+    }
+    if (info) {
+        info->converged = result == DG_OK;
+        info->newton_iterations = it;
+        info->gmres_iterations = ctx->gmres_its;
+        info->residual_evals = ctx->res_evals;
+        info->jvp_evals = ctx->jvp_evals;
+        info->norm = nrm;
+    }
+    return result;
+}
+
+extern "C" dg_status dg_step(dg_ctx* ctx, const double* zn, double* z, double t, double dt, dg_step_info* info) {
+    if (!ctx || !zn || !z || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_step: bad argument");
+    const int64_t N = ctx->ndof;
+    CK(cudaMemcpyAsync(ctx->zn, zn, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->L.st));
+    CK(cudaMemcpyAsync(ctx->zc, zn, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->L.st));
+    dg_status s = newton_(ctx, ctx->zn, t + dt, dt, 0, info);
+    if (s != DG_OK && s != DG_ERR_NOCONV) return s;
+    CK(cudaMemcpyAsync(z, ctx->zc, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->L.st));
+    dg_status s2 = sync_(ctx);
+    return s != DG_OK ? s : s2;
+}
+
+extern "C" dg_status dg_step_host(dg_ctx* ctx, const double* zn_host, double* z_host, double t, double dt,
+                                  dg_step_info* info) {
+    if (!ctx || !zn_host || !z_host || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_step_host: bad argument");
+    const int64_t N = ctx->ndof;
+    CK(cudaMemcpyAsync(ctx->za, zn_host, N * sizeof(double), cudaMemcpyHostToDevice, ctx->L.st));
+    dg_status s = dg_step(ctx, ctx->za, ctx->zb, t, dt, info);
+    if (s != DG_OK && s != DG_ERR_NOCONV) return s;
+    CK(cudaMemcpyAsync(z_host, ctx->zb, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->L.st));
+    dg_status s2 = sync_(ctx);
+    return s != DG_OK ? s : s2;
+}
+
+extern "C" dg_status dg_relax(dg_ctx* ctx, double* z, double dt, int32_t n_steps) {
+    if (!ctx || !z || !(dt > 0) || n_steps < 0) return fail(ctx, DG_ERR_ARG, "dg_relax: bad argument");
+    const int64_t N = ctx->ndof;
+    double t = 0.0;
+    for (int k = 0; k < n_steps; ++k) {
+        CK(cudaMemcpyAsync(ctx->zn, z, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->L.st));
+        CK(cudaMemcpyAsync(ctx->zc, z, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->L.st));
+        dg_step_info info;
+        dg_status s = newton_(ctx, ctx->zn, t + dt, dt, 1, &info);
+        if (s != DG_OK) return s;
+        CK(cudaMemcpyAsync(z, ctx->zc, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->L.st));
+        t += dt;
+    }
+    return sync_(ctx);
+}
+
+// ------------------------------------------------------------------ discharge
+// One implicit Euler attempt from `from` (device) to `to` (device).
+static dg_status attempt_(dg_ctx* ctx, const double* from, double* to, double t, double dt, dg_step_info* info) {
+    return dg_step(ctx, from, to, t, dt, info);
+}
+
+static double rel_err_(dg_ctx* ctx, const double* zF, const double* zC, dg_status* st) {
+    // ||zF - zC|| / ||zF|| with the deterministic reductions
+    const int64_t N = ctx->ndof;
+    const LaunchCtx& L = ctx->L;
+    *st = DG_OK;
+    if (cudaMemcpyAsync(ctx->zt, zF, N * sizeof(double), cudaMemcpyDeviceToDevice, L.st) != cudaSuccess ||
+        axpby(L, ctx->zt, 1.0, zC, -1.0, N) != cudaSuccess ||
+        mdot<double>(L, ctx->zt, N, N, 1, ctx->zt, ctx->partial, ctx->dres + 230) != cudaSuccess ||
+        mdot<double>(L, zF, N, N, 1, zF, ctx->partial, ctx->dres + 231) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->hres + 230, ctx->dres + 230, 2 * sizeof(double), cudaMemcpyDeviceToHost, L.st) != cudaSuccess) {
+        *st = fail(ctx, DG_ERR_CUDA, "error estimate failed");
+        return 0.0;
+    }
+    *st = sync_(ctx);
+    return std::sqrt(ctx->hres[230] / ctx->hres[231]);
+}
+
+extern "C" dg_status dg_discharge(dg_ctx* ctx, double* z, const dg_discharge_opts* o, dg_curve* out) {
+    if (!ctx || !z || !o || !out || out->n_max < 1 || !out->t || !out->dt || !out->U_cell || !out->c_m)
+        return fail(ctx, DG_ERR_ARG, "dg_discharge: bad argument");
+    const int64_t N = ctx->ndof;
+    const LaunchCtx& L = ctx->L;
+    const double c_theo_ah = 16.0 * F_ / M_S8 / 3600.0;
+    out->n = 0;
+    out->attempts = 0;
+    out->failures = 0;
+    out->status = DG_OK;
+    double t = o->t0, dt = o->dt0;
+    double* cur = ctx->za;
+    double* nxt = ctx->zb;
+    CK(cudaMemcpyAsync(cur, z, N * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+    int sct = 0, halv = 0, n = 0;
+    const int max_h = o->max_halvings > 0 ? o->max_halvings : 30;
+    const double t_end = o->t_end > 0 ? o->t_end : INFINITY;
+    const int max_steps = std::min(o->max_steps > 0 ? o->max_steps : out->n_max, out->n_max);
+    double err_prev = o->tol, dt_prev = dt;
+    dg_status result = DG_OK;
+    while (n < max_steps && t < t_end) {
+        dg_step_info info;
+        std::memset(&info, 0, sizeof(info));
+        bool ok = false;
+        double lim = 1.0;
+        if (o->replay_dt) {
+            if (n >= o->n_replay) break;
+            dt = o->replay_dt[n];
+        }
+        if (o->controller == DG_CTRL_H211B && !o->replay_dt) {
+            // Eqs. 51-54 (see the oracle's controller for the reading of Fig. 5)
+            lim = 0.0;
+            double err = INFINITY;
+            int tries = 0;
+            bool aborted = false;
+            while (err > 1.02 * o->tol || lim < 0.9) {
+                out->attempts++;
+                dg_status sC = attempt_(ctx, cur, ctx->zC, t, dt, &info);
+                dg_status sF1 = sC == DG_OK ? attempt_(ctx, cur, nxt, t, 0.5 * dt, &info) : sC;
+                dg_status sF = sF1 == DG_OK ? attempt_(ctx, nxt, ctx->zF, t + 0.5 * dt, 0.5 * dt, &info) : sF1;
+                if (sF != DG_OK && sF != DG_ERR_NOCONV && sF != DG_ERR_NONFINITE) return sF;
+                if (sF != DG_OK) {
+                    out->failures++;
+                    dt *= 0.5;
+                    ++halv;
+                    lim = 0.0;
+                    err = INFINITY;
+                    if (halv > max_h || dt < o->dt_min) { aborted = true; break; }
+                    continue;
+                }
+                halv = 0;
+                dg_status se;
+                err = std::max(rel_err_(ctx, ctx->zF, ctx->zC, &se), 1e-300);
+                if (se != DG_OK) return se;
+                double ratio = std::pow(o->tol / err, 0.25) * std::pow(o->tol / err_prev, 0.25) * std::pow(dt / dt_prev, -0.25);
+                lim = 1.0 + std::atan(ratio - 1.0);
+                if (err > 1.02 * o->tol || lim < 0.9) {
+                    if (++tries > 50) { aborted = true; break; }
+                    err_prev = err;
+                    dt_prev = dt;
+                    dt = std::min(dt * lim, o->dt_max);
+                }
+            }
+            if (aborted) { result = fail(ctx, DG_ERR_ABORTED, "H211b controller gave up"); break; }
+            // Richardson extrapolation, Eq. 54: z = 2 z_F - z_C
+            CK(cudaMemcpyAsync(nxt, ctx->zF, N * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+            CK(axpby(L, nxt, 2.0, ctx->zC, -1.0, N));
+            err_prev = err;
+            dt_prev = dt;
+            ok = true;
+        } else {
+            out->attempts++;
+            dg_status s = attempt_(ctx, cur, nxt, t, dt, &info);
+            if (s != DG_OK && s != DG_ERR_NOCONV && s != DG_ERR_NONFINITE) return s;
+            ok = s == DG_OK;
+        }
+        if (ok) {
+            std::swap(cur, nxt);
+            t += dt;
+            halv = 0;
+            double U;
+            dg_status s = dg_cell_voltage(ctx, cur, &U);
+            if (s != DG_OK) return s;
+            out->t[n] = t;
+            out->dt[n] = dt;
+            out->U_cell[n] = U;
+            out->c_m[n] = t / 3600.0 * ctx->prm.f_C * c_theo_ah;
+            if (out->newton_its) out->newton_its[n] = info.newton_iterations;
+            if (out->gmres_its) out->gmres_its[n] = info.gmres_iterations;
+            ++n;
+            out->n = n;
+            if (U <= o->cutoff_V) break;
+            if (o->controller == DG_CTRL_H211B && !o->replay_dt) {
+                dt = std::min(lim * dt, o->dt_max);
+            } else if (o->controller == DG_CTRL_NAIVE && !o->replay_dt) {
+                if (++sct == 3) { dt *= 1.2; sct = 0; }
+                dt = std::min(dt, o->dt_max);
+            }
+        } else {
+            if (o->replay_dt) { result = fail(ctx, DG_ERR_NOCONV, "replayed step did not converge"); break; }
+            out->failures++;
+            dt *= 0.5;
+            sct = 0;
+            if (++halv > max_h || dt < o->dt_min) { result = fail(ctx, DG_ERR_ABORTED, "30 consecutive halvings"); break; }
+        }
+    }
+    CK(cudaMemcpyAsync(z, cur, N * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+    dg_status s = sync_(ctx);
+    out->status = result;
+    return result != DG_OK ? result : s;
+}

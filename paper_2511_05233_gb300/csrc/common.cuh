@@ -1,0 +1,265 @@
+// Shared device-side definitions of libdgls: parameters, forward-mode dual numbers and the
+// pointwise Li-S model (constitutive laws and reaction sources) templated on the scalar type.
+//
+// Scalar types: double / float (values) and Dual<double> / Dual<float> (value + one tangent):
+// the same model code gives the residual (double), the exact Jacobian-vector product
+// (Dual<double>), its FP32 version for the mixed-precision Krylov loop (Dual<float>), and the
+// columns of the diagonal Jacobian blocks (Dual<double> seeded with one own-field direction).
+#pragma once
+#include <cstdint>
+#include <cmath>
+#include <cuda_runtime.h>
+#include <type_traits>
+
+#define DG_MAXF 10
+
+namespace dgls {
+
+// ------------------------------------------------------------------------------ parameters
+// All physical inputs of the model in SI units, filled on the host in dg_setup from the
+// paper's tables and passed to every kernel by value.
+struct DevParams {
+    int nx, ny, nz;
+    int n_cell, n_struct;
+    int nf, nl, ns;            // fields, liquid species, solid species
+    int order;
+    double h, V, A;            // voxel width, volume, face area
+    double F, RT, F_RT, F_2RT, cref;
+    double D0[6];              // liquid species at infinite dilution (Tab. 5.2)
+    double zc[6];              // charge numbers
+    double wS[6];              // sulfur atoms per species (c_S^L of Sec. 2.2)
+    double D0A;                // eliminated anion
+    double visc;               // Eq. 2 exponent, m^3/mol
+    double kappa_m[6];         // z_i F/(RT) D0_i: migration coefficient over g c_i
+    double Kd[6];              // z_j F (D0_j - D0_A): liquid-charge diffusion coefficient over g
+    double Km[6];              // z_j F^2/(RT) (z_j D0_j + D0_A): liquid-charge migration over g c_j
+    double eps_sep, cbd;       // separator porosity (Sec. 2.1), localised CBD fraction (Eq. 57)
+    double eps_frozen[2];      // solid fractions when the chemistry has no solid fields
+    double aV0p, s8ref, li2sref;   // Eq. 57: a_V0/eps_struct, 1.2 eps_S8,0/eps_struct, a e^{-b f_C}/eps_struct
+    double rhoM[2];            // rho/M of S8(S), Li2S(S)
+    double kappa_s;            // kappa_S^eff (Tab. 5.1)
+    double kAno;               // k_E,Ano
+    double j_cc;               // Neumann current per structure face at x = 0, A/m^2
+    double kC[2], sqK[2];      // C1, C2: k_C and sqrt(K_sp)
+    double kE[6], U0[6];       // E1..E6
+    double penalty;            // DG1 interior penalty factor
+    int smooth;                // T_H on C2 and E4
+    int64_t off[DG_MAXF];      // field offsets in the state vector
+    int64_t flen[DG_MAXF];     // field lengths (per node for DG1)
+    int is_struct[DG_MAXF];    // field lives on structure voxels only
+    double rscale[DG_MAXF];    // Newton row scales divided by dt (per field)
+};
+
+// ------------------------------------------------------------------------------ dual numbers
+template <class S>
+struct Dual {
+    S v, d;
+};
+
+template <class S> __host__ __device__ __forceinline__ Dual<S> mkd(S v, S d) { Dual<S> r; r.v = v; r.d = d; return r; }
+
+template <class S> __device__ __forceinline__ Dual<S> operator+(Dual<S> a, Dual<S> b) { return mkd(a.v + b.v, a.d + b.d); }
+template <class S> __device__ __forceinline__ Dual<S> operator-(Dual<S> a, Dual<S> b) { return mkd(a.v - b.v, a.d - b.d); }
+template <class S> __device__ __forceinline__ Dual<S> operator-(Dual<S> a) { return mkd(-a.v, -a.d); }
+template <class S> __device__ __forceinline__ Dual<S> operator*(Dual<S> a, Dual<S> b) { return mkd(a.v * b.v, a.v * b.d + a.d * b.v); }
+template <class S> __device__ __forceinline__ Dual<S> operator*(Dual<S> a, S b) { return mkd(a.v * b, a.d * b); }
+template <class S> __device__ __forceinline__ Dual<S> operator*(S a, Dual<S> b) { return mkd(a * b.v, a * b.d); }
+template <class S> __device__ __forceinline__ Dual<S> operator+(Dual<S> a, S b) { return mkd(a.v + b, a.d); }
+template <class S> __device__ __forceinline__ Dual<S> operator+(S a, Dual<S> b) { return mkd(a + b.v, b.d); }
+template <class S> __device__ __forceinline__ Dual<S> operator-(Dual<S> a, S b) { return mkd(a.v - b, a.d); }
+template <class S> __device__ __forceinline__ Dual<S> operator-(S a, Dual<S> b) { return mkd(a - b.v, -b.d); }
+template <class S> __device__ __forceinline__ Dual<S>& operator+=(Dual<S>& a, Dual<S> b) { a.v += b.v; a.d += b.d; return a; }
+template <class S> __device__ __forceinline__ Dual<S>& operator-=(Dual<S>& a, Dual<S> b) { a.v -= b.v; a.d -= b.d; return a; }
+
+__device__ __forceinline__ double sexp(double x) { return exp(x); }
+__device__ __forceinline__ float sexp(float x) { return expf(x); }
+__device__ __forceinline__ double ssqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float ssqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double slog(double x) { return log(x); }
+__device__ __forceinline__ float slog(float x) { return logf(x); }
+
+template <class S> __device__ __forceinline__ S val(S x) { return x; }
+template <class S> __device__ __forceinline__ S val(Dual<S> x) { return x.v; }
+
+// scalar-type traits
+template <class T> struct Base { typedef T type; };
+template <class S> struct Base<Dual<S>> { typedef S type; };
+
+template <class T> __device__ __forceinline__ T cst(double v) { return T(v); }
+
+template <class T> struct Make {
+    static __device__ __forceinline__ T c(double v) { return T(v); }
+    static __device__ __forceinline__ T var(double v, double d) { return T(v); }
+};
+template <class S> struct Make<Dual<S>> {
+    static __device__ __forceinline__ Dual<S> c(double v) { return mkd<S>(S(v), S(0)); }
+    static __device__ __forceinline__ Dual<S> var(double v, double d) { return mkd<S>(S(v), S(d)); }
+};
+
+template <class S> __device__ __forceinline__ Dual<S> operator/(Dual<S> a, Dual<S> b) {
+    S q = a.v / b.v;
+    return mkd(q, (a.d - q * b.d) / b.v);
+}
+template <class S> __device__ __forceinline__ Dual<S> operator/(Dual<S> a, S b) { return mkd(a.v / b, a.d / b); }
+
+template <class S> __device__ __forceinline__ Dual<S> sexp(Dual<S> x) { S e = sexp(x.v); return mkd(e, e * x.d); }
+template <class S> __device__ __forceinline__ Dual<S> ssqrt(Dual<S> x) { S r = ssqrt(x.v); return mkd(r, x.d / (S(2) * r)); }
+
+// max(x, 0) with the branch taken on the value
+template <class S> __device__ __forceinline__ S pos(S x) { return x > S(0) ? x : S(0); }
+template <class S> __device__ __forceinline__ Dual<S> pos(Dual<S> x) { return x.v > S(0) ? x : mkd(S(0), S(0)); }
+
+// x^{3/2} of max(x, 0)
+template <class T> __device__ __forceinline__ T pow15(T x) {
+    typedef typename Base<T>::type S;
+    if (val(x) > S(0)) return x * ssqrt(x);
+    return Make<T>::c(0.0);
+}
+
+// log of an activity a = max(c, 0)/c_ref: -inf (with zero tangent) at a <= 0, so that
+// exp(nu log a - x) vanishes like the mass-action product a^nu does.
+template <class S> __device__ __forceinline__ S log_act(S c, double cref) {
+    return c > S(0) ? slog(c / S(cref)) : -S(INFINITY);
+}
+template <class S> __device__ __forceinline__ Dual<S> log_act(Dual<S> c, double cref) {
+    if (c.v > S(0)) return mkd(slog(c.v / S(cref)), c.d / c.v);
+    return mkd(-S(INFINITY), S(0));
+}
+
+// {a, b}_H = 2ab/(a+b) (Eq. 45), 0 unless ab > 0
+template <class T> __device__ __forceinline__ T harm(T a, T b) {
+    typedef typename Base<T>::type S;
+    if (val(a) * val(b) > S(0)) return (S(2) * a * b) / (a + b);
+    return Make<T>::c(0.0);
+}
+
+// T_H(t) of Eq. 56
+__host__ __device__ inline double smooth_step(double t) { return 0.5 * (1.0 + tanh(6.0 * (t - 1.0))); }
+
+// ------------------------------------------------------------------------------ chemistries
+// Three-species chemistry: liquid Li+, S8(L), S8^2- (fields 0..2), Phi^L (3), Phi^S (4); E1 only.
+struct ChemR3 {
+    static constexpr int NL = 3, NS = 0, NF = 5;
+    static constexpr int PHIL = 3, PHIS = 4;
+};
+// Tradeoff Chemistry (Tab. 3): Li+, S8(L), S8^2-, S6^2-, S4^2-, S^2- (0..5), eps_S8 (6),
+// eps_Li2S (7), Phi^L (8), Phi^S (9).
+struct ChemTO {
+    static constexpr int NL = 6, NS = 2, NF = 10;
+    static constexpr int PHIL = 8, PHIS = 9;
+};
+
+// Liquid volume fraction: 1 - CBD - solids in structure (Sec. 2.5 (ii), Eq. 57), 0.4 in the
+// separator, 1 in macro-pores.
+template <class Chem, class T>
+__device__ __forceinline__ T liquid_fraction(const DevParams& p, int ph, const T* es) {
+    if (ph == 1) {
+        T s = Make<T>::c(1.0 - p.cbd);
+        if (Chem::NS == 2) {
+            s = s - es[0];
+            s = s - es[1];
+        } else {
+            s = s - Make<T>::c(p.eps_frozen[0] + p.eps_frozen[1]);
+        }
+        return s;
+    }
+    return Make<T>::c(ph == 2 ? p.eps_sep : 1.0);
+}
+
+// g = max(eps_L,0)^{3/2} exp(-7.76e-4 c_S): Bruggeman (Eq. 18 final) x Stokes-Einstein (Eqs. 2-3)
+template <class Chem, class T>
+__device__ __forceinline__ T transport_factor(const DevParams& p, T epsL, const T* c) {
+    T cS = Make<T>::c(0.0);
+#pragma unroll
+    for (int m = 0; m < Chem::NL; ++m)
+        if (p.wS[m] != 0.0) cS = cS + c[m] * (typename Base<T>::type)(p.wS[m]);
+    return pow15(epsL) * sexp(cS * (typename Base<T>::type)(-p.visc));
+}
+
+// Specific surface a_V, Eq. 18 with the Eq. 57 localisation
+template <class T>
+__device__ __forceinline__ T specific_surface(const DevParams& p, T e8, T e2) {
+    typedef typename Base<T>::type S;
+    T t1 = pow15(e8 * S(1.0 / p.s8ref));
+    T t2 = pow15(e2 * S(1.0 / p.li2sref));
+    return pos(Make<T>::c(1.0) - t1 - t2) * S(p.aV0p);
+}
+
+// Reaction sources at a structure point (mol m^-3 s^-1 for species, A m^-3 for the charges):
+//   S_i = sum_C nu_ik eps_s(k) k_C,k r_k + a_V sum_E nu_ik k_E,k r_k      (Eqs. 5, 6, 16, 17)
+//   q_L = -F a_V sum_E k_E,k r_k,  q_S = +F a_V sum_E k_E,k r_k           (Tab. 4 rows 2 and 4)
+// with r_C = <a>_r sqrt(K) - <a>_p / sqrt(K) and r_E = <a>_r e^{-x} - <a>_p e^{x},
+// x = F (Phi^S - Phi^L - U0)/(2RT): the Butler-Volmer forms of Eqs. 19-24 at alpha = 1/2.
+template <class Chem, class T>
+__device__ __forceinline__ void sources(const DevParams& p, const T* c, const T* es, T phiL, T phiS,
+                                        double tH, T* S, T* Ss, T& qL, T& qS) {
+    typedef typename Base<T>::type Sc;
+    const T zero = Make<T>::c(0.0);
+    T eta = (phiS - phiL) * Sc(p.F_2RT);
+    if constexpr (Chem::NS == 0) {
+        // three-species: E1 only, solids frozen
+        T aV = Make<T>::c(p.aV0p);
+        {
+            T e8 = Make<T>::c(p.eps_frozen[0]), e2 = Make<T>::c(p.eps_frozen[1]);
+            aV = specific_surface<T>(p, e8, e2);
+        }
+        T la1 = log_act(c[1], p.cref), la2 = log_act(c[2], p.cref);
+        T x1 = eta - Make<T>::c(p.F_2RT * p.U0[0]);
+        T r1 = sexp(la1 * Sc(0.5) - x1) - sexp(la2 * Sc(0.5) + x1);
+        T w1 = aV * r1 * Sc(p.kE[0]);
+        S[0] = zero;
+        S[1] = w1 * Sc(-0.5);
+        S[2] = w1 * Sc(0.5);
+        qS = w1 * Sc(p.F);
+        qL = -qS;
+        return;
+    } else {
+        T aV = specific_surface<T>(p, es[0], es[1]);
+        T la[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) la[m] = log_act(c[m], p.cref);
+        T x[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x[k] = eta - Make<T>::c(p.F_2RT * p.U0[k]);
+        const Sc th = Sc(p.smooth ? tH : 1.0);
+        // electrochemical rates, Tab. 3 rows E1..E6
+        T r1 = sexp(la[1] * Sc(0.5) - x[0]) - sexp(la[2] * Sc(0.5) + x[0]);
+        T r2 = sexp(la[2] * Sc(1.5) - x[1]) - sexp(la[3] * Sc(2.0) + x[1]);
+        T r3 = sexp(la[3] - x[2]) - sexp(la[4] * Sc(1.5) + x[2]);
+        T r4 = (sexp(la[4] * Sc(1.0 / 6.0) - x[3]) - sexp(la[5] * Sc(2.0 / 3.0) + x[3])) * th;
+        T r5 = sexp(la[2] * Sc(0.5) - x[4]) - sexp(la[4] + x[4]);
+        T r6 = sexp(la[4] * Sc(1.0 / 6.0) + la[0] * Sc(4.0 / 3.0) - x[5]) - sexp(x[5]);
+        // chemical rates C1, C2 (solid reactant, activity 1)
+        T a0 = pos(c[0]) * Sc(1.0 / p.cref), a1 = pos(c[1]) * Sc(1.0 / p.cref), a5 = pos(c[5]) * Sc(1.0 / p.cref);
+        T rc1 = Make<T>::c(p.sqK[0]) - a1 * Sc(1.0 / p.sqK[0]);
+        T rc2 = (Make<T>::c(p.sqK[1]) - a0 * a0 * a5 * Sc(1.0 / p.sqK[1])) * th;
+        T wc1 = es[0] * rc1 * Sc(p.kC[0]);
+        T wc2 = es[1] * rc2 * Sc(p.kC[1]);
+        T w1 = aV * r1 * Sc(p.kE[0]);
+        T w2 = aV * r2 * Sc(p.kE[1]);
+        T w3 = aV * r3 * Sc(p.kE[2]);
+        T w4 = aV * r4 * Sc(p.kE[3]);
+        T w5 = aV * r5 * Sc(p.kE[4]);
+        T w6 = aV * r6 * Sc(p.kE[5]);
+        S[0] = wc2 * Sc(2.0) - w6 * Sc(4.0 / 3.0);
+        S[1] = wc1 - w1 * Sc(0.5);
+        S[2] = w1 * Sc(0.5) - w2 * Sc(1.5) - w5 * Sc(0.5);
+        S[3] = w2 * Sc(2.0) - w3;
+        S[4] = w3 * Sc(1.5) - w4 * Sc(1.0 / 6.0) + w5 - w6 * Sc(1.0 / 6.0);
+        S[5] = wc2 + w4 * Sc(2.0 / 3.0);
+        Ss[0] = -wc1;
+        Ss[1] = w6 * Sc(2.0 / 3.0) - wc2;
+        qS = (w1 + w2 + w3 + w4 + w5 + w6) * Sc(p.F);
+        qL = -qS;
+    }
+}
+
+// Anode exchange r_A,Ano = a_Li e^{-x} - e^{x}, x = F (0 - Phi^L)/(2RT) (Eqs. 22-24, 26, 27)
+template <class T>
+__device__ __forceinline__ T anode_rate(const DevParams& p, T cLi, T phiL) {
+    typedef typename Base<T>::type Sc;
+    T x = phiL * Sc(-p.F_2RT);
+    return pos(cLi) * Sc(1.0 / p.cref) * sexp(-x) - sexp(x);
+}
+
+}  // namespace dgls

@@ -1,0 +1,78 @@
+// Internal interfaces between the C-ABI layer (api.cu) and the kernel translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace dgls {
+
+// Device geometry shared by all kernels.
+struct Geo {
+    const uint8_t* phase;      // [n_cell]
+    const int32_t* cmap;       // [n_cell] structure index or -1
+    const int32_t* sidx;       // [n_struct] structure index -> voxel
+};
+
+// Launch counter increment hook (owned by the context).
+struct LaunchCtx {
+    cudaStream_t st;
+    int64_t* counter;
+};
+
+// ------------------------------------------------------------------ DG0 (dg0.cu)
+// relax: 1 for the parabolic relaxation residual (Sec. 2.8); tH = T_H(t) for the smoothed
+// reactions and the ramped current; scale: multiply outputs by dt * rscale (Newton rows).
+cudaError_t dg0_residual(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
+                         const double* zn, double t, double dt, int relax, double* r, double* gbuf);
+template <class S>
+cudaError_t dg0_jvp(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v,
+                    double t, double dt, int relax, double out_scale_dt, S* out, S* gbuf, S* gbuf_d);
+cudaError_t dg0_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
+                       double t, double dt, int relax, double* blk, double* gbuf);
+
+// ------------------------------------------------------------------ DG1 (dg1.cu)
+cudaError_t dg1_residual(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
+                         const double* zn, double t, double dt, int relax, double* r, double* fbuf);
+template <class S>
+cudaError_t dg1_jvp(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v,
+                    double t, double dt, int relax, double out_scale_dt, S* out, S* fbuf, S* fbuf_d);
+cudaError_t dg1_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
+                       double t, double dt, int relax, double* blk, double* fbuf);
+int64_t dg1_face_buffer_len(const DevParams& p);
+
+// ------------------------------------------------------------------ linear algebra (la.cu)
+// Block-Jacobi: invert nblk blocks of nf x nf (row-major) in place; identity rows for absent
+// fields are set by the builders.  Returns the count of singular blocks in *bad (device).
+cudaError_t block_invert(const LaunchCtx& L, double* blk, int64_t nblk, int nf, float* blk32, int* bad);
+template <class S>
+cudaError_t block_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const void* blk,
+                        const S* v, S* out);
+template <class S>
+cudaError_t mdot(const LaunchCtx& L, const S* V, int64_t ld, int64_t n, int k, const S* w,
+                 double* partial, double* out);
+template <class S>
+cudaError_t maxpy(const LaunchCtx& L, S* w, const S* V, int64_t ld, int64_t n, int k, const double* h,
+                  double sign);
+template <class S>
+cudaError_t scale_copy(const LaunchCtx& L, S* dst, const S* src, int64_t n, const double* inv_norm_dev, double a);
+template <class S>
+cudaError_t neg_scaled(const LaunchCtx& L, const DevParams& p, const double* r, double dt, S* out);
+cudaError_t scaled_norm2(const LaunchCtx& L, const DevParams& p, const double* r, double dt,
+                         double* partial, double* out);
+cudaError_t axpby(const LaunchCtx& L, double* y, double a, const double* x, double b, int64_t n);
+cudaError_t to_f32(const LaunchCtx& L, float* dst, const double* src, int64_t n);
+cudaError_t to_f64_add(const LaunchCtx& L, double* dst, const float* src, double a, int64_t n);
+cudaError_t row_scales(const LaunchCtx& L, const DevParams& p, double dt, double* s);
+cudaError_t fill_equilibrium(const LaunchCtx& L, const DevParams& p, const double* vals, double* z);
+cudaError_t reduce_sum(const LaunchCtx& L, const double* x, int64_t n, double* partial, double* out);
+cudaError_t cell_voltage(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
+                         double* partial, double* out);
+cudaError_t ledger(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
+                   double* partial, double* out5);
+
+constexpr int RED_BLOCKS = 1216;   // 8 x 152 SMs: fixed grid so that reductions are deterministic
+constexpr int RED_THREADS = 256;
+constexpr int MAXK = 32;           // GMRES restart + 1 upper bound for the fused dot kernels
+
+}  // namespace dgls

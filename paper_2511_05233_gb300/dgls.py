@@ -1,0 +1,263 @@
+"""ctypes binding of libdgls.so (include/dgls.h): argument marshalling only.
+
+Device buffers are torch CUDA tensors (float64, contiguous); every compute step runs in the
+library's CUDA kernels.  There is no CPU fallback: ``lib()`` raises if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOCONV, ERR_NONFINITE, ERR_TIMEOUT, ERR_ABORTED = 0, -1, -2, -3, -4, -5, -6, -7
+STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_OOM", -3: "DG_ERR_CUDA", -4: "DG_ERR_NOCONV",
+          -5: "DG_ERR_NONFINITE", -6: "DG_ERR_TIMEOUT", -7: "DG_ERR_ABORTED"}
+REDUCED3, TRADEOFF = 0, 1
+FP64, MIXED = 0, 1
+NAIVE, H211B, FIXED = 0, 1, 2
+
+
+class Structure(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("h", C.c_double),
+                ("phase", C.POINTER(C.c_uint8))]
+
+
+class Params(C.Structure):
+    _fields_ = [("order", C.c_int32), ("chemistry", C.c_int32), ("T", C.c_double), ("f_C", C.c_double),
+                ("j_el", C.c_double), ("eps_struct", C.c_double), ("penalty", C.c_double), ("smooth", C.c_int32),
+                ("precision", C.c_int32), ("gmres_restart", C.c_int32), ("gmres_max_it", C.c_int32),
+                ("newton_rtol", C.c_double), ("newton_max_it", C.c_int32), ("eta_max", C.c_double),
+                ("eta_min", C.c_double), ("hbm_budget_bytes", C.c_int64)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("converged", C.c_int32), ("newton_iterations", C.c_int32), ("gmres_iterations", C.c_int32),
+                ("residual_evals", C.c_int32), ("jvp_evals", C.c_int32), ("norm0", C.c_double), ("norm", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DischargeOpts(C.Structure):
+    _fields_ = [("controller", C.c_int32), ("t0", C.c_double), ("dt0", C.c_double), ("dt_min", C.c_double),
+                ("dt_max", C.c_double), ("tol", C.c_double), ("cutoff_V", C.c_double), ("t_end", C.c_double),
+                ("max_steps", C.c_int32), ("max_halvings", C.c_int32), ("replay_dt", C.POINTER(C.c_double)),
+                ("n_replay", C.c_int32)]
+
+
+class Curve(C.Structure):
+    _fields_ = [("n_max", C.c_int32), ("n", C.c_int32), ("t", C.POINTER(C.c_double)), ("dt", C.POINTER(C.c_double)),
+                ("U_cell", C.POINTER(C.c_double)), ("c_m", C.POINTER(C.c_double)),
+                ("newton_its", C.POINTER(C.c_int32)), ("gmres_its", C.POINTER(C.c_int32)),
+                ("status", C.c_int32), ("attempts", C.c_int32), ("failures", C.c_int32)]
+
+
+_LIB = None
+_P = C.c_void_p
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libdgls.so (raises if it has not been built: there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} not built; run paper_2511_05233_gb300.build.build()")
+        L = C.CDLL(path)
+        sig = {
+            "dg_params_default": (C.c_int, [C.POINTER(Params), C.c_int32, C.c_int32]),
+            "dg_setup": (C.c_int, [C.POINTER(Structure), C.POINTER(Params), _P, C.POINTER(_P)]),
+            "dg_destroy": (C.c_int, [_P]),
+            "dg_last_error": (C.c_char_p, [_P]),
+            "dg_layout": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64)]),
+            "dg_equilibrium_state": (C.c_int, [_P, _P]),
+            "dg_relax": (C.c_int, [_P, _P, C.c_double, C.c_int32]),
+            "dg_residual": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P]),
+            "dg_jvp": (C.c_int, [_P, _P, C.c_double, C.c_double, _P, _P]),
+            "dg_block_jacobi": (C.c_int, [_P, _P, C.c_double, C.c_double, _P, _P]),
+            "dg_row_scales": (C.c_int, [_P, C.c_double, _P]),
+            "dg_step": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.POINTER(StepInfo)]),
+            "dg_step_host": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.POINTER(StepInfo)]),
+            "dg_cell_voltage": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
+            "dg_ledger": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
+            "dg_discharge": (C.c_int, [_P, _P, C.POINTER(DischargeOpts), C.POINTER(Curve)]),
+            "dg_launch_count": (C.c_int64, [_P]),
+            "dg_workspace_bytes": (C.c_int64, [_P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def default_params(chemistry=TRADEOFF, order=0, **kw):
+    p = Params()
+    st = lib().dg_params_default(C.byref(p), chemistry, order)
+    if st != OK:
+        raise DGError(st, "dg_params_default")
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    """Device pointer of a contiguous float64 torch CUDA tensor."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One discretised cell (structure + parameters) with its device workspaces."""
+
+    def __init__(self, phase, h, params, stream=None):
+        import torch
+
+        self._lib = lib()
+        ph = np.ascontiguousarray(phase, dtype=np.uint8)
+        if ph.ndim != 3:
+            raise ValueError("phase must be (nz, ny, nx)")
+        nz, ny, nx = ph.shape
+        self._phase = ph
+        s = Structure(nx, ny, nz, float(h), ph.ctypes.data_as(C.POINTER(C.c_uint8)))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h_ = C.c_void_p()
+        st = self._lib.dg_setup(C.byref(s), C.byref(params), C.c_void_p(stream.cuda_stream), C.byref(h_))
+        if st != OK:
+            raise DGError(st, "dg_setup (no structure voxel at x = 0, bad arguments or out of memory)")
+        self._h = h_
+        self.params = params
+        n = C.c_int64()
+        nf = C.c_int32()
+        off = (C.c_int64 * 10)()
+        ln = (C.c_int64 * 10)()
+        self._check(self._lib.dg_layout(self._h, C.byref(n), C.byref(nf), off, ln))
+        self.n_dof = n.value
+        self.n_fields = nf.value
+        self.offsets = list(off)[: nf.value]
+        self.lengths = list(ln)[: nf.value]
+
+    def _check(self, st):
+        if st != OK:
+            raise DGError(st, self._lib.dg_last_error(self._h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- device-buffer calls
+    def new_state(self):
+        import torch
+
+        return torch.empty(self.n_dof, dtype=torch.float64, device="cuda")
+
+    def equilibrium_state(self, z):
+        self._check(self._lib.dg_equilibrium_state(self._h, _ptr(z)))
+        return z
+
+    def relax(self, z, dt=0.1, n_steps=40):
+        self._check(self._lib.dg_relax(self._h, _ptr(z), dt, n_steps))
+        return z
+
+    def residual(self, z, zold, t, dt, out):
+        self._check(self._lib.dg_residual(self._h, _ptr(z), _ptr(zold), t, dt, _ptr(out)))
+        return out
+
+    def jvp(self, z, t, dt, v, out):
+        self._check(self._lib.dg_jvp(self._h, _ptr(z), t, dt, _ptr(v), _ptr(out)))
+        return out
+
+    def block_jacobi(self, z, t, dt, v, out):
+        self._check(self._lib.dg_block_jacobi(self._h, _ptr(z), t, dt, _ptr(v), _ptr(out)))
+        return out
+
+    def row_scales(self, dt, out):
+        self._check(self._lib.dg_row_scales(self._h, dt, _ptr(out)))
+        return out
+
+    def step(self, zn, z, t, dt, check=True):
+        info = StepInfo()
+        st = self._lib.dg_step(self._h, _ptr(zn), _ptr(z), t, dt, C.byref(info))
+        if check and st != OK:
+            self._check(st)
+        return st, info
+
+    def step_host(self, zn_host, z_host, t, dt, check=True):
+        zn_host = np.ascontiguousarray(zn_host, dtype=np.float64)
+        if z_host.dtype != np.float64 or not z_host.flags.c_contiguous:
+            raise TypeError("z_host must be a contiguous float64 array")
+        info = StepInfo()
+        st = self._lib.dg_step_host(self._h, zn_host.ctypes.data_as(C.c_void_p), z_host.ctypes.data_as(C.c_void_p),
+                                    t, dt, C.byref(info))
+        if check and st != OK:
+            self._check(st)
+        return st, info
+
+    def cell_voltage(self, z):
+        u = C.c_double()
+        self._check(self._lib.dg_cell_voltage(self._h, _ptr(z), C.byref(u)))
+        return u.value
+
+    def ledger(self, z):
+        out = (C.c_double * 5)()
+        self._check(self._lib.dg_ledger(self._h, _ptr(z), out))
+        return list(out)
+
+    def discharge(self, z, controller=NAIVE, dt0=1e-3, dt_min=1e-6, dt_max=10.0, tol=1e-5, cutoff_V=1.9,
+                  t_end=0.0, max_steps=100000, max_halvings=30, replay_dt=None, t0=0.0):
+        n_max = max_steps if replay_dt is None else len(replay_dt)
+        arr = {k: np.zeros(n_max) for k in ("t", "dt", "U_cell", "c_m")}
+        nit = np.zeros(n_max, dtype=np.int32)
+        git = np.zeros(n_max, dtype=np.int32)
+        rp = None
+        if replay_dt is not None:
+            rp = np.ascontiguousarray(replay_dt, dtype=np.float64)
+        o = DischargeOpts(controller, t0, dt0, dt_min, dt_max, tol, cutoff_V, t_end, max_steps, max_halvings,
+                          rp.ctypes.data_as(C.POINTER(C.c_double)) if rp is not None else None,
+                          len(rp) if rp is not None else 0)
+        cv = Curve(n_max, 0, *[arr[k].ctypes.data_as(C.POINTER(C.c_double)) for k in ("t", "dt", "U_cell", "c_m")],
+                   nit.ctypes.data_as(C.POINTER(C.c_int32)), git.ctypes.data_as(C.POINTER(C.c_int32)), 0, 0, 0)
+        st = self._lib.dg_discharge(self._h, _ptr(z), C.byref(o), C.byref(cv))
+        n = cv.n
+        res = {k: v[:n].copy() for k, v in arr.items()}
+        res.update(newton_its=nit[:n].copy(), gmres_its=git[:n].copy(), status=STATUS.get(st, st),
+                   attempts=cv.attempts, failures=cv.failures)
+        if st not in (OK, ERR_ABORTED, ERR_NOCONV):
+            self._check(st)
+        return res
+
+    def launch_count(self):
+        return int(self._lib.dg_launch_count(self._h))
+
+    def workspace_bytes(self):
+        return int(self._lib.dg_workspace_bytes(self._h))

@@ -1,0 +1,45 @@
+"""The C-ABI library builds, loads and exports every function that include/dgls.h declares
+(no compute calls: these run without a GPU)."""
+import os
+import re
+
+import pytest
+
+from paper_2511_05233_gb300 import build, dgls
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "dgls.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(build.LIB):
+        build.build()
+    return dgls.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("dg_setup", "dg_residual", "dg_jvp", "dg_step", "dg_discharge"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_params_default_and_argument_checks(lib):
+    p = dgls.default_params(dgls.TRADEOFF, 1)
+    assert p.order == 1 and p.chemistry == 1 and p.gmres_restart == 30 and p.newton_rtol == 1e-10
+    assert abs(p.T - 298.15) < 1e-12
+    import ctypes as C
+    bad = dgls.Params()
+    assert lib.dg_params_default(C.byref(bad), 7, 0) == dgls.ERR_ARG
+    h = C.c_void_p()
+    assert lib.dg_setup(None, C.byref(p), None, C.byref(h)) == dgls.ERR_ARG
