@@ -70,11 +70,15 @@ typedef struct {
                                   inside the FP64 Newton iteration */
     int32_t gmres_restart;     /* Krylov subspace size m (30) */
     int32_t gmres_max_it;      /* total GMRES iterations per linear solve */
-    double newton_rtol;        /* ||S R|| <= rtol ||S R(z^n)|| (1e-10) */
+    double newton_rtol;        /* converged when ||S R|| <= max(rtol ||S R(z^n)||, atol sqrt(n_dof)) */
+    double newton_atol;        /* RMS floor of the scaled residual (1e-13, rounding level) */
     int32_t newton_max_it;     /* 25 */
     double eta_max;            /* Eisenstat-Walker forcing-term cap (1e-2) */
     double eta_min;            /* forcing-term floor */
     int64_t hbm_budget_bytes;  /* workspace cap checked in dg_setup (0: no cap) */
+    int32_t preconditioner;    /* 0: cell-block Jacobi; 1: two-stage (CPR): multigrid on the potential
+                                  block, then block Jacobi on the remainder (default) */
+    int32_t mg_cycles;         /* V-cycles of the potential multigrid per application (1) */
 } dg_params;
 
 typedef struct {
@@ -180,6 +184,13 @@ dg_status dg_ledger(dg_ctx* ctx, const double* z_dev, double out[5]);
 /* Galvanostatic discharge from z_dev (in place) under the chosen controller until the
  * cut-off voltage, t_end or max_steps; one curve point per accepted step.  Synchronous. */
 dg_status dg_discharge(dg_ctx* ctx, double* z_dev, const dg_discharge_opts* opts, dg_curve* out);
+
+/* Kernel timing by category, recorded with CUDA events on the context stream while enabled:
+ * 0 residual, 1 Jacobian-vector product, 2 preconditioner build, 3 preconditioner apply,
+ * 4 Krylov orthogonalisation and updates.  dg_profile(ctx, 1) clears and enables, 0 disables;
+ * dg_profile_read fills ms[5] (summed device milliseconds) and launches[5] (calls). */
+dg_status dg_profile(dg_ctx* ctx, int32_t enable);
+dg_status dg_profile_read(const dg_ctx* ctx, double ms[5], int64_t calls[5]);
 
 /* Number of CUDA kernels this context has launched (monotone counter). */
 int64_t dg_launch_count(const dg_ctx* ctx);

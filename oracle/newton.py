@@ -8,7 +8,8 @@ subtractive cancellation, for any residual written with complex-analytic operati
 
 Newton (the role of PETSc ``newtonls`` in Sec. 2.7): exact linear solves with SuperLU,
 backtracking line search on the scaled residual norm ||S R||_2 (Armijo 1e-4, step
-halving, at most 10 cuts), convergence when ||S R||_2 <= rtol ||S R(z^n)||_2,
+halving, at most 10 cuts), convergence when ||S R||_2 <= max(rtol ||S R(z^n)||_2, atol sqrt(N))
+(atol = 1e-13: an RMS scaled residual at the rounding level, for steps that start almost converged),
 failure on the iteration limit, a failed line search or non-finite values.
 Row scales S: Delta t / (M c_ref) for species and solid rows, Delta t / (M F c_ref)
 for the two charge rows, M the cell (DG0) or node (DG1) volume.
@@ -113,7 +114,7 @@ class NewtonInfo:
     reason: str = ""
 
 
-def newton(model, grid, zn, t, dt, z0=None, rtol=1e-10, max_it=25, relax=False, max_cuts=10):
+def newton(model, grid, zn, t, dt, z0=None, rtol=1e-10, max_it=25, relax=False, max_cuts=10, atol=1e-13):
     """Solve R(z; z^n, t, dt) = 0 for z = z^{n+1} starting from z0 (default z^n)."""
     S = row_scales(model, grid, dt)
     z = (zn if z0 is None else z0).astype(float).copy()
@@ -123,8 +124,9 @@ def newton(model, grid, zn, t, dt, z0=None, rtol=1e-10, max_it=25, relax=False, 
     if not np.isfinite(nrm):
         return z, NewtonInfo(False, 0, n0, nrm, "nonfinite")
     it = 0
+    floor = atol * np.sqrt(z.size)
     while True:
-        if nrm <= rtol * n0 or nrm == 0.0:
+        if nrm <= max(rtol * n0, floor) or nrm == 0.0:
             return z, NewtonInfo(True, it, n0, nrm)
         if it >= max_it:
             return z, NewtonInfo(False, it, n0, nrm, "max_it")

@@ -44,6 +44,9 @@ struct dg_ctx {
     void* w = nullptr;
     void* u = nullptr;
     void* x = nullptr;             // Krylov combination sum y_k V_k
+    void* y1 = nullptr;            // CPR: potential correction
+    void* t2 = nullptr;            // CPR: remaining residual
+    std::vector<MGLevel> mg;
     float* z32 = nullptr;
     // discharge work states
     double *za = nullptr, *zb = nullptr, *zC = nullptr, *zF = nullptr;
@@ -54,7 +57,52 @@ struct dg_ctx {
     double* d_vals = nullptr;      // equilibrium field values
     // statistics of the last step
     int gmres_its = 0, res_evals = 0, jvp_evals = 0;
+    // optional per-category kernel timing (CUDA events on the context stream)
+    bool prof = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[5] = {0, 0, 0, 0, 0};
+    int64_t prof_calls[5] = {0, 0, 0, 0, 0};
 };
+
+namespace {
+struct ProfScope {
+    dg_ctx* c;
+    int cat;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(dg_ctx* ctx, int category) : c(ctx), cat(category) {
+        if (!c->prof) return;
+        a = take();
+        b = take();
+        if (a && b) cudaEventRecord(a, c->L.st);
+    }
+    cudaEvent_t take() {
+        if (!c->ev_pool.empty()) { cudaEvent_t e = c->ev_pool.back(); c->ev_pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    ~ProfScope() {
+        if (!c->prof || !a || !b) return;
+        cudaEventRecord(b, c->L.st);
+        c->ev.push_back({cat, {a, b}});
+    }
+};
+
+// Resolve recorded event pairs (the stream must have been synchronised).
+void prof_flush(dg_ctx* c) {
+    for (auto& e : c->ev) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.second.first, e.second.second) == cudaSuccess) {
+            c->prof_ms[e.first] += ms;
+            c->prof_calls[e.first] += 1;
+        }
+        c->ev_pool.push_back(e.second.first);
+        c->ev_pool.push_back(e.second.second);
+    }
+    c->ev.clear();
+}
+}  // namespace
 
 static dg_status fail(dg_ctx* c, dg_status s, const std::string& m) {
     if (c) c->err = m;
@@ -119,6 +167,9 @@ extern "C" dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t 
     p->gmres_restart = 30;
     p->gmres_max_it = 600;
     p->newton_rtol = 1e-10;
+    p->newton_atol = 1e-13;
+    p->preconditioner = 1;
+    p->mg_cycles = 1;
     p->newton_max_it = 25;
     p->eta_max = 1e-2;
     p->eta_min = 1e-12;
@@ -140,6 +191,10 @@ static cudaError_t dalloc(dg_ctx* ctx, T** ptr, int64_t n) {
 }
 
 static void free_all(dg_ctx* ctx) {
+    for (auto& e : ctx->ev) { ctx->ev_pool.push_back(e.second.first); ctx->ev_pool.push_back(e.second.second); }
+    ctx->ev.clear();
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    ctx->ev_pool.clear();
     for (void* q : ctx->allocs) cudaFree(q);
     ctx->allocs.clear();
     if (ctx->hres) cudaFreeHost(ctx->hres);
@@ -305,17 +360,22 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     AL(ctx->dres, 256);
     AL(ctx->d_vals, DG_MAXF);
     if (mixed) {
-        float *V, *w, *u, *x;
-        AL(V, (int64_t)(m + 1) * N); AL(w, N); AL(u, N); AL(x, N);
-        ctx->V = V; ctx->w = w; ctx->u = u; ctx->x = x;
+        float *V, *w, *u, *x, *y1, *t2;
+        AL(V, (int64_t)(m + 1) * N); AL(w, N); AL(u, N); AL(x, N); AL(y1, N); AL(t2, N);
+        ctx->V = V; ctx->w = w; ctx->u = u; ctx->x = x; ctx->y1 = y1; ctx->t2 = t2;
         AL(ctx->z32, N);
         AL(ctx->gb32, scratch);
         AL(ctx->gbd32, scratch);
         AL(ctx->blk32, ctx->nblk * P.nf * P.nf);
     } else {
-        double *V, *w, *u, *x;
-        AL(V, (int64_t)(m + 1) * N); AL(w, N); AL(u, N); AL(x, N);
-        ctx->V = V; ctx->w = w; ctx->u = u; ctx->x = x;
+        double *V, *w, *u, *x, *y1, *t2;
+        AL(V, (int64_t)(m + 1) * N); AL(w, N); AL(u, N); AL(x, N); AL(y1, N); AL(t2, N);
+        ctx->V = V; ctx->w = w; ctx->u = u; ctx->x = x; ctx->y1 = y1; ctx->t2 = t2;
+    }
+    if (prm->preconditioner == 1 && mg_levels_alloc(ctx->mg, nx, ny, nz, ctx->allocs, &ctx->ws_bytes) != cudaSuccess) {
+        free_all(ctx);
+        delete ctx;
+        return DG_ERR_OOM;
     }
 #undef AL
     if (cudaMallocHost(&ctx->hres, 256 * sizeof(double)) != cudaSuccess) {
@@ -367,6 +427,7 @@ extern "C" dg_status dg_layout(const dg_ctx* ctx, int64_t* n_dof, int32_t* n_fie
 
 // ------------------------------------------------------------------ model calls
 static dg_status residual_(dg_ctx* ctx, const double* z, const double* zn, double t, double dt, int relax, double* r) {
+    ProfScope ps(ctx, 0);
     cudaError_t e = ctx->P.order == 0 ? dg0_residual(ctx->L, ctx->P, ctx->G, z, zn, t, dt, relax, r, ctx->gb)
                                       : dg1_residual(ctx->L, ctx->P, ctx->G, z, zn, t, dt, relax, r, ctx->gb);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("residual: ") + cudaGetErrorString(e));
@@ -377,6 +438,7 @@ static dg_status residual_(dg_ctx* ctx, const double* z, const double* zn, doubl
 template <class S>
 static dg_status jvp_(dg_ctx* ctx, const S* z, const S* v, double t, double dt, int relax, double sc_dt, S* out,
                       S* gb, S* gbd) {
+    ProfScope ps(ctx, 1);
     cudaError_t e = ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd)
                                       : dg1_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("jvp: ") + cudaGetErrorString(e));
@@ -385,18 +447,63 @@ static dg_status jvp_(dg_ctx* ctx, const S* z, const S* v, double t, double dt, 
 }
 
 static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt, int relax) {
+    ProfScope ps(ctx, 2);
     cudaError_t e = ctx->P.order == 0 ? dg0_blocks(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb)
                                       : dg1_blocks(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("blocks: ") + cudaGetErrorString(e));
     e = cudaMemsetAsync(ctx->d_bad, 0, sizeof(int), ctx->L.st);
     if (e == cudaSuccess) e = block_invert(ctx->L, ctx->blk, ctx->nblk, ctx->P.nf, ctx->blk32, ctx->d_bad);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
+    if (ctx->prm.preconditioner == 1) {
+        e = mg_setup(ctx->L, ctx->P, ctx->G, z, ctx->gb, t, dt, relax, ctx->mg);
+        if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("multigrid setup: ") + cudaGetErrorString(e));
+    }
+    return DG_OK;
+}
+
+// u = M^{-1} v: block Jacobi, or the two-stage CPR preconditioner
+//   y1 = P MG(R v);  u = B^{-1} (v - S J y1) + y1
+template <class S>
+static dg_status precond_apply_(dg_ctx* ctx, const S* v, S* u, const S* zS, double t, double dt, int relax, S* gbS,
+                                S* gbdS, const void* blkS) {
+    ProfScope ps(ctx, 3);
+    const int64_t N = ctx->ndof;
+    if (ctx->prm.preconditioner != 1) {
+        CK(block_apply<S>(ctx->L, ctx->P, ctx->G, blkS, v, u));
+        return DG_OK;
+    }
+    S* y1 = (S*)ctx->y1;
+    S* t2 = (S*)ctx->t2;
+    CK(cpr_stage1<S>(ctx->L, ctx->P, ctx->G, ctx->mg, ctx->prm.mg_cycles, v, y1));
+    cudaError_t e = ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, zS, y1, t, dt, relax, dt, t2, gbS, gbdS)
+                                      : dg1_jvp<S>(ctx->L, ctx->P, ctx->G, zS, y1, t, dt, relax, dt, t2, gbS, gbdS);
+    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("jvp: ") + cudaGetErrorString(e));
+    ctx->jvp_evals++;
+    CK(saxpby<S>(ctx->L, t2, -1.0, v, 1.0, N));
+    CK(block_apply<S>(ctx->L, ctx->P, ctx->G, blkS, t2, u));
+    CK(saxpby<S>(ctx->L, u, 1.0, y1, 1.0, N));
     return DG_OK;
 }
 
 static dg_status sync_(dg_ctx* ctx) {
     cudaError_t e = cudaStreamSynchronize(ctx->L.st);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+    if (ctx->prof) prof_flush(ctx);
+    return DG_OK;
+}
+
+extern "C" dg_status dg_profile(dg_ctx* ctx, int32_t enable) {
+    if (!ctx) return DG_ERR_ARG;
+    dg_status s = sync_(ctx);
+    if (s != DG_OK) return s;
+    ctx->prof = enable != 0;
+    for (int k = 0; k < 5; ++k) { ctx->prof_ms[k] = 0.0; ctx->prof_calls[k] = 0; }
+    return DG_OK;
+}
+
+extern "C" dg_status dg_profile_read(const dg_ctx* ctx, double ms[5], int64_t calls[5]) {
+    if (!ctx || !ms || !calls) return DG_ERR_ARG;
+    for (int k = 0; k < 5; ++k) { ms[k] = ctx->prof_ms[k]; calls[k] = ctx->prof_calls[k]; }
     return DG_OK;
 }
 
@@ -513,15 +620,19 @@ static dg_status gmres_(dg_ctx* ctx, const double* z, double t, double dt, int r
         int j = 0;
         for (; j < m && total < max_it; ++j) {
             S* vj = V + (int64_t)j * N;
-            CK(block_apply<S>(L, ctx->P, ctx->G, blkS, vj, u));
+            s = precond_apply_<S>(ctx, vj, u, zS, t, dt, relax, gbS, gbdS, blkS);
+            if (s != DG_OK) return s;
             s = jvp_<S>(ctx, zS, u, t, dt, relax, dt, w, gbS, gbdS);
             if (s != DG_OK) return s;
-            CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres));
-            CK(maxpy<S>(L, w, V, N, N, j + 1, ctx->dres, -1.0));
-            CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres + 32));
-            CK(maxpy<S>(L, w, V, N, N, j + 1, ctx->dres + 32, -1.0));
-            CK(mdot<S>(L, w, N, N, 1, w, ctx->partial, ctx->dres + 64));
-            CK(scale_copy<S>(L, V + (int64_t)(j + 1) * N, w, N, ctx->dres + 64, 1.0));
+            {
+                ProfScope ps(ctx, 4);
+                CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres));
+                CK(maxpy<S>(L, w, V, N, N, j + 1, ctx->dres, -1.0));
+                CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres + 32));
+                CK(maxpy<S>(L, w, V, N, N, j + 1, ctx->dres + 32, -1.0));
+                CK(mdot<S>(L, w, N, N, 1, w, ctx->partial, ctx->dres + 64));
+                CK(scale_copy<S>(L, V + (int64_t)(j + 1) * N, w, N, ctx->dres + 64, 1.0));
+            }
             CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 65 * sizeof(double), cudaMemcpyDeviceToHost, L.st));
             s = sync_(ctx);
             if (s != DG_OK) return s;
@@ -555,7 +666,8 @@ static dg_status gmres_(dg_ctx* ctx, const double* z, double t, double dt, int r
         CK(cudaMemcpyAsync(ctx->dres + 100, ctx->hres + 100, j * sizeof(double), cudaMemcpyHostToDevice, L.st));
         CK(cudaMemsetAsync(x, 0, N * sizeof(S), L.st));
         CK(maxpy<S>(L, x, V, N, N, j, ctx->dres + 100, 1.0));
-        CK(block_apply<S>(L, ctx->P, ctx->G, blkS, x, u));
+        s = precond_apply_<S>(ctx, x, u, zS, t, dt, relax, gbS, gbdS, blkS);
+        if (s != DG_OK) return s;
         if (mixed) CK(to_f64_add(L, ctx->dz, (const float*)u, 1.0, N));
         else CK(axpby(L, ctx->dz, 1.0, (const double*)u, 1.0, N));
         // restore dres[100] = 1 for the restart residual update
@@ -588,8 +700,9 @@ static dg_status newton_(dg_ctx* ctx, const double* zn, double t1, double dt, in
     const bool mixed = ctx->prm.precision == DG_PREC_MIXED;
     int it = 0;
     dg_status result = DG_OK;
+    const double floor_ = ctx->prm.newton_atol * std::sqrt((double)N);
     for (;;) {
-        if (nrm <= ctx->prm.newton_rtol * n0 || nrm == 0.0) break;
+        if (nrm <= std::max(ctx->prm.newton_rtol * n0, floor_) || nrm == 0.0) break;
         if (it >= ctx->prm.newton_max_it) { result = fail(ctx, DG_ERR_NOCONV, "Newton: iteration limit"); break; }
         s = build_precond(ctx, ctx->zc, t1, dt, relax);
         if (s != DG_OK) return s;

@@ -1,16 +1,612 @@
-// DG1 kernels (placeholder until the Q1 interior-penalty kernels land).
+// DG1 (tensor-product Q1) residual, Jacobian-vector product and per-node diagonal blocks.
+//
+// Discretisation (Eqs. 43-47): Lagrange basis on the 2-point Gauss-Legendre nodes of each voxel,
+// the same points for volume quadrature (diagonal mass h^3/8 per node) and 2 x 2 Gauss points
+// per face lying on the nodal lines; interior faces carry
+//   -int {K}_H {d_n psi} [[v]] + penalty int {K}_H [[psi]].[[v]] / h
+// per (coefficient x gradient) term of Tab. 4, the coefficient taken from the traced fields on
+// each side.  Everything factorises along nodal lines: in direction d a voxel has 4 lines of
+// 2 nodes, each line meets one face point on either side, and the volume term of a line is
+// +-(3h/8)(K_0 + K_1)(psi_1 - psi_0).
+//
+// Kernels: (A) transport factors g at the 8 nodes and the 24 face points of every voxel (the
+// only exponentials of the transport part), (B1) one thread per (node, voxel) for storage and
+// reaction sources, (B2) one pass per direction with one thread per (line, voxel) adding the
+// volume and face terms of that line into its two nodes.  Each direction pass touches disjoint
+// node pairs, so the read-modify-write of B2 is race free without atomics.
 #include "internal.h"
+
 namespace dgls {
-cudaError_t dg1_residual(const LaunchCtx&, const DevParams&, const Geo&, const double*, const double*, double, double,
-                         int, double*, double*) { return cudaErrorNotSupported; }
+
+namespace {
+constexpr double SQ3 = 1.7320508075688772935;
+constexpr double ALPHA = 0.5 * (1.0 + SQ3);   // trace weight of the node next to the face
+constexpr double BETA = 0.5 * (1.0 - SQ3);    // trace weight of the far node
+constexpr int NG = 32;                         // g slots per voxel: 8 nodes + 6 faces x 4 points
+
+__device__ __forceinline__ void cell_ijk(const DevParams& p, int cell, int& i, int& j, int& k) {
+    i = cell % p.nx;
+    int r = cell / p.nx;
+    j = r % p.ny;
+    k = r / p.ny;
+}
+
+// node index from per-direction node coordinates
+__device__ __forceinline__ int node_of(int ax, int ay, int az) { return ax + 2 * ay + 4 * az; }
+
+// the two nodes of line q (0..3) in direction d: n0 has coordinate 0 along d, n1 has 1
+__device__ __forceinline__ void line_nodes(int d, int q, int& n0, int& n1) {
+    int u = q & 1, w = q >> 1;
+    if (d == 0) { n0 = node_of(0, u, w); n1 = node_of(1, u, w); }
+    else if (d == 1) { n0 = node_of(u, 0, w); n1 = node_of(u, 1, w); }
+    else { n0 = node_of(u, w, 0); n1 = node_of(u, w, 1); }
+}
+
+// g-slot of face (d, side) point q: 8 + (2d + (side > 0)) * 4 + q
+__device__ __forceinline__ int face_slot(int d, int side, int q) { return 8 + (2 * d + (side > 0 ? 1 : 0)) * 4 + q; }
+
 template <class S>
-cudaError_t dg1_jvp(const LaunchCtx&, const DevParams&, const Geo&, const S*, const S*, double, double, int, double, S*,
-                    S*, S*) { return cudaErrorNotSupported; }
+__device__ __forceinline__ S ld(const S* z, const DevParams& p, int f, int node, int idx) {
+    return z[p.off[f] + (int64_t)node * p.flen[f] + idx];
+}
+}  // namespace
+
+// ------------------------------------------------------------------ (A) transport factors
+template <class Chem, class S, bool TAN>
+__global__ void __launch_bounds__(128) k_dg1_g(const DevParams p, const Geo g, const S* __restrict__ z,
+                                               const S* __restrict__ v, S* __restrict__ gb, S* __restrict__ gbd) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    typedef typename std::conditional<TAN, Dual<S>, S>::type T;
+    constexpr int NL = Chem::NL, NS = Chem::NS;
+    const int ph = g.phase[cell];
+    const int s = g.cmap[cell];
+    // nodal concentrations and solid fractions
+    T c[8][NL], es[8][2];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+#pragma unroll
+        for (int m = 0; m < NL; ++m)
+            c[n][m] = Make<T>::var(ld(z, p, m, n, cell), TAN ? (double)ld(v, p, m, n, cell) : 0.0);
+        es[n][0] = es[n][1] = Make<T>::c(0.0);
+        if (NS == 2 && ph == 1) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                es[n][q] = Make<T>::var(ld(z, p, NL + q, n, s), TAN ? (double)ld(v, p, NL + q, n, s) : 0.0);
+        }
+        T eL = liquid_fraction<Chem, T>(p, ph, es[n]);
+        T gg = transport_factor<Chem, T>(p, eL, c[n]);
+        gb[(int64_t)n * p.n_cell + cell] = val(gg);
+        if constexpr (TAN) gbd[(int64_t)n * p.n_cell + cell] = gg.d;
+    }
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll 1
+        for (int side = -1; side <= 1; side += 2) {
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) {
+                int n0, n1;
+                line_nodes(d, q, n0, n1);
+                const typename Base<T>::type wn = side > 0 ? ALPHA : BETA, wf = side > 0 ? BETA : ALPHA;
+                T ct[NL], et[2];
+#pragma unroll
+                for (int m = 0; m < NL; ++m) ct[m] = c[n1][m] * wn + c[n0][m] * wf;
+                et[0] = es[n1][0] * wn + es[n0][0] * wf;
+                et[1] = es[n1][1] * wn + es[n0][1] * wf;
+                T eL = liquid_fraction<Chem, T>(p, ph, et);
+                T gg = transport_factor<Chem, T>(p, eL, ct);
+                int slot = face_slot(d, side, q);
+                gb[(int64_t)slot * p.n_cell + cell] = val(gg);
+                if constexpr (TAN) gbd[(int64_t)slot * p.n_cell + cell] = gg.d;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ (B1) nodes: storage + sources
+template <class Chem, class T>
+__device__ __forceinline__ void node_terms(const DevParams& p, int ph, const T* c, const T* es, T phiL, T phiS,
+                                           const double* old, double tH, double dt, int relax, T* R) {
+    typedef typename Base<T>::type Sc;
+    constexpr int NL = Chem::NL, NS = Chem::NS, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
+    const bool st = ph == 1;
+    const double M = p.V / 8.0;
+    const Sc Mdt = Sc(M / dt);
+#pragma unroll
+    for (int f = 0; f < Chem::NF; ++f) R[f] = Make<T>::c(0.0);
+    T epsL = liquid_fraction<Chem, T>(p, ph, es);
+    double esn[2] = {0.0, 0.0};
+    if (NS == 2) { esn[0] = old[NL]; esn[1] = old[NL + 1]; }
+    double epsLn = val(liquid_fraction<Chem, double>(p, ph, esn));
+#pragma unroll
+    for (int m = 0; m < NL; ++m) {
+        if (relax) R[m] = (c[m] - Make<T>::c(old[m])) * Mdt;
+        else R[m] = (epsL * c[m] - Make<T>::c(epsLn * old[m])) * Mdt;
+    }
+    if (st) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) R[NL + q] = (es[q] - Make<T>::c(old[NL + q])) * Sc(M * p.rhoM[q] / dt);
+    }
+    if (relax) {
+        R[PHIL] = (phiL - Make<T>::c(old[PHIL])) * Mdt;
+        if (st) R[PHIS] = (phiS - Make<T>::c(old[PHIS])) * Mdt;
+    }
+    if (st) {
+        T Sv[NL], Ss[2], qL, qS;
+        sources<Chem, T>(p, c, es, phiL, phiS, tH, Sv, Ss, qL, qS);
+        if (!relax) {
+#pragma unroll
+            for (int m = 0; m < NL; ++m) R[m] -= Sv[m] * Sc(M);
+#pragma unroll
+            for (int q = 0; q < NS; ++q) R[NL + q] -= Ss[q] * Sc(M);
+        }
+        R[PHIL] -= qL * Sc(M);
+        R[PHIS] -= qS * Sc(M);
+    }
+}
+
+template <class Chem, class S, int MODE>   // MODE 0: residual (S = double), 1: JVP tangent
+__global__ void __launch_bounds__(128) k_dg1_nodes(const DevParams p, const Geo g, const S* __restrict__ z,
+                                                   const S* __restrict__ v, const double* __restrict__ zn,
+                                                   double t, double dt, int relax, double sc_dt, S* __restrict__ r) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 8) return;
+    typedef typename std::conditional<MODE == 1, Dual<S>, S>::type T;
+    constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
+    const int n = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)n * p.n_cell);
+    const int ph = g.phase[cell];
+    const int s = g.cmap[cell];
+    const bool st = ph == 1;
+    T c[NL], es[2], phiL, phiS;
+#pragma unroll
+    for (int m = 0; m < NL; ++m) c[m] = Make<T>::var(ld(z, p, m, n, cell), MODE == 1 ? (double)ld(v, p, m, n, cell) : 0.0);
+    es[0] = es[1] = Make<T>::c(0.0);
+    phiS = Make<T>::c(0.0);
+    phiL = Make<T>::var(ld(z, p, PHIL, n, cell), MODE == 1 ? (double)ld(v, p, PHIL, n, cell) : 0.0);
+    if (st) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) es[q] = Make<T>::var(ld(z, p, NL + q, n, s), MODE == 1 ? (double)ld(v, p, NL + q, n, s) : 0.0);
+        phiS = Make<T>::var(ld(z, p, PHIS, n, s), MODE == 1 ? (double)ld(v, p, PHIS, n, s) : 0.0);
+    }
+    double old[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        old[f] = 0.0;
+        if (MODE == 0) {
+            if (!p.is_struct[f]) old[f] = zn[p.off[f] + (int64_t)n * p.flen[f] + cell];
+            else if (st) old[f] = zn[p.off[f] + (int64_t)n * p.flen[f] + s];
+        }
+    }
+    T R[NF];
+    node_terms<Chem, T>(p, ph, c, es, phiL, phiS, old, smooth_step(t), dt, relax, R);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        if (p.is_struct[f] && !st) continue;
+        int64_t o = p.off[f] + (int64_t)n * p.flen[f] + (p.is_struct[f] ? s : cell);
+        if constexpr (MODE == 1) {
+            S val_ = R[f].d;
+            if (sc_dt > 0.0) val_ = val_ * S(sc_dt * p.rscale[f]);
+            r[o] = val_;
+        } else {
+            r[o] = R[f];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ (B2) lines: volume + faces
+// Values of one nodal line of a voxel: the fields that carry fluxes (liquid species, Phi^L, Phi^S).
+template <class Chem, class T>
+struct Line {
+    T c[2][Chem::NL];
+    T phiL[2], phiS[2];
+};
+
+template <class Chem, class T, class S>
+__device__ __forceinline__ void load_line(const DevParams& p, const S* z, const S* v, bool tan, int cell, int sidx,
+                                          bool st, int n0, int n1, int seed_node, int seed_f, Line<Chem, T>& L) {
+    const int nodes[2] = {n0, n1};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int n = nodes[a];
+#pragma unroll
+        for (int m = 0; m < Chem::NL; ++m) {
+            double d = tan ? (double)ld(v, p, m, n, cell) : ((n == seed_node && m == seed_f) ? 1.0 : 0.0);
+            L.c[a][m] = Make<T>::var(ld(z, p, m, n, cell), d);
+        }
+        {
+            double d = tan ? (double)ld(v, p, Chem::PHIL, n, cell) : ((n == seed_node && Chem::PHIL == seed_f) ? 1.0 : 0.0);
+            L.phiL[a] = Make<T>::var(ld(z, p, Chem::PHIL, n, cell), d);
+        }
+        if (st) {
+            double d = tan ? (double)ld(v, p, Chem::PHIS, n, sidx) : ((n == seed_node && Chem::PHIS == seed_f) ? 1.0 : 0.0);
+            L.phiS[a] = Make<T>::var(ld(z, p, Chem::PHIS, n, sidx), d);
+        } else {
+            L.phiS[a] = Make<T>::c(0.0);
+        }
+    }
+}
+
+// Contributions of one line to its two nodes: acc[0][e] -> node n0, acc[1][e] -> node n1 for the
+// transport equations e = 0..NL-1 (species), NL (Phi^L), NL+1 (Phi^S).
+//   gN[2]: g at the two nodes; gP[2]: own face g at the -/+ face points; gQ[2]: neighbour face g
+//   on the other side of the -/+ face; Qm/Qp: neighbour lines (valid flags hasQ).
+template <class Chem, class T>
+__device__ __forceinline__ void line_terms(const DevParams& p, const Line<Chem, T>& P, const T* gN, const T* gP,
+                                           bool stP, const Line<Chem, T>* Q, const T* gQ, const bool* hasQ,
+                                           const bool* stQ, int relax, T acc[2][Chem::NL + 2]) {
+    typedef typename Base<T>::type Sc;
+    constexpr int NL = Chem::NL;
+    const Sc h = Sc(p.h);
+    const Sc vol = Sc(3.0 * p.h / 8.0);
+    const Sc wf = Sc(0.25 * p.h * p.h);
+    const Sc gq = Sc(SQ3 / p.h);
+    const Sc pen = Sc(p.penalty / p.h);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int e = 0; e < NL + 2; ++e) acc[a][e] = Make<T>::c(0.0);
+
+    // ---- volume term of the line
+    {
+        T gsum = gN[0] + gN[1];
+        T dPhi = P.phiL[1] - P.phiL[0];
+        T accL = Make<T>::c(0.0);
+#pragma unroll
+        for (int m = 0; m < NL; ++m) {
+            T dc = P.c[1][m] - P.c[0][m];
+            T fl = Make<T>::c(0.0);
+            if (!relax) fl = gsum * dc * Sc(p.D0[m]);
+            if (p.zc[m] != 0.0) {
+                T msum = gN[0] * P.c[0][m] + gN[1] * P.c[1][m];
+                if (!relax) fl += msum * dPhi * Sc(p.kappa_m[m]);
+                accL += gsum * dc * Sc(p.Kd[m]) + msum * dPhi * Sc(p.Km[m]);
+            }
+            fl = fl * vol;
+            acc[1][m] += fl;
+            acc[0][m] -= fl;
+        }
+        accL = accL * vol;
+        acc[1][NL] += accL;
+        acc[0][NL] -= accL;
+        if (stP) {
+            T fs = (P.phiS[1] - P.phiS[0]) * Sc(2.0 * p.kappa_s) * vol;
+            acc[1][NL + 1] += fs;
+            acc[0][NL + 1] -= fs;
+        }
+    }
+    // ---- faces: side 0 is the xi = -1 face (neighbour on the left), side 1 the xi = +1 face
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        if (!hasQ[sd]) continue;
+        const Line<Chem, T>& N = Q[sd];
+        // own trace at this face and the neighbour's trace at its opposite face
+        const Sc wn = Sc(ALPHA), wfar = Sc(BETA);
+        const int near = sd, far = 1 - sd;          // own near node index on this side
+        // left cell / right cell roles: for sd = 1 P is left (minus), for sd = 0 P is right (plus)
+        T gl = sd == 1 ? gP[1] : gQ[0];
+        T gr = sd == 1 ? gQ[1] : gP[0];
+        // traces: P at its face, N at its opposite face (near node of N is index 1 - sd)
+        T Hg = harm(gl, gr);
+        // potentials
+        T tPL = P.phiL[near] * wn + P.phiL[far] * wfar;
+        T tNL = N.phiL[far] * wn + N.phiL[near] * wfar;
+        T grPL = (P.phiL[1] - P.phiL[0]) * gq;
+        T grNL = (N.phiL[1] - N.phiL[0]) * gq;
+        // jump oriented left minus right, mean normal gradient
+        T jL = sd == 1 ? tPL - tNL : tNL - tPL;
+        T mL = (grPL + grNL) * Sc(0.5);
+        T fl[NL + 2];
+#pragma unroll
+        for (int e = 0; e < NL + 2; ++e) fl[e] = Make<T>::c(0.0);
+        T accL = Make<T>::c(0.0);
+#pragma unroll
+        for (int m = 0; m < NL; ++m) {
+            T tPc = P.c[near][m] * wn + P.c[far][m] * wfar;
+            T tNc = N.c[far][m] * wn + N.c[near][m] * wfar;
+            T jc = sd == 1 ? tPc - tNc : tNc - tPc;
+            T mc = (P.c[1][m] - P.c[0][m] + N.c[1][m] - N.c[0][m]) * (gq * Sc(0.5));
+            // flux of the (left -> right) face written as -{K}_H {d_n psi} + pen {K}_H [[psi]]
+            T dterm = (jc * pen - mc) * Hg;
+            T f = Make<T>::c(0.0);
+            if (!relax) f = dterm * Sc(p.D0[m]);
+            if (p.zc[m] != 0.0) {
+                T cl = sd == 1 ? tPc : tNc;
+                T cr = sd == 1 ? tNc : tPc;
+                T Hm = harm(gl * cl, gr * cr);
+                T mterm = (jL * pen - mL) * Hm;
+                if (!relax) f += mterm * Sc(p.kappa_m[m]);
+                accL += dterm * Sc(p.Kd[m]) + mterm * Sc(p.Km[m]);
+            }
+            fl[m] = f;
+        }
+        fl[NL] = accL;
+        if (stP && stQ[sd]) {
+            T tPS = P.phiS[near] * wn + P.phiS[far] * wfar;
+            T tNS = N.phiS[far] * wn + N.phiS[near] * wfar;
+            T jS = sd == 1 ? tPS - tNS : tNS - tPS;
+            T mS = (P.phiS[1] - P.phiS[0] + N.phiS[1] - N.phiS[0]) * (gq * Sc(0.5));
+            fl[NL + 1] = (jS * pen - mS) * Sc(p.kappa_s);
+        }
+        // left cell receives +f * v-, right cell -f * v+; P is left when sd = 1
+        const Sc sgn = sd == 1 ? Sc(1.0) : Sc(-1.0);
+#pragma unroll
+        for (int e = 0; e < NL + 2; ++e) {
+            T f = fl[e] * (wf * sgn);
+            acc[near][e] += f * wn;
+            acc[far][e] += f * wfar;
+        }
+    }
+}
+
+// Neumann terms on domain faces of a line: anode (x = nx face of the last layer) and current
+// collector (x = 0 face of structure voxels), Eqs. 25-27 at the face Gauss point of the line.
+template <class Chem, class T>
+__device__ __forceinline__ void line_boundary(const DevParams& p, const Line<Chem, T>& P, int d, int i, bool stP,
+                                              double jscale, int relax, T acc[2][Chem::NL + 2]) {
+    typedef typename Base<T>::type Sc;
+    constexpr int NL = Chem::NL;
+    if (d != 0) return;
+    const Sc wf = Sc(0.25 * p.h * p.h);
+    if (i == p.nx - 1) {
+        T cLi = P.c[1][0] * Sc(ALPHA) + P.c[0][0] * Sc(BETA);
+        T phL = P.phiL[1] * Sc(ALPHA) + P.phiL[0] * Sc(BETA);
+        T rA = anode_rate<T>(p, cLi, phL);
+        T fLi = rA * (wf * Sc(p.kAno));
+        T fL = rA * (wf * Sc(p.F * p.kAno));
+        if (!relax) { acc[1][0] += fLi * Sc(ALPHA); acc[0][0] += fLi * Sc(BETA); }
+        acc[1][NL] += fL * Sc(ALPHA);
+        acc[0][NL] += fL * Sc(BETA);
+    }
+    if (i == 0 && stP) {
+        double fj = 0.25 * p.h * p.h * p.j_cc * jscale;
+        acc[0][NL + 1] += Make<T>::c(fj * ALPHA);
+        acc[1][NL + 1] += Make<T>::c(fj * BETA);
+    }
+}
+
+template <class Chem, class S, int MODE>    // MODE 0 residual, 1 JVP tangent
+__global__ void __launch_bounds__(128) k_dg1_lines(const DevParams p, const Geo g, const S* __restrict__ z,
+                                                   const S* __restrict__ v, const S* __restrict__ gb,
+                                                   const S* __restrict__ gbd, int d, double t, double dt, int relax,
+                                                   double sc_dt, S* __restrict__ r) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 4) return;
+    typedef typename std::conditional<MODE == 1, Dual<S>, S>::type T;
+    constexpr int NL = Chem::NL;
+    const bool tan = MODE == 1;
+    const int q = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)q * p.n_cell);
+    int i, j, k;
+    cell_ijk(p, cell, i, j, k);
+    int n0, n1;
+    line_nodes(d, q, n0, n1);
+    const int ph = g.phase[cell];
+    const int sidx = g.cmap[cell];
+    const bool st = ph == 1;
+    Line<Chem, T> P;
+    load_line<Chem, T, S>(p, z, v, tan, cell, sidx, st, n0, n1, -1, -1, P);
+    auto gload = [&](int slot, int c) -> T {
+        int64_t o = (int64_t)slot * p.n_cell + c;
+        return Make<T>::var(gb[o], tan ? (double)gbd[o] : 0.0);
+    };
+    T gN[2] = {gload(n0, cell), gload(n1, cell)};
+    T gP[2] = {gload(face_slot(d, -1, q), cell), gload(face_slot(d, +1, q), cell)};
+    Line<Chem, T> Q[2];
+    T gQ[2];
+    bool hasQ[2], stQ[2];
+    const int coord = d == 0 ? i : d == 1 ? j : k;
+    const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
+    const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        int qc = coord + (sd == 0 ? -1 : 1);
+        hasQ[sd] = qc >= 0 && qc < ext;
+        stQ[sd] = false;
+        gQ[sd] = Make<T>::c(0.0);
+        if (hasQ[sd]) {
+            int qcell = cell + (sd == 0 ? -stride : stride);
+            int qph = g.phase[qcell];
+            stQ[sd] = qph == 1;
+            load_line<Chem, T, S>(p, z, v, tan, qcell, g.cmap[qcell], stQ[sd], n0, n1, -1, -1, Q[sd]);
+            gQ[sd] = gload(face_slot(d, sd == 0 ? +1 : -1, q), qcell);
+        }
+    }
+    T acc[2][NL + 2];
+    line_terms<Chem, T>(p, P, gN, gP, st, Q, gQ, hasQ, stQ, relax, acc);
+    line_boundary<Chem, T>(p, P, d, i, st, relax ? smooth_step(t) : 1.0, relax, acc);
+    const int nodes[2] = {n0, n1};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+#pragma unroll
+        for (int e = 0; e < NL + 2; ++e) {
+            int f = e < NL ? e : (e == NL ? Chem::PHIL : Chem::PHIS);
+            if (f == Chem::PHIS && !st) continue;
+            int64_t o = p.off[f] + (int64_t)nodes[a] * p.flen[f] + (f == Chem::PHIS ? sidx : cell);
+            if constexpr (MODE == 1) {
+                S add = acc[a][e].d;
+                if (sc_dt > 0.0) add = add * S(sc_dt * p.rscale[f]);
+                r[o] += add;
+            } else {
+                r[o] += acc[a][e];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ per-node diagonal blocks of S J
+// One thread per (node, voxel): for each own unknown (column) seed it, evaluate the node terms and
+// the three lines through the node with the seed (own g values recomputed so that they carry the
+// tangent), and keep the rows of this node.
+template <class Chem>
+__global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                const double* __restrict__ gb, double t, double dt, int relax,
+                                                double* __restrict__ blk) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 8) return;
+    typedef Dual<double> T;
+    constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
+    const int n = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)n * p.n_cell);
+    int i, j, k;
+    cell_ijk(p, cell, i, j, k);
+    const int ph = g.phase[cell];
+    const int sidx = g.cmap[cell];
+    const bool st = ph == 1;
+    double* B = blk + b * NF * NF;
+    double old[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) old[f] = 0.0;
+    const double tH = smooth_step(t);
+    const int an[3] = {n & 1, (n >> 1) & 1, (n >> 2) & 1};
+#pragma unroll 1
+    for (int col = 0; col < NF; ++col) {
+        if (p.is_struct[col] && !st) {
+            for (int row = 0; row < NF; ++row) B[row * NF + col] = row == col ? 1.0 : 0.0;
+            continue;
+        }
+        double colv[NF];
+        // node terms with the seed
+        {
+            T c[NL], es[2], phiL, phiS;
+#pragma unroll
+            for (int m = 0; m < NL; ++m) c[m] = Make<T>::var(ld(z, p, m, n, cell), col == m ? 1.0 : 0.0);
+            es[0] = es[1] = Make<T>::c(0.0);
+            phiS = Make<T>::c(0.0);
+            phiL = Make<T>::var(ld(z, p, PHIL, n, cell), col == PHIL ? 1.0 : 0.0);
+            if (st) {
+#pragma unroll
+                for (int q = 0; q < NS; ++q) es[q] = Make<T>::var(ld(z, p, NL + q, n, sidx), col == NL + q ? 1.0 : 0.0);
+                phiS = Make<T>::var(ld(z, p, PHIS, n, sidx), col == PHIS ? 1.0 : 0.0);
+            }
+            T R[NF];
+            node_terms<Chem, T>(p, ph, c, es, phiL, phiS, old, tH, dt, relax, R);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) colv[f] = R[f].d;
+        }
+        // the three lines through node n
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            int u = d == 0 ? an[1] : an[0];
+            int w = d == 2 ? an[1] : an[2];
+            int q = u + 2 * w;
+            int n0, n1;
+            line_nodes(d, q, n0, n1);
+            Line<Chem, T> P;
+            load_line<Chem, T, double>(p, z, z, false, cell, sidx, st, n0, n1, n, col, P);
+            // own g at the nodes and at the two face points of the line, with the seed
+            T es2[2][2];
+            for (int a = 0; a < 2; ++a) {
+                int nn = a == 0 ? n0 : n1;
+                for (int s2 = 0; s2 < 2; ++s2)
+                    es2[a][s2] = (NS == 2 && st) ? Make<T>::var(ld(z, p, NL + s2, nn, sidx), (nn == n && col == NL + s2) ? 1.0 : 0.0)
+                                                 : Make<T>::c(0.0);
+            }
+            T gN[2], gP[2];
+            for (int a = 0; a < 2; ++a) {
+                T eL = liquid_fraction<Chem, T>(p, ph, es2[a]);
+                gN[a] = transport_factor<Chem, T>(p, eL, P.c[a]);
+            }
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const double wn = s2 == 1 ? ALPHA : BETA, wfar = s2 == 1 ? BETA : ALPHA;
+                T ct[NL], et[2];
+                for (int m = 0; m < NL; ++m) ct[m] = P.c[1][m] * wn + P.c[0][m] * wfar;
+                et[0] = es2[1][0] * wn + es2[0][0] * wfar;
+                et[1] = es2[1][1] * wn + es2[0][1] * wfar;
+                T eL = liquid_fraction<Chem, T>(p, ph, et);
+                gP[s2] = transport_factor<Chem, T>(p, eL, ct);
+            }
+            Line<Chem, T> Q[2];
+            T gQ[2];
+            bool hasQ[2], stQ[2];
+            const int coord = d == 0 ? i : d == 1 ? j : k;
+            const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
+            const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+            for (int sd = 0; sd < 2; ++sd) {
+                int qc = coord + (sd == 0 ? -1 : 1);
+                hasQ[sd] = qc >= 0 && qc < ext;
+                stQ[sd] = false;
+                gQ[sd] = Make<T>::c(0.0);
+                if (hasQ[sd]) {
+                    int qcell = cell + (sd == 0 ? -stride : stride);
+                    stQ[sd] = g.phase[qcell] == 1;
+                    load_line<Chem, T, double>(p, z, z, false, qcell, g.cmap[qcell], stQ[sd], n0, n1, -1, -1, Q[sd]);
+                    gQ[sd] = Make<T>::c(gb[(int64_t)face_slot(d, sd == 0 ? +1 : -1, q) * p.n_cell + qcell]);
+                }
+            }
+            T acc[2][NL + 2];
+            line_terms<Chem, T>(p, P, gN, gP, st, Q, gQ, hasQ, stQ, relax, acc);
+            line_boundary<Chem, T>(p, P, d, i, st, relax ? tH : 1.0, relax, acc);
+            const int a = (n == n1) ? 1 : 0;
+            for (int e = 0; e < NL + 2; ++e) {
+                int f = e < NL ? e : (e == NL ? PHIL : PHIS);
+                colv[f] += acc[a][e].d;
+            }
+        }
+#pragma unroll
+        for (int row = 0; row < NF; ++row) {
+            double o = colv[row] * dt * p.rscale[row];
+            if (p.is_struct[row] && !st) o = row == col ? 1.0 : 0.0;
+            B[row * NF + col] = o;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+static inline int nblocks(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+int64_t dg1_face_buffer_len(const DevParams& p) { return (int64_t)NG * p.n_cell; }
+
+template <class Chem>
+static cudaError_t residual_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* zn,
+                                 double t, double dt, int relax, double* r, double* gb) {
+    k_dg1_g<Chem, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
+    k_dg1_nodes<Chem, double, 0><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, g, z, z, zn, t, dt, relax, 0.0, r);
+    for (int d = 0; d < 3; ++d)
+        k_dg1_lines<Chem, double, 0><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb, d, t, dt, relax, 0.0, r);
+    *L.counter += 5;
+    return cudaGetLastError();
+}
+
+cudaError_t dg1_residual(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* zn,
+                         double t, double dt, int relax, double* r, double* gb) {
+    return p.nf == 10 ? residual_impl<ChemTO>(L, p, g, z, zn, t, dt, relax, r, gb)
+                      : residual_impl<ChemR3>(L, p, g, z, zn, t, dt, relax, r, gb);
+}
+
+template <class Chem, class S>
+static cudaError_t jvp_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v, double t,
+                            double dt, int relax, double sc_dt, S* out, S* gb, S* gbd) {
+    k_dg1_g<Chem, S, true><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, v, gb, gbd);
+    k_dg1_nodes<Chem, S, 1><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, g, z, v, nullptr, t, dt, relax, sc_dt, out);
+    for (int d = 0; d < 3; ++d)
+        k_dg1_lines<Chem, S, 1><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, v, gb, gbd, d, t, dt, relax, sc_dt, out);
+    *L.counter += 5;
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t dg1_jvp(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v, double t, double dt,
+                    int relax, double sc_dt, S* out, S* gb, S* gbd) {
+    return p.nf == 10 ? jvp_impl<ChemTO, S>(L, p, g, z, v, t, dt, relax, sc_dt, out, gb, gbd)
+                      : jvp_impl<ChemR3, S>(L, p, g, z, v, t, dt, relax, sc_dt, out, gb, gbd);
+}
 template cudaError_t dg1_jvp<double>(const LaunchCtx&, const DevParams&, const Geo&, const double*, const double*, double,
                                      double, int, double, double*, double*, double*);
 template cudaError_t dg1_jvp<float>(const LaunchCtx&, const DevParams&, const Geo&, const float*, const float*, double,
                                     double, int, double, float*, float*, float*);
-cudaError_t dg1_blocks(const LaunchCtx&, const DevParams&, const Geo&, const double*, double, double, int, double*,
-                       double*) { return cudaErrorNotSupported; }
-int64_t dg1_face_buffer_len(const DevParams& p) { return p.n_cell; }
+
+cudaError_t dg1_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t, double dt,
+                       int relax, double* blk, double* gb) {
+    if (p.nf == 10) {
+        k_dg1_g<ChemTO, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
+        k_dg1_blk<ChemTO><<<nblocks((int64_t)p.n_cell * 8, 64), 64, 0, L.st>>>(p, g, z, gb, t, dt, relax, blk);
+    } else {
+        k_dg1_g<ChemR3, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
+        k_dg1_blk<ChemR3><<<nblocks((int64_t)p.n_cell * 8, 64), 64, 0, L.st>>>(p, g, z, gb, t, dt, relax, blk);
+    }
+    *L.counter += 2;
+    return cudaGetLastError();
+}
+
 }  // namespace dgls

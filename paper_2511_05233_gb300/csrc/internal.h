@@ -1,6 +1,7 @@
 // Internal interfaces between the C-ABI layer (api.cu) and the kernel translation units.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -12,6 +13,21 @@ struct Geo {
     const uint8_t* phase;      // [n_cell]
     const int32_t* cmap;       // [n_cell] structure index or -1
     const int32_t* sidx;       // [n_struct] structure index -> voxel
+};
+
+// One level of the potential multigrid (two fields per voxel: Phi^L, Phi^S).
+struct MGLevel {
+    int nx, ny, nz, n;
+    double* gL;    // [3][n] liquid conductance to the + neighbour in x, y, z
+    double* gS;    // [3][n] solid conductance to the + neighbour
+    double* a;     // [n] Butler-Volmer coupling between the two potentials
+    double* dL;    // [n] diagonal of the Phi^L row (anode exchange, relaxation term)
+    double* dS;    // [n] diagonal of the Phi^S row (relaxation term)
+    uint8_t* st;   // [n] voxel carries Phi^S
+    double* dinv;  // [4][n] inverse of the 2 x 2 diagonal block
+    double* x;     // [2][n]
+    double* xt;    // [2][n]
+    double* b;     // [2][n]
 };
 
 // Launch counter increment hook (owned by the context).
@@ -70,6 +86,17 @@ cudaError_t cell_voltage(const LaunchCtx& L, const DevParams& p, const Geo& g, c
                          double* partial, double* out);
 cudaError_t ledger(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
                    double* partial, double* out5);
+
+// ------------------------------------------------------------------ potential multigrid (mg.cu)
+cudaError_t mg_levels_alloc(std::vector<MGLevel>& lv, int nx, int ny, int nz, std::vector<void*>& allocs,
+                            int64_t* bytes);
+cudaError_t mg_setup(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* gb,
+                     double t, double dt, int relax, std::vector<MGLevel>& lv);
+template <class S>
+cudaError_t cpr_stage1(const LaunchCtx& L, const DevParams& p, const Geo& g, std::vector<MGLevel>& lv, int cycles,
+                       const S* v, S* y);
+template <class S>
+cudaError_t saxpby(const LaunchCtx& L, S* y, double a, const S* x, double b, int64_t n);
 
 constexpr int RED_BLOCKS = 1216;   // 8 x 152 SMs: fixed grid so that reductions are deterministic
 constexpr int RED_THREADS = 256;

@@ -281,6 +281,20 @@ cudaError_t axpby(const LaunchCtx& L, double* y, double a, const double* x, doub
     return cudaGetLastError();
 }
 
+template <class S>
+__global__ void k_saxpby(S* __restrict__ y, double a, const S* __restrict__ x, double b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (S)(a * (double)y[i] + b * (double)x[i]);
+}
+template <class S>
+cudaError_t saxpby(const LaunchCtx& L, S* y, double a, const S* x, double b, int64_t n) {
+    k_saxpby<S><<<RED_BLOCKS * 2, 256, 0, L.st>>>(y, a, x, b, n);
+    *L.counter += 1;
+    return cudaGetLastError();
+}
+template cudaError_t saxpby<double>(const LaunchCtx&, double*, double, const double*, double, int64_t);
+template cudaError_t saxpby<float>(const LaunchCtx&, float*, double, const float*, double, int64_t);
+
 __global__ void k_to_f32(float* __restrict__ d, const double* __restrict__ s, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         d[i] = (float)s[i];

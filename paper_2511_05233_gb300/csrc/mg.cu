@@ -1,0 +1,468 @@
+// Two-stage (CPR-type) preconditioner of the Newton systems: an aggregation multigrid for the
+// potential block, followed by cell-block Jacobi on the whole system.
+//
+// The two charge equations of Tab. 4 carry no storage term, so their block of S J is elliptic:
+// with the Butler-Volmer derivatives (a = -M dq_S/dPhi^S >= 0) it is exactly
+//   (A x)_L = sum_faces G_L (x_L,P - x_L,Q) + a (x_L - x_S) + d_L x_L
+//   (A x)_S = sum_faces G_S (x_S,P - x_S,Q) + a (x_S - x_L) + d_S x_S
+// a symmetric M-matrix (two coupled graph Laplacians grounded by the anode exchange current d_L),
+// where G_L = h sum_j K^m_j {g c_j}_H (DG0) is the liquid conductance of the migration terms and
+// G_S = h kappa_S the solid one.  Block Jacobi alone needs O(n) Krylov iterations on it; one
+// V-cycle of this multigrid removes the smooth potential error at every level.
+//
+// DG1 uses the same operator on voxel averages: with the voxel-constant prolongation P, P^T A P of
+// the DG1 potential block keeps only the penalty term of Eq. 46 (face conductance
+// penalty (h/4) sum_{4 face points} sum_j K^m_j {g c_j}_H) and the node sums of a and d.
+//
+// Hierarchy: 2 x 2 x 2 aggregation with piecewise-constant interpolation (the Galerkin coarse
+// operator of a graph Laplacian is the aggregated graph Laplacian: coarse conductances are sums of
+// the fine conductances crossing aggregate boundaries); damped 2 x 2 block-Jacobi smoothing;
+// the coarsest level (<= 512 voxels) is relaxed by one thread block.
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "internal.h"
+
+namespace dgls {
+
+namespace {
+constexpr double SQ3 = 1.7320508075688772935;
+constexpr double ALPHA = 0.5 * (1.0 + SQ3);
+constexpr double BETA = 0.5 * (1.0 - SQ3);
+
+inline int nb(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+__device__ __forceinline__ void ijk(int c, int nx, int ny, int& i, int& j, int& k) {
+    i = c % nx;
+    int r = c / nx;
+    j = r % ny;
+    k = r / ny;
+}
+}  // namespace
+
+// ------------------------------------------------------------------ level-0 coefficients (DG0)
+template <class Chem>
+__global__ void k_pp_dg0(const DevParams p, const Geo g, const double* __restrict__ z, const double* __restrict__ gb,
+                         double t, double dt, int relax, MGLevel L) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    constexpr int NL = Chem::NL;
+    const double s = dt * p.rscale[Chem::PHIL];
+    int i, j, k;
+    ijk(cell, p.nx, p.ny, i, j, k);
+    const int ph = g.phase[cell];
+    const int sidx = g.cmap[cell];
+    const bool st = ph == 1;
+    double cP[NL];
+    for (int m = 0; m < NL; ++m) cP[m] = z[p.off[m] + cell];
+    const double gP = gb[cell];
+    for (int d = 0; d < 3; ++d) {
+        int qi = i + (d == 0), qj = j + (d == 1), qk = k + (d == 2);
+        double gl = 0.0, gs = 0.0;
+        if (qi < p.nx && qj < p.ny && qk < p.nz) {
+            int q = qi + p.nx * (qj + p.ny * qk);
+            double gQ = gb[q];
+            for (int m = 0; m < NL; ++m)
+                if (p.zc[m] != 0.0) gl += p.Km[m] * harm(gP * cP[m], gQ * z[p.off[m] + q]);
+            gl *= p.h;
+            if (st && g.phase[q] == 1) gs = p.h * p.kappa_s;
+        }
+        L.gL[(int64_t)d * L.n + cell] = s * gl;
+        L.gS[(int64_t)d * L.n + cell] = s * gs;
+    }
+    double a = 0.0, dL = 0.0, dS = 0.0;
+    if (st) {
+        typedef Dual<double> T;
+        T c[NL], es[2], Sv[NL], Ss[2], qL, qS;
+        for (int m = 0; m < NL; ++m) c[m] = mkd(cP[m], 0.0);
+        es[0] = es[1] = mkd(0.0, 0.0);
+        for (int q = 0; q < Chem::NS; ++q) es[q] = mkd(z[p.off[NL + q] + sidx], 0.0);
+        T phiL = mkd(z[p.off[Chem::PHIL] + cell], 0.0);
+        T phiS = mkd(z[p.off[Chem::PHIS] + sidx], 1.0);
+        sources<Chem, T>(p, c, es, phiL, phiS, smooth_step(t), Sv, Ss, qL, qS);
+        a = -p.V * qS.d;
+    }
+    if (i == p.nx - 1) {
+        Dual<double> r = anode_rate<Dual<double>>(p, mkd(cP[0], 0.0), mkd(z[p.off[Chem::PHIL] + cell], 1.0));
+        dL = p.A * p.F * p.kAno * r.d;
+    }
+    if (relax) {
+        dL += p.V / dt;
+        if (st) dS += p.V / dt;
+    }
+    L.a[cell] = s * a;
+    L.dL[cell] = s * dL;
+    L.dS[cell] = s * dS;
+    L.st[cell] = st ? 1 : 0;
+}
+
+// ------------------------------------------------------------------ level-0 coefficients (DG1)
+template <class Chem>
+__global__ void k_pp_dg1(const DevParams p, const Geo g, const double* __restrict__ z, const double* __restrict__ gb,
+                         double t, double dt, int relax, MGLevel L) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    constexpr int NL = Chem::NL;
+    const double s = dt * p.rscale[Chem::PHIL];         // node row scale of the potential rows
+    int i, j, k;
+    ijk(cell, p.nx, p.ny, i, j, k);
+    const int ph = g.phase[cell];
+    const int sidx = g.cmap[cell];
+    const bool st = ph == 1;
+    auto zf = [&](int f, int n, int idx) { return z[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
+    const double wf = 0.25 * p.h * p.h;
+    for (int d = 0; d < 3; ++d) {
+        int qi = i + (d == 0), qj = j + (d == 1), qk = k + (d == 2);
+        double gl = 0.0, gs = 0.0;
+        if (qi < p.nx && qj < p.ny && qk < p.nz) {
+            int q = qi + p.nx * (qj + p.ny * qk);
+            for (int pt = 0; pt < 4; ++pt) {
+                int u = pt & 1, w = pt >> 1;
+                int n0, n1;
+                if (d == 0) { n0 = 0 + 2 * u + 4 * w; n1 = n0 + 1; }
+                else if (d == 1) { n0 = u + 0 + 4 * w; n1 = n0 + 2; }
+                else { n0 = u + 2 * w; n1 = n0 + 4; }
+                // own + face point (slot 8 + (2d+1)*4 + pt), neighbour - face point (slot 8 + 2d*4 + pt)
+                double gP = gb[(int64_t)(8 + (2 * d + 1) * 4 + pt) * p.n_cell + cell];
+                double gQ = gb[(int64_t)(8 + (2 * d) * 4 + pt) * p.n_cell + q];
+                double acc = 0.0;
+                for (int m = 0; m < NL; ++m) {
+                    if (p.zc[m] == 0.0) continue;
+                    double cp = ALPHA * zf(m, n1, cell) + BETA * zf(m, n0, cell);
+                    double cq = ALPHA * zf(m, n0, q) + BETA * zf(m, n1, q);
+                    acc += p.Km[m] * harm(gP * cp, gQ * cq);
+                }
+                gl += acc;
+            }
+            gl *= wf * p.penalty / p.h;
+            if (st && g.phase[q] == 1) gs = 4.0 * wf * p.penalty / p.h * p.kappa_s;
+        }
+        L.gL[(int64_t)d * L.n + cell] = s * gl;
+        L.gS[(int64_t)d * L.n + cell] = s * gs;
+    }
+    double a = 0.0, dL = 0.0, dS = 0.0;
+    const double M = p.V / 8.0;
+    if (st) {
+        typedef Dual<double> T;
+        for (int n = 0; n < 8; ++n) {
+            T c[NL], es[2], Sv[NL], Ss[2], qL, qS;
+            for (int m = 0; m < NL; ++m) c[m] = mkd(zf(m, n, cell), 0.0);
+            es[0] = es[1] = mkd(0.0, 0.0);
+            for (int q = 0; q < Chem::NS; ++q) es[q] = mkd(zf(NL + q, n, sidx), 0.0);
+            T phiL = mkd(zf(Chem::PHIL, n, cell), 0.0);
+            T phiS = mkd(zf(Chem::PHIS, n, sidx), 1.0);
+            sources<Chem, T>(p, c, es, phiL, phiS, smooth_step(t), Sv, Ss, qL, qS);
+            a += -M * qS.d;
+        }
+    }
+    if (i == p.nx - 1) {
+        for (int pt = 0; pt < 4; ++pt) {
+            int n0 = 2 * (pt & 1) + 4 * (pt >> 1), n1 = n0 + 1;
+            double cLi = ALPHA * zf(0, n1, cell) + BETA * zf(0, n0, cell);
+            double phL = ALPHA * zf(Chem::PHIL, n1, cell) + BETA * zf(Chem::PHIL, n0, cell);
+            Dual<double> r = anode_rate<Dual<double>>(p, mkd(cLi, 0.0), mkd(phL, 1.0));
+            dL += wf * p.F * p.kAno * r.d;
+        }
+    }
+    if (relax) {
+        dL += p.V / dt;
+        if (st) dS += p.V / dt;
+    }
+    L.a[cell] = s * a;
+    L.dL[cell] = s * dL;
+    L.dS[cell] = s * dS;
+    L.st[cell] = st ? 1 : 0;
+}
+
+// ------------------------------------------------------------------ hierarchy
+__global__ void k_mg_coarsen(MGLevel F, MGLevel C) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C.n) return;
+    int I, J, K;
+    ijk(c, C.nx, C.ny, I, J, K);
+    double gl[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, a = 0, dL = 0, dS = 0;
+    int st = 0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+                if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
+                int f = i + F.nx * (j + F.ny * k);
+                a += F.a[f];
+                dL += F.dL[f];
+                dS += F.dS[f];
+                st |= F.st[f];
+                // faces leaving the aggregate in + direction come from its last child layer
+                if (di == 1) { gl[0] += F.gL[f]; gs[0] += F.gS[f]; }
+                if (dj == 1) { gl[1] += F.gL[(int64_t)F.n + f]; gs[1] += F.gS[(int64_t)F.n + f]; }
+                if (dk == 1) { gl[2] += F.gL[2 * (int64_t)F.n + f]; gs[2] += F.gS[2 * (int64_t)F.n + f]; }
+            }
+    // an aggregate with a single child layer along d has no "+" child: its + faces are those of
+    // that layer (only at the grid end, where they are zero anyway)
+    for (int d = 0; d < 3; ++d) {
+        C.gL[(int64_t)d * C.n + c] = gl[d];
+        C.gS[(int64_t)d * C.n + c] = gs[d];
+    }
+    C.a[c] = a;
+    C.dL[c] = dL;
+    C.dS[c] = dS;
+    C.st[c] = st;
+}
+
+// 2 x 2 block diagonal of A and its inverse
+__global__ void k_mg_diag(MGLevel L) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.n) return;
+    int i, j, k;
+    ijk(c, L.nx, L.ny, i, j, k);
+    double sl = 0.0, ss = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        sl += L.gL[(int64_t)d * L.n + c];
+        ss += L.gS[(int64_t)d * L.n + c];
+    }
+    if (i > 0) { sl += L.gL[c - 1]; ss += L.gS[c - 1]; }
+    if (j > 0) { sl += L.gL[(int64_t)L.n + c - L.nx]; ss += L.gS[(int64_t)L.n + c - L.nx]; }
+    if (k > 0) { sl += L.gL[2 * (int64_t)L.n + c - L.nx * L.ny]; ss += L.gS[2 * (int64_t)L.n + c - L.nx * L.ny]; }
+    double a = L.a[c];
+    double d00 = sl + a + L.dL[c], d01 = -a, d10 = -a, d11 = ss + a + L.dS[c];
+    if (!L.st[c]) { d01 = d10 = 0.0; d11 = 1.0; }
+    if (!(d00 > 0.0)) d00 = 1.0;
+    if (!(d11 > 0.0)) d11 = 1.0;
+    double det = d00 * d11 - d01 * d10;
+    L.dinv[c] = d11 / det;
+    L.dinv[(int64_t)L.n + c] = -d01 / det;
+    L.dinv[2 * (int64_t)L.n + c] = -d10 / det;
+    L.dinv[3 * (int64_t)L.n + c] = d00 / det;
+}
+
+// (A x) at cell c for both fields
+__device__ __forceinline__ void apply_A(const MGLevel& L, const double* x, int c, double& yl, double& ys) {
+    int i, j, k;
+    ijk(c, L.nx, L.ny, i, j, k);
+    const int64_t n = L.n;
+    double xl = x[c], xs = x[n + c];
+    double accl = 0.0, accs = 0.0;
+    // + neighbours
+    if (i + 1 < L.nx) { double gl = L.gL[c], gs = L.gS[c]; accl += gl * (xl - x[c + 1]); accs += gs * (xs - x[n + c + 1]); }
+    if (j + 1 < L.ny) { double gl = L.gL[n + c], gs = L.gS[n + c]; int q = c + L.nx; accl += gl * (xl - x[q]); accs += gs * (xs - x[n + q]); }
+    if (k + 1 < L.nz) { double gl = L.gL[2 * n + c], gs = L.gS[2 * n + c]; int q = c + L.nx * L.ny; accl += gl * (xl - x[q]); accs += gs * (xs - x[n + q]); }
+    // - neighbours
+    if (i > 0) { int q = c - 1; accl += L.gL[q] * (xl - x[q]); accs += L.gS[q] * (xs - x[n + q]); }
+    if (j > 0) { int q = c - L.nx; accl += L.gL[n + q] * (xl - x[q]); accs += L.gS[n + q] * (xs - x[n + q]); }
+    if (k > 0) { int q = c - L.nx * L.ny; accl += L.gL[2 * n + q] * (xl - x[q]); accs += L.gS[2 * n + q] * (xs - x[n + q]); }
+    double a = L.a[c];
+    yl = accl + a * (xl - xs) + L.dL[c] * xl;
+    ys = L.st[c] ? accs + a * (xs - xl) + L.dS[c] * xs : xs;
+}
+
+// x_out = x_in + w D^-1 (b - A x_in); zero_in: x_in = 0
+__global__ void k_mg_jacobi(MGLevel L, const double* __restrict__ xin, double* __restrict__ xout, double w, int zero_in) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.n) return;
+    const int64_t n = L.n;
+    double rl = L.b[c], rs = L.b[n + c];
+    double xl = 0.0, xs = 0.0;
+    if (!zero_in) {
+        double yl, ys;
+        apply_A(L, xin, c, yl, ys);
+        rl -= yl;
+        rs -= ys;
+        xl = xin[c];
+        xs = xin[n + c];
+    }
+    xout[c] = xl + w * (L.dinv[c] * rl + L.dinv[n + c] * rs);
+    xout[n + c] = xs + w * (L.dinv[2 * n + c] * rl + L.dinv[3 * n + c] * rs);
+}
+
+// coarse b = restriction of the fine residual b - A x (sum over the aggregate; S only over
+// structure children)
+__global__ void k_mg_restrict(MGLevel F, MGLevel C) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C.n) return;
+    int I, J, K;
+    ijk(c, C.nx, C.ny, I, J, K);
+    double bl = 0.0, bs = 0.0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+                if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
+                int f = i + F.nx * (j + F.ny * k);
+                double yl, ys;
+                apply_A(F, F.x, f, yl, ys);
+                bl += F.b[f] - yl;
+                if (F.st[f]) bs += F.b[(int64_t)F.n + f] - ys;
+            }
+    C.b[c] = bl;
+    C.b[(int64_t)C.n + c] = bs;
+}
+
+__global__ void k_mg_prolong(MGLevel F, MGLevel C) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F.n) return;
+    int i, j, k;
+    ijk(f, F.nx, F.ny, i, j, k);
+    int c = (i >> 1) + C.nx * ((j >> 1) + C.ny * (k >> 1));
+    F.x[f] += C.x[c];
+    if (F.st[f]) F.x[(int64_t)F.n + f] += C.x[(int64_t)C.n + c];
+}
+
+// coarsest level: damped Jacobi sweeps by one thread block (n <= 1024)
+__global__ void __launch_bounds__(1024) k_mg_coarse(MGLevel L, int sweeps, double w) {
+    const int c = threadIdx.x;
+    const int64_t n = L.n;
+    double* x = L.x;
+    double* y = L.xt;
+    if (c < n) { x[c] = 0.0; x[n + c] = 0.0; }
+    __syncthreads();
+    for (int s = 0; s < sweeps; ++s) {
+        if (c < n) {
+            double yl, ys;
+            apply_A(L, x, c, yl, ys);
+            double rl = L.b[c] - yl, rs = L.b[n + c] - ys;
+            y[c] = x[c] + w * (L.dinv[c] * rl + L.dinv[n + c] * rs);
+            y[n + c] = x[n + c] + w * (L.dinv[2 * n + c] * rl + L.dinv[3 * n + c] * rs);
+        }
+        __syncthreads();
+        if (c < n) { x[c] = y[c]; x[n + c] = y[n + c]; }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ CPR restriction / prolongation
+template <class S>
+__global__ void k_cpr_restrict(const DevParams p, const Geo g, const S* __restrict__ v, MGLevel L) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    const int nn = p.order == 1 ? 8 : 1;
+    const int fL = p.nf - 2, fS = p.nf - 1;
+    const int s = g.cmap[cell];
+    double bl = 0.0, bs = 0.0;
+    for (int n = 0; n < nn; ++n) {
+        bl += (double)v[p.off[fL] + (int64_t)n * p.flen[fL] + cell];
+        if (s >= 0) bs += (double)v[p.off[fS] + (int64_t)n * p.flen[fS] + s];
+    }
+    L.b[cell] = bl;
+    L.b[(int64_t)L.n + cell] = bs;
+}
+
+// y = P x (potential fields), zero elsewhere
+template <class S>
+__global__ void k_cpr_prolong(const DevParams p, const Geo g, MGLevel L, S* __restrict__ y) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nn = p.order == 1 ? 8 : 1;
+    if (b >= (int64_t)p.n_cell * nn) return;
+    const int n = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)n * p.n_cell);
+    const int fL = p.nf - 2, fS = p.nf - 1;
+    for (int f = 0; f < fL; ++f) {
+        if (!p.is_struct[f]) y[p.off[f] + (int64_t)n * p.flen[f] + cell] = S(0);
+        else if (g.cmap[cell] >= 0) y[p.off[f] + (int64_t)n * p.flen[f] + g.cmap[cell]] = S(0);
+    }
+    y[p.off[fL] + (int64_t)n * p.flen[fL] + cell] = (S)L.x[cell];
+    const int s = g.cmap[cell];
+    if (s >= 0) y[p.off[fS] + (int64_t)n * p.flen[fS] + s] = (S)L.x[(int64_t)L.n + cell];
+}
+
+// ------------------------------------------------------------------ host drivers
+cudaError_t mg_levels_alloc(std::vector<MGLevel>& lv, int nx, int ny, int nz, std::vector<void*>& allocs,
+                            int64_t* bytes) {
+    lv.clear();
+    int x = nx, y = ny, zz = nz;
+    for (;;) {
+        MGLevel L;
+        std::memset(&L, 0, sizeof(L));
+        L.nx = x; L.ny = y; L.nz = zz;
+        L.n = x * y * zz;
+        auto al = [&](auto** ptr, int64_t cnt) -> cudaError_t {
+            void* q = nullptr;
+            cudaError_t e = cudaMalloc(&q, (size_t)cnt * sizeof(**ptr));
+            if (e != cudaSuccess) return e;
+            allocs.push_back(q);
+            *bytes += cnt * (int64_t)sizeof(**ptr);
+            *ptr = (std::remove_reference_t<decltype(*ptr)>)q;
+            return cudaSuccess;
+        };
+        cudaError_t e;
+        if ((e = al(&L.gL, 3 * (int64_t)L.n)) != cudaSuccess) return e;
+        if ((e = al(&L.gS, 3 * (int64_t)L.n)) != cudaSuccess) return e;
+        if ((e = al(&L.a, L.n)) != cudaSuccess) return e;
+        if ((e = al(&L.dL, L.n)) != cudaSuccess) return e;
+        if ((e = al(&L.dS, L.n)) != cudaSuccess) return e;
+        if ((e = al(&L.st, L.n)) != cudaSuccess) return e;
+        if ((e = al(&L.dinv, 4 * (int64_t)L.n)) != cudaSuccess) return e;
+        if ((e = al(&L.x, 2 * (int64_t)L.n)) != cudaSuccess) return e;
+        if ((e = al(&L.xt, 2 * (int64_t)L.n)) != cudaSuccess) return e;
+        if ((e = al(&L.b, 2 * (int64_t)L.n)) != cudaSuccess) return e;
+        lv.push_back(L);
+        if (L.n <= 512 || (x == 1 && y == 1 && zz == 1)) break;
+        x = (x + 1) / 2;
+        y = (y + 1) / 2;
+        zz = (zz + 1) / 2;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t mg_setup(const LaunchCtx& Lc, const DevParams& p, const Geo& g, const double* z, const double* gb,
+                     double t, double dt, int relax, std::vector<MGLevel>& lv) {
+    if (lv.empty()) return cudaErrorInvalidValue;
+    if (p.order == 0) {
+        if (p.nf == 10) k_pp_dg0<ChemTO><<<nb(p.n_cell, 128), 128, 0, Lc.st>>>(p, g, z, gb, t, dt, relax, lv[0]);
+        else k_pp_dg0<ChemR3><<<nb(p.n_cell, 128), 128, 0, Lc.st>>>(p, g, z, gb, t, dt, relax, lv[0]);
+    } else {
+        if (p.nf == 10) k_pp_dg1<ChemTO><<<nb(p.n_cell, 128), 128, 0, Lc.st>>>(p, g, z, gb, t, dt, relax, lv[0]);
+        else k_pp_dg1<ChemR3><<<nb(p.n_cell, 128), 128, 0, Lc.st>>>(p, g, z, gb, t, dt, relax, lv[0]);
+    }
+    *Lc.counter += 1;
+    for (size_t l = 0; l + 1 < lv.size(); ++l) {
+        k_mg_coarsen<<<nb(lv[l + 1].n, 256), 256, 0, Lc.st>>>(lv[l], lv[l + 1]);
+        *Lc.counter += 1;
+    }
+    for (auto& L : lv) {
+        k_mg_diag<<<nb(L.n, 256), 256, 0, Lc.st>>>(L);
+        *Lc.counter += 1;
+    }
+    return cudaGetLastError();
+}
+
+static void vcycle(const LaunchCtx& Lc, std::vector<MGLevel>& lv, size_t l) {
+    MGLevel& L = lv[l];
+    const double w = 0.8;
+    if (l + 1 == lv.size()) {
+        k_mg_coarse<<<1, 1024, 0, Lc.st>>>(L, 60, w);
+        *Lc.counter += 1;
+        return;
+    }
+    const int g = nb(L.n, 256);
+    k_mg_jacobi<<<g, 256, 0, Lc.st>>>(L, L.x, L.xt, w, 1);
+    k_mg_jacobi<<<g, 256, 0, Lc.st>>>(L, L.xt, L.x, w, 0);
+    k_mg_restrict<<<nb(lv[l + 1].n, 256), 256, 0, Lc.st>>>(L, lv[l + 1]);
+    *Lc.counter += 3;
+    vcycle(Lc, lv, l + 1);
+    k_mg_prolong<<<g, 256, 0, Lc.st>>>(L, lv[l + 1]);
+    k_mg_jacobi<<<g, 256, 0, Lc.st>>>(L, L.x, L.xt, w, 0);
+    k_mg_jacobi<<<g, 256, 0, Lc.st>>>(L, L.xt, L.x, w, 0);
+    *Lc.counter += 3;
+}
+
+// y = P (V-cycles on R v): the potential correction of the first CPR stage
+template <class S>
+cudaError_t cpr_stage1(const LaunchCtx& Lc, const DevParams& p, const Geo& g, std::vector<MGLevel>& lv, int cycles,
+                       const S* v, S* y) {
+    MGLevel& L0 = lv[0];
+    k_cpr_restrict<S><<<nb(p.n_cell, 256), 256, 0, Lc.st>>>(p, g, v, L0);
+    *Lc.counter += 1;
+    (void)cycles;
+    vcycle(Lc, lv, 0);
+    const int nn = p.order == 1 ? 8 : 1;
+    k_cpr_prolong<S><<<nb((int64_t)p.n_cell * nn, 256), 256, 0, Lc.st>>>(p, g, L0, y);
+    *Lc.counter += 1;
+    return cudaGetLastError();
+}
+template cudaError_t cpr_stage1<double>(const LaunchCtx&, const DevParams&, const Geo&, std::vector<MGLevel>&, int,
+                                        const double*, double*);
+template cudaError_t cpr_stage1<float>(const LaunchCtx&, const DevParams&, const Geo&, std::vector<MGLevel>&, int,
+                                       const float*, float*);
+
+}  // namespace dgls

@@ -29,8 +29,9 @@ class Params(C.Structure):
     _fields_ = [("order", C.c_int32), ("chemistry", C.c_int32), ("T", C.c_double), ("f_C", C.c_double),
                 ("j_el", C.c_double), ("eps_struct", C.c_double), ("penalty", C.c_double), ("smooth", C.c_int32),
                 ("precision", C.c_int32), ("gmres_restart", C.c_int32), ("gmres_max_it", C.c_int32),
-                ("newton_rtol", C.c_double), ("newton_max_it", C.c_int32), ("eta_max", C.c_double),
-                ("eta_min", C.c_double), ("hbm_budget_bytes", C.c_int64)]
+                ("newton_rtol", C.c_double), ("newton_atol", C.c_double), ("newton_max_it", C.c_int32),
+                ("eta_max", C.c_double), ("eta_min", C.c_double), ("hbm_budget_bytes", C.c_int64),
+                ("preconditioner", C.c_int32), ("mg_cycles", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -89,6 +90,8 @@ def lib():
             "dg_cell_voltage": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
             "dg_ledger": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
             "dg_discharge": (C.c_int, [_P, _P, C.POINTER(DischargeOpts), C.POINTER(Curve)]),
+            "dg_profile": (C.c_int, [_P, C.c_int32]),
+            "dg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "dg_launch_count": (C.c_int64, [_P]),
             "dg_workspace_bytes": (C.c_int64, [_P]),
         }
@@ -255,6 +258,17 @@ class Context:
         if st not in (OK, ERR_ABORTED, ERR_NOCONV):
             self._check(st)
         return res
+
+    PROFILE_CATEGORIES = ("residual", "jvp", "precond_build", "precond_apply", "krylov")
+
+    def profile(self, enable=True):
+        self._check(self._lib.dg_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms = (C.c_double * 5)()
+        calls = (C.c_int64 * 5)()
+        self._check(self._lib.dg_profile_read(self._h, ms, calls))
+        return {k: (ms[i], calls[i]) for i, k in enumerate(self.PROFILE_CATEGORIES)}
 
     def launch_count(self):
         return int(self._lib.dg_launch_count(self._h))

@@ -18,11 +18,40 @@ def ensure_built():
     _BUILT = True
 
 
+def structure_with_collector(n, porosity, corr, seed):
+    """The first structure from seed, seed + 1, ... that keeps a structure voxel on the current
+    collector after the connectivity clean-up (small grids can lose all of it)."""
+    for s in range(seed, seed + 100):
+        phase = inputs.make_structure(n, porosity, corr, s)
+        if np.any(phase[:, :, 0] == inputs.STRUCT):
+            return phase
+    raise RuntimeError("no structure touching x = 0")
+
+
+def assert_state_close(model, grid, got, ref, rtol):
+    """Max error per field relative to the magnitude of its kind of unknown: concentrations
+    against the largest concentration, volume fractions against the largest volume fraction,
+    potentials against the largest potential.  Newton stops on the row-scaled norm ||S R||, so a
+    species present at 1e-12 mol/m^3 (S^2-) is only resolved to rtol times the concentration
+    scale, not to rtol of itself."""
+    lay = lis.layout(model, grid)
+
+    def kind(f):
+        return "pot" if f in ("PhiL", "PhiS") else ("eps" if f.startswith("eps_") else "conc")
+    scale = {}
+    for f, off, ln, s in lay:
+        k = kind(f)
+        scale[k] = max(scale.get(k, 0.0), np.abs(ref[off:off + ln]).max())
+    for f, off, ln, s in lay:
+        err = np.abs(got[off:off + ln] - ref[off:off + ln]).max() / (scale[kind(f)] + 1e-300)
+        assert err <= rtol, (f, err)
+
+
 def make_case(chem_name, order, n, porosity=0.6, corr=2.0, seed=1, noise_seed=2, f_C=0.5, potential_noise=0.0):
     """A seeded structure and a perturbed state built from the oracle's equilibrium (never from
     the CUDA path): returns (oracle model, grid, phase, z^n, z)."""
     chem = ch.reduced3() if chem_name == "reduced3" else ch.tradeoff()
-    phase = inputs.make_structure(n, porosity, corr, seed)
+    phase = structure_with_collector(n, porosity, corr, seed)
     grid = lis.Grid(phase, 1e-6)
     model = lis.Model(chem, order=order, f_C=f_C, eps_struct=1.0 - porosity)
     z0 = init.uniform_state(model, grid, init.equilibrium_fields(model))

@@ -4,7 +4,7 @@ import pytest
 
 from oracle import init, lis, newton
 from paper_2511_05233_gb300 import inputs
-from tests.gpu_helpers import ensure_built, gpu_context, jvp_magnitude, make_case, to_dev, to_host
+from tests.gpu_helpers import assert_state_close, ensure_built, gpu_context, jvp_magnitude, make_case, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -39,11 +39,7 @@ def test_dg0_relaxation_parity(chem):
     ref = init.relax(model, grid, z0, dt=0.1, t_init=0.2)
     zd = to_dev(z0)
     ctx.relax(zd, 0.1, 2)
-    got = to_host(zd)
-    for f, off, ln, s in lis.layout(model, grid):
-        a, b = got[off:off + ln], ref[off:off + ln]
-        scale = np.abs(b).max() + 1e-300
-        assert np.abs(a - b).max() <= 1e-8 * scale, (f, np.abs(a - b).max() / scale)
+    assert_state_close(model, grid, to_host(zd), ref, 1e-8)
 
 
 @pytest.mark.parametrize("chem,n", CASES)
@@ -93,11 +89,7 @@ def test_dg0_step_parity(chem, n):
     out = to_dev(np.zeros_like(z))
     st, ginfo = ctx.step(zd, out, t, dt)
     assert ginfo.converged
-    got = to_host(out)
-    for f, off, ln, s in lis.layout(model, grid):
-        a, b = got[off:off + ln], ref[off:off + ln]
-        scale = np.abs(b).max() + 1e-300
-        assert np.abs(a - b).max() <= 1e-8 * scale, (f, np.abs(a - b).max() / scale)
+    assert_state_close(model, grid, to_host(out), ref, 1e-8)
 
 
 def test_dg0_equilibrium_and_voltage():
@@ -144,7 +136,4 @@ def test_dg0_mixed_precision_step_matches_fp64():
     _, i64 = c64.step(to_dev(z), a, 0.0, 1e-3)
     _, i32 = c32.step(to_dev(z), b, 0.0, 1e-3)
     assert i64.converged and i32.converged
-    A, B = to_host(a), to_host(b)
-    for f, off, ln, s in lis.layout(model, grid):
-        scale = np.abs(A[off:off + ln]).max()
-        assert np.abs(A[off:off + ln] - B[off:off + ln]).max() <= 1e-8 * scale, f
+    assert_state_close(model, grid, to_host(b), to_host(a), 1e-8)

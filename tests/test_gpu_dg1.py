@@ -1,0 +1,86 @@
+"""GPU parity of the DG1 (Q1 interior-penalty) path against the CPU oracle."""
+import numpy as np
+import pytest
+
+from oracle import lis, newton
+from paper_2511_05233_gb300 import inputs
+from tests.gpu_helpers import assert_state_close, ensure_built, gpu_context, jvp_magnitude, make_case, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("reduced3", (7, 5, 4)), ("tradeoff", (7, 5, 4)), ("tradeoff", (10, 6, 5))]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_built()
+
+
+@pytest.mark.parametrize("chem,n", CASES)
+def test_dg1_residual_parity(chem, n):
+    model, grid, phase, z0, z = make_case(chem, 1, n, potential_noise=0.01)
+    ctx = gpu_context(model, phase)
+    assert ctx.n_dof == z.size
+    t, dt = 1.5, 1e-3
+    R_or = lis.residual(model, grid, z, z0, t, dt)
+    M = lis.residual_magnitude(model, grid, z, z0, t, dt)
+    r = to_dev(np.zeros_like(z))
+    ctx.residual(to_dev(z), to_dev(z0), t, dt, r)
+    err = np.abs(to_host(r) - R_or)
+    assert np.all(err <= 1e-12 * M), (err / M).max()
+
+
+@pytest.mark.parametrize("chem,n", CASES[:2])
+def test_dg1_jvp_parity(chem, n):
+    model, grid, phase, z0, z = make_case(chem, 1, n, potential_noise=0.01)
+    ctx = gpu_context(model, phase)
+    t, dt = 1.5, 1e-3
+    v = inputs.normal_noise(z.size, 7) * (np.abs(z) + 1e-3)
+    ref = newton.jvp(model, grid, z, z0, t, dt, v)
+    mag, _ = jvp_magnitude(model, grid, z, z0, t, dt, v)
+    out = to_dev(np.zeros_like(z))
+    ctx.jvp(to_dev(z), t, dt, to_dev(v), out)
+    err = np.abs(to_host(out) - ref)
+    assert np.all(err <= 1e-12 * mag + 1e-300), (err / np.maximum(mag, 1e-300)).max()
+
+
+def test_dg1_point_block_parity():
+    """Per-node diagonal blocks of S J (DG1 point-block Jacobi) against the oracle's Jacobian."""
+    model, grid, phase, z0, z = make_case("tradeoff", 1, (5, 4, 3), potential_noise=0.01)
+    ctx = gpu_context(model, phase)
+    t, dt = 1.5, 1e-3
+    J = newton.assemble_jacobian(model, grid, z, z0, t, dt).tocsr()
+    S = newton.row_scales(model, grid, dt)
+    v = inputs.normal_noise(z.size, 3)
+    maps, nn = newton._dof_maps(model, grid)
+    ref = np.zeros_like(v)
+    for node in range(8):
+        for cell in range(grid.n_cell):
+            idx = [off + node * ln + loc[cell] for (f, off, ln, st, loc) in maps if loc[cell] >= 0]
+            B = S[idx, None] * J[idx][:, idx].toarray()
+            ref[idx] = np.linalg.solve(B, v[idx])
+    out = to_dev(np.zeros_like(z))
+    ctx.block_jacobi(to_dev(z), t, dt, to_dev(v), out)
+    assert np.abs(to_host(out) - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_dg1_step_parity():
+    model, grid, phase, z0, z = make_case("reduced3", 1, (6, 4, 3))
+    ctx = gpu_context(model, phase)
+    ref, info = newton.implicit_euler_step(model, grid, z, 0.0, 1e-3)
+    assert info.converged
+    out = to_dev(np.zeros_like(z))
+    st, ginfo = ctx.step(to_dev(z), out, 0.0, 1e-3)
+    assert ginfo.converged
+    assert_state_close(model, grid, to_host(out), ref, 1e-8)
+
+
+def test_dg1_cell_voltage_and_ledger():
+    model, grid, phase, z0, z = make_case("tradeoff", 1, (7, 5, 4))
+    ctx = gpu_context(model, phase)
+    U = ctx.cell_voltage(to_dev(z))
+    assert abs(U - lis.cell_voltage(model, grid, z)) <= 1e-13 * abs(U)
+    led = ctx.ledger(to_dev(z))
+    mo = lis.cell_means(model, grid, z)
+    assert abs(led[0] - mo["sulfur"]) <= 1e-12 * abs(mo["sulfur"])
+    assert abs(led[1] - mo["lithium"]) <= 1e-12 * abs(mo["lithium"])
