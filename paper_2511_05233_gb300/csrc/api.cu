@@ -295,7 +295,12 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     double ceq[6], d0, U5, U6;
     tab6(prm->T, ceq, &d0, &U5, &U6);
     const double U0s[6] = {U01, U02, U03, U04, U5, U6};
-    for (int k = 0; k < 6; ++k) { P.kE[k] = KE[k]; P.U0[k] = U0s[k]; }
+    for (int k = 0; k < 6; ++k) {
+        P.kE[k] = KE[k];
+        P.U0[k] = U0s[k];
+        P.eUf[k] = std::exp(P.F_2RT * U0s[k]);
+        P.eUb[k] = std::exp(-P.F_2RT * U0s[k]);
+    }
     P.penalty = prm->penalty;
     P.smooth = prm->smooth;
     const int nn = prm->order == 1 ? 8 : 1;

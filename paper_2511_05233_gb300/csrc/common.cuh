@@ -42,6 +42,7 @@ struct DevParams {
     double j_cc;               // Neumann current per structure face at x = 0, A/m^2
     double kC[2], sqK[2];      // C1, C2: k_C and sqrt(K_sp)
     double kE[6], U0[6];       // E1..E6
+    double eUf[6], eUb[6];     // exp(+F U0/(2RT)), exp(-F U0/(2RT))
     double penalty;            // DG1 interior penalty factor
     int smooth;                // T_H on C2 and E4
     int64_t off[DG_MAXF];      // field offsets in the state vector
@@ -77,6 +78,8 @@ __device__ __forceinline__ double ssqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float ssqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double slog(double x) { return log(x); }
 __device__ __forceinline__ float slog(float x) { return logf(x); }
+__device__ __forceinline__ double scbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float scbrt(float x) { return cbrtf(x); }
 
 template <class S> __device__ __forceinline__ S val(S x) { return x; }
 template <class S> __device__ __forceinline__ S val(Dual<S> x) { return x.v; }
@@ -104,6 +107,25 @@ template <class S> __device__ __forceinline__ Dual<S> operator/(Dual<S> a, S b) 
 
 template <class S> __device__ __forceinline__ Dual<S> sexp(Dual<S> x) { S e = sexp(x.v); return mkd(e, e * x.d); }
 template <class S> __device__ __forceinline__ Dual<S> ssqrt(Dual<S> x) { S r = ssqrt(x.v); return mkd(r, x.d / (S(2) * r)); }
+
+// square and cube roots of an activity (>= 0); zero activity gives zero with a zero tangent
+template <class S> __device__ __forceinline__ S act_sqrt(S a) { return ssqrt(a); }
+template <class S> __device__ __forceinline__ Dual<S> act_sqrt(Dual<S> a) {
+    if (!(a.v > S(0))) return mkd(S(0), S(0));
+    S r = ssqrt(a.v);
+    return mkd(r, a.d / (S(2) * r));
+}
+template <class S> __device__ __forceinline__ S act_cbrt(S a) { return scbrt(a); }
+template <class S> __device__ __forceinline__ Dual<S> act_cbrt(Dual<S> a) {
+    if (!(a.v > S(0))) return mkd(S(0), S(0));
+    S r = scbrt(a.v);
+    return mkd(r, a.d / (S(3) * r * r));
+}
+template <class S> __device__ __forceinline__ S srcp(S a) { return S(1) / a; }
+template <class S> __device__ __forceinline__ Dual<S> srcp(Dual<S> a) {
+    S r = S(1) / a.v;
+    return mkd(r, -a.d * r * r);
+}
 
 // max(x, 0) with the branch taken on the value
 template <class S> __device__ __forceinline__ S pos(S x) { return x > S(0) ? x : S(0); }
@@ -203,9 +225,16 @@ __device__ __forceinline__ void sources(const DevParams& p, const T* c, const T*
             T e8 = Make<T>::c(p.eps_frozen[0]), e2 = Make<T>::c(p.eps_frozen[1]);
             aV = specific_surface<T>(p, e8, e2);
         }
-        T la1 = log_act(c[1], p.cref), la2 = log_act(c[2], p.cref);
-        T x1 = eta - Make<T>::c(p.F_2RT * p.U0[0]);
-        T r1 = sexp(la1 * Sc(0.5) - x1) - sexp(la2 * Sc(0.5) + x1);
+        T r1;
+        if constexpr (std::is_same<Sc, double>::value) {
+            T ep = sexp(eta), em = srcp(ep);
+            T s1 = act_sqrt(pos(c[1]) * Sc(1.0 / p.cref)), s2 = act_sqrt(pos(c[2]) * Sc(1.0 / p.cref));
+            r1 = s1 * em * Sc(p.eUf[0]) - s2 * ep * Sc(p.eUb[0]);
+        } else {
+            T la1 = log_act(c[1], p.cref), la2 = log_act(c[2], p.cref);
+            T x1 = eta - Make<T>::c(p.F_2RT * p.U0[0]);
+            r1 = sexp(la1 * Sc(0.5) - x1) - sexp(la2 * Sc(0.5) + x1);
+        }
         T w1 = aV * r1 * Sc(p.kE[0]);
         S[0] = zero;
         S[1] = w1 * Sc(-0.5);
@@ -213,7 +242,50 @@ __device__ __forceinline__ void sources(const DevParams& p, const T* c, const T*
         qS = w1 * Sc(p.F);
         qL = -qS;
         return;
+    } else if constexpr (std::is_same<Sc, double>::value) {
+        // FP64: every e^{-+x_k} is e^{-+eta} times the constant e^{+-F U0_k/(2RT)}, and the
+        // fractional activity powers of Tab. 3 are square and cube roots: one exponential, one
+        // reciprocal, three square roots and three cube roots per point instead of six
+        // logarithms and twelve exponentials.
+        T aV = specific_surface<T>(p, es[0], es[1]);
+        const Sc icr = Sc(1.0 / p.cref);
+        T a0 = pos(c[0]) * icr, a1 = pos(c[1]) * icr, a2 = pos(c[2]) * icr;
+        T a3 = pos(c[3]) * icr, a4 = pos(c[4]) * icr, a5 = pos(c[5]) * icr;
+        T ep = sexp(eta), em = srcp(ep);
+        T s1 = act_sqrt(a1), s2 = act_sqrt(a2), s4 = act_sqrt(a4);
+        T q4 = act_cbrt(s4);                 // a4^{1/6}
+        T q5 = act_cbrt(a5);                 // a5^{1/3}
+        T qL = act_cbrt(a0);                 // a0^{1/3}
+        const Sc th = Sc(p.smooth ? tH : 1.0);
+        T r1 = s1 * em * Sc(p.eUf[0]) - s2 * ep * Sc(p.eUb[0]);
+        T r2 = a2 * s2 * em * Sc(p.eUf[1]) - a3 * a3 * ep * Sc(p.eUb[1]);
+        T r3 = a3 * em * Sc(p.eUf[2]) - a4 * s4 * ep * Sc(p.eUb[2]);
+        T r4 = (q4 * em * Sc(p.eUf[3]) - q5 * q5 * ep * Sc(p.eUb[3])) * th;
+        T r5 = s2 * em * Sc(p.eUf[4]) - a4 * ep * Sc(p.eUb[4]);
+        T r6 = q4 * a0 * qL * em * Sc(p.eUf[5]) - ep * Sc(p.eUb[5]);
+        T rc1 = Make<T>::c(p.sqK[0]) - a1 * Sc(1.0 / p.sqK[0]);
+        T rc2 = (Make<T>::c(p.sqK[1]) - a0 * a0 * a5 * Sc(1.0 / p.sqK[1])) * th;
+        T wc1 = es[0] * rc1 * Sc(p.kC[0]);
+        T wc2 = es[1] * rc2 * Sc(p.kC[1]);
+        T w1 = aV * r1 * Sc(p.kE[0]);
+        T w2 = aV * r2 * Sc(p.kE[1]);
+        T w3 = aV * r3 * Sc(p.kE[2]);
+        T w4 = aV * r4 * Sc(p.kE[3]);
+        T w5 = aV * r5 * Sc(p.kE[4]);
+        T w6 = aV * r6 * Sc(p.kE[5]);
+        S[0] = wc2 * Sc(2.0) - w6 * Sc(4.0 / 3.0);
+        S[1] = wc1 - w1 * Sc(0.5);
+        S[2] = w1 * Sc(0.5) - w2 * Sc(1.5) - w5 * Sc(0.5);
+        S[3] = w2 * Sc(2.0) - w3;
+        S[4] = w3 * Sc(1.5) - w4 * Sc(1.0 / 6.0) + w5 - w6 * Sc(1.0 / 6.0);
+        S[5] = wc2 + w4 * Sc(2.0 / 3.0);
+        Ss[0] = -wc1;
+        Ss[1] = w6 * Sc(2.0 / 3.0) - wc2;
+        qS = (w1 + w2 + w3 + w4 + w5 + w6) * Sc(p.F);
+        qL = -qS;
     } else {
+        // FP32: exponents formed as differences of O(1) numbers, which cannot overflow for the
+        // potentials a Newton iterate may take
         T aV = specific_surface<T>(p, es[0], es[1]);
         T la[6];
 #pragma unroll
