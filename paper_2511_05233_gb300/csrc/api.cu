@@ -451,10 +451,23 @@ static dg_status jvp_(dg_ctx* ctx, const S* z, const S* v, double t, double dt, 
     return DG_OK;
 }
 
+// Diagonal blocks of S J (in FP32 arithmetic when the Krylov loop is FP32: they only precondition),
+// their inverses, and the potential multigrid hierarchy at z.
 static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt, int relax) {
     ProfScope ps(ctx, 2);
-    cudaError_t e = ctx->P.order == 0 ? dg0_blocks(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb)
-                                      : dg1_blocks(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb);
+    cudaError_t e;
+    if (ctx->prm.precision == DG_PREC_MIXED) {
+        e = to_f32(ctx->L, ctx->z32, z, ctx->ndof);
+        if (e == cudaSuccess)
+            e = ctx->P.order == 0 ? dg0_blocks<float>(ctx->L, ctx->P, ctx->G, ctx->z32, t, dt, relax, ctx->blk, ctx->gb32)
+                                  : dg1_blocks<float>(ctx->L, ctx->P, ctx->G, ctx->z32, t, dt, relax, ctx->blk, ctx->gb32);
+        if (e == cudaSuccess && ctx->prm.preconditioner == 1)
+            e = ctx->P.order == 0 ? dg0_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb)
+                                  : dg1_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb);
+    } else {
+        e = ctx->P.order == 0 ? dg0_blocks<double>(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb)
+                              : dg1_blocks<double>(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb);
+    }
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("blocks: ") + cudaGetErrorString(e));
     e = cudaMemsetAsync(ctx->d_bad, 0, sizeof(int), ctx->L.st);
     if (e == cudaSuccess) e = block_invert(ctx->L, ctx->blk, ctx->nblk, ctx->P.nf, ctx->blk32, ctx->d_bad);

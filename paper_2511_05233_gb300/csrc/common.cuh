@@ -255,14 +255,14 @@ __device__ __forceinline__ void sources(const DevParams& p, const T* c, const T*
         T s1 = act_sqrt(a1), s2 = act_sqrt(a2), s4 = act_sqrt(a4);
         T q4 = act_cbrt(s4);                 // a4^{1/6}
         T q5 = act_cbrt(a5);                 // a5^{1/3}
-        T qL = act_cbrt(a0);                 // a0^{1/3}
+        T cLi = act_cbrt(a0);                // a0^{1/3}
         const Sc th = Sc(p.smooth ? tH : 1.0);
         T r1 = s1 * em * Sc(p.eUf[0]) - s2 * ep * Sc(p.eUb[0]);
         T r2 = a2 * s2 * em * Sc(p.eUf[1]) - a3 * a3 * ep * Sc(p.eUb[1]);
         T r3 = a3 * em * Sc(p.eUf[2]) - a4 * s4 * ep * Sc(p.eUb[2]);
         T r4 = (q4 * em * Sc(p.eUf[3]) - q5 * q5 * ep * Sc(p.eUb[3])) * th;
         T r5 = s2 * em * Sc(p.eUf[4]) - a4 * ep * Sc(p.eUb[4]);
-        T r6 = q4 * a0 * qL * em * Sc(p.eUf[5]) - ep * Sc(p.eUb[5]);
+        T r6 = q4 * a0 * cLi * em * Sc(p.eUf[5]) - ep * Sc(p.eUb[5]);
         T rc1 = Make<T>::c(p.sqK[0]) - a1 * Sc(1.0 / p.sqK[0]);
         T rc2 = (Make<T>::c(p.sqK[1]) - a0 * a0 * a5 * Sc(1.0 / p.sqK[1])) * th;
         T wc1 = es[0] * rc1 * Sc(p.kC[0]);

@@ -241,20 +241,20 @@ __global__ void __launch_bounds__(128) k_dg0_jvp(const DevParams p, const Geo g,
 // ------------------------------------------------------------------ diagonal blocks of S J
 // blk[cell][row][col] = dt * rscale[row] * dR_row/dz_col over the voxel's own unknowns; rows
 // and columns of fields the voxel does not carry are the identity.
-template <class Chem>
-__global__ void __launch_bounds__(128) k_dg0_blk(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                 const double* __restrict__ gb, double t, double dt, int relax,
+template <class Chem, class S>
+__global__ void __launch_bounds__(128) k_dg0_blk(const DevParams p, const Geo g, const S* __restrict__ z,
+                                                 const S* __restrict__ gb, double t, double dt, int relax,
                                                  double* __restrict__ blk) {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= p.n_cell) return;
-    typedef Dual<double> T;
+    typedef Dual<S> T;
     constexpr int NF = Chem::NF;
     int i, j, k;
     cell_ijk(p, cell, i, j, k);
     double old[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) old[f] = 0.0;
-    auto getQ = [&](int q, CellVals<Chem, T>& Q) { load_vals<Chem, double, false, false>(p, g, q, z, z, gb, gb, -1, Q); };
+    auto getQ = [&](int q, CellVals<Chem, T>& Q) { load_vals<Chem, S, false, false>(p, g, q, z, z, gb, gb, -1, Q); };
     double tH = smooth_step(t);
     double* B = blk + (int64_t)cell * NF * NF;
     const int ph = g.phase[cell];
@@ -265,12 +265,12 @@ __global__ void __launch_bounds__(128) k_dg0_blk(const DevParams p, const Geo g,
             continue;
         }
         CellVals<Chem, T> P;
-        load_vals<Chem, double, false, true>(p, g, cell, z, z, gb, gb, col, P);
+        load_vals<Chem, S, false, true>(p, g, cell, z, z, gb, gb, col, P);
         T R[NF];
         dg0_cell<Chem, T>(p, i, j, k, P, getQ, old, tH, relax ? tH : 1.0, dt, relax, R);
 #pragma unroll
         for (int row = 0; row < NF; ++row) {
-            double o = R[row].d * dt * p.rscale[row];
+            double o = (double)R[row].d * dt * p.rscale[row];
             if (p.is_struct[row] && ph != 1) o = (row == col) ? 1.0 : 0.0;
             B[row * NF + col] = o;
         }
@@ -313,17 +313,30 @@ template cudaError_t dg0_jvp<double>(const LaunchCtx&, const DevParams&, const G
 template cudaError_t dg0_jvp<float>(const LaunchCtx&, const DevParams&, const Geo&, const float*, const float*,
                                     double, double, int, double, float*, float*, float*);
 
-cudaError_t dg0_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t, double dt,
-                       int relax, double* blk, double* gbuf) {
+template <class S>
+cudaError_t dg0_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, double t, double dt,
+                       int relax, double* blk, S* gbuf) {
     int nb = nblocks(p.n_cell, 128);
     if (p.nf == 10) {
-        k_dg0_g<ChemTO, double, false><<<nb, 128, 0, L.st>>>(p, g, z, z, gbuf, gbuf);
-        k_dg0_blk<ChemTO><<<nb, 128, 0, L.st>>>(p, g, z, gbuf, t, dt, relax, blk);
+        k_dg0_g<ChemTO, S, false><<<nb, 128, 0, L.st>>>(p, g, z, z, gbuf, gbuf);
+        k_dg0_blk<ChemTO, S><<<nb, 128, 0, L.st>>>(p, g, z, gbuf, t, dt, relax, blk);
     } else {
-        k_dg0_g<ChemR3, double, false><<<nb, 128, 0, L.st>>>(p, g, z, z, gbuf, gbuf);
-        k_dg0_blk<ChemR3><<<nb, 128, 0, L.st>>>(p, g, z, gbuf, t, dt, relax, blk);
+        k_dg0_g<ChemR3, S, false><<<nb, 128, 0, L.st>>>(p, g, z, z, gbuf, gbuf);
+        k_dg0_blk<ChemR3, S><<<nb, 128, 0, L.st>>>(p, g, z, gbuf, t, dt, relax, blk);
     }
     *L.counter += 2;
+    return cudaGetLastError();
+}
+template cudaError_t dg0_blocks<double>(const LaunchCtx&, const DevParams&, const Geo&, const double*, double, double,
+                                        int, double*, double*);
+template cudaError_t dg0_blocks<float>(const LaunchCtx&, const DevParams&, const Geo&, const float*, double, double,
+                                       int, double*, float*);
+
+cudaError_t dg0_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double* gbuf) {
+    int nb = nblocks(p.n_cell, 128);
+    if (p.nf == 10) k_dg0_g<ChemTO, double, false><<<nb, 128, 0, L.st>>>(p, g, z, z, gbuf, gbuf);
+    else k_dg0_g<ChemR3, double, false><<<nb, 128, 0, L.st>>>(p, g, z, z, gbuf, gbuf);
+    *L.counter += 1;
     return cudaGetLastError();
 }
 

@@ -438,13 +438,14 @@ __global__ void __launch_bounds__(128) k_dg1_lines(const DevParams p, const Geo 
 // One thread per (node, voxel): for each own unknown (column) seed it, evaluate the node terms and
 // the three lines through the node with the seed (own g values recomputed so that they carry the
 // tangent), and keep the rows of this node.
-template <class Chem>
-__global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                const double* __restrict__ gb, double t, double dt, int relax,
+template <class Chem, class S>
+__global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, const S* __restrict__ z,
+                                                const S* __restrict__ gb, double t, double dt, int relax,
                                                 double* __restrict__ blk) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 8) return;
-    typedef Dual<double> T;
+    typedef Dual<S> T;
+    typedef S Sc;
     constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
     const int n = (int)(b / p.n_cell);
     const int cell = (int)(b - (int64_t)n * p.n_cell);
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, 
             T R[NF];
             node_terms<Chem, T>(p, ph, c, es, phiL, phiS, old, tH, dt, relax, R);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) colv[f] = R[f].d;
+            for (int f = 0; f < NF; ++f) colv[f] = (double)R[f].d;
         }
         // the three lines through node n
 #pragma unroll 1
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, 
             int n0, n1;
             line_nodes(d, q, n0, n1);
             Line<Chem, T> P;
-            load_line<Chem, T, double>(p, z, z, false, cell, sidx, st, n0, n1, n, col, P);
+            load_line<Chem, T, S>(p, z, z, false, cell, sidx, st, n0, n1, n, col, P);
             // own g at the nodes and at the two face points of the line, with the seed
             T es2[2][2];
             for (int a = 0; a < 2; ++a) {
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, 
                 gN[a] = transport_factor<Chem, T>(p, eL, P.c[a]);
             }
             for (int s2 = 0; s2 < 2; ++s2) {
-                const double wn = s2 == 1 ? ALPHA : BETA, wfar = s2 == 1 ? BETA : ALPHA;
+                const Sc wn = Sc(s2 == 1 ? ALPHA : BETA), wfar = Sc(s2 == 1 ? BETA : ALPHA);
                 T ct[NL], et[2];
                 for (int m = 0; m < NL; ++m) ct[m] = P.c[1][m] * wn + P.c[0][m] * wfar;
                 et[0] = es2[1][0] * wn + es2[0][0] * wfar;
@@ -530,7 +531,7 @@ __global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, 
                 if (hasQ[sd]) {
                     int qcell = cell + (sd == 0 ? -stride : stride);
                     stQ[sd] = g.phase[qcell] == 1;
-                    load_line<Chem, T, double>(p, z, z, false, qcell, g.cmap[qcell], stQ[sd], n0, n1, -1, -1, Q[sd]);
+                    load_line<Chem, T, S>(p, z, z, false, qcell, g.cmap[qcell], stQ[sd], n0, n1, -1, -1, Q[sd]);
                     gQ[sd] = Make<T>::c(gb[(int64_t)face_slot(d, sd == 0 ? +1 : -1, q) * p.n_cell + qcell]);
                 }
             }
@@ -540,7 +541,7 @@ __global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, 
             const int a = (n == n1) ? 1 : 0;
             for (int e = 0; e < NL + 2; ++e) {
                 int f = e < NL ? e : (e == NL ? PHIL : PHIS);
-                colv[f] += acc[a][e].d;
+                colv[f] += (double)acc[a][e].d;
             }
         }
 #pragma unroll
@@ -596,16 +597,28 @@ template cudaError_t dg1_jvp<double>(const LaunchCtx&, const DevParams&, const G
 template cudaError_t dg1_jvp<float>(const LaunchCtx&, const DevParams&, const Geo&, const float*, const float*, double,
                                     double, int, double, float*, float*, float*);
 
-cudaError_t dg1_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t, double dt,
-                       int relax, double* blk, double* gb) {
+template <class S>
+cudaError_t dg1_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, double t, double dt,
+                       int relax, double* blk, S* gb) {
     if (p.nf == 10) {
-        k_dg1_g<ChemTO, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
-        k_dg1_blk<ChemTO><<<nblocks((int64_t)p.n_cell * 8, 64), 64, 0, L.st>>>(p, g, z, gb, t, dt, relax, blk);
+        k_dg1_g<ChemTO, S, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
+        k_dg1_blk<ChemTO, S><<<nblocks((int64_t)p.n_cell * 8, 64), 64, 0, L.st>>>(p, g, z, gb, t, dt, relax, blk);
     } else {
-        k_dg1_g<ChemR3, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
-        k_dg1_blk<ChemR3><<<nblocks((int64_t)p.n_cell * 8, 64), 64, 0, L.st>>>(p, g, z, gb, t, dt, relax, blk);
+        k_dg1_g<ChemR3, S, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
+        k_dg1_blk<ChemR3, S><<<nblocks((int64_t)p.n_cell * 8, 64), 64, 0, L.st>>>(p, g, z, gb, t, dt, relax, blk);
     }
     *L.counter += 2;
+    return cudaGetLastError();
+}
+template cudaError_t dg1_blocks<double>(const LaunchCtx&, const DevParams&, const Geo&, const double*, double, double,
+                                        int, double*, double*);
+template cudaError_t dg1_blocks<float>(const LaunchCtx&, const DevParams&, const Geo&, const float*, double, double,
+                                       int, double*, float*);
+
+cudaError_t dg1_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double* gb) {
+    if (p.nf == 10) k_dg1_g<ChemTO, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
+    else k_dg1_g<ChemR3, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
+    *L.counter += 1;
     return cudaGetLastError();
 }
 

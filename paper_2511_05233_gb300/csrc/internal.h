@@ -44,8 +44,10 @@ cudaError_t dg0_residual(const LaunchCtx& L, const DevParams& p, const Geo& g, c
 template <class S>
 cudaError_t dg0_jvp(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v,
                     double t, double dt, int relax, double out_scale_dt, S* out, S* gbuf, S* gbuf_d);
-cudaError_t dg0_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
-                       double t, double dt, int relax, double* blk, double* gbuf);
+template <class S>
+cudaError_t dg0_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z,
+                       double t, double dt, int relax, double* blk, S* gbuf);
+cudaError_t dg0_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double* gbuf);
 
 // ------------------------------------------------------------------ DG1 (dg1.cu)
 cudaError_t dg1_residual(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
@@ -53,8 +55,10 @@ cudaError_t dg1_residual(const LaunchCtx& L, const DevParams& p, const Geo& g, c
 template <class S>
 cudaError_t dg1_jvp(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v,
                     double t, double dt, int relax, double out_scale_dt, S* out, S* fbuf, S* fbuf_d);
-cudaError_t dg1_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
-                       double t, double dt, int relax, double* blk, double* fbuf);
+template <class S>
+cudaError_t dg1_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z,
+                       double t, double dt, int relax, double* blk, S* fbuf);
+cudaError_t dg1_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double* fbuf);
 int64_t dg1_face_buffer_len(const DevParams& p);
 
 // ------------------------------------------------------------------ linear algebra (la.cu)

@@ -136,21 +136,23 @@ template <class S, int KM>
 __global__ void __launch_bounds__(RED_THREADS) k_mdot(const S* __restrict__ V, int64_t ld, int64_t n, int k,
                                                       const S* __restrict__ w, double* __restrict__ partial) {
     __shared__ double sh[RED_THREADS];
-    double acc[KM];
+    // per-thread partial sums in the basis precision (FP32 FMAs for an FP32 basis: on GB300 an
+    // FP64 FMA per 4-byte element would make this pass FP64-bound), block and grid sums in FP64
+    S acc[KM];
 #pragma unroll
-    for (int v = 0; v < KM; ++v) acc[v] = 0.0;
+    for (int v = 0; v < KM; ++v) acc[v] = S(0);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double wi = (double)w[i];
+        S wi = w[i];
 #pragma unroll
         for (int v = 0; v < KM; ++v)
-            if (v < k) acc[v] += (double)V[(int64_t)v * ld + i] * wi;
+            if (v < k) acc[v] += V[(int64_t)v * ld + i] * wi;
     }
 #pragma unroll 1
     for (int v = 0; v < k; ++v) {
         double a = 0.0;
 #pragma unroll
         for (int u = 0; u < KM; ++u)
-            if (u == v) a = acc[u];
+            if (u == v) a = (double)acc[u];
         double s = block_sum(a, sh);
         if (threadIdx.x == 0) partial[(int64_t)v * gridDim.x + blockIdx.x] = s;
     }
@@ -173,13 +175,13 @@ template cudaError_t mdot<float>(const LaunchCtx&, const float*, int64_t, int64_
 template <class S>
 __global__ void __launch_bounds__(256) k_maxpy(S* __restrict__ w, const S* __restrict__ V, int64_t ld, int64_t n, int k,
                                                const double* __restrict__ h, double sign) {
-    __shared__ double hs[MAXK];
-    if (threadIdx.x < k) hs[threadIdx.x] = sign * h[threadIdx.x];
+    __shared__ S hs[MAXK];
+    if (threadIdx.x < k) hs[threadIdx.x] = (S)(sign * h[threadIdx.x]);
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double acc = (double)w[i];
-        for (int v = 0; v < k; ++v) acc += hs[v] * (double)V[(int64_t)v * ld + i];
-        w[i] = (S)acc;
+        S acc = w[i];
+        for (int v = 0; v < k; ++v) acc += hs[v] * V[(int64_t)v * ld + i];
+        w[i] = acc;
     }
 }
 
@@ -198,8 +200,9 @@ __global__ void k_scale_copy(S* __restrict__ dst, const S* __restrict__ src, int
                              double a) {
     double f = a;
     if (nrm2) f = a / sqrt(*nrm2);
+    const S fs = (S)f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = (S)((double)src[i] * f);
+        dst[i] = src[i] * fs;
 }
 
 template <class S>
@@ -283,8 +286,9 @@ cudaError_t axpby(const LaunchCtx& L, double* y, double a, const double* x, doub
 
 template <class S>
 __global__ void k_saxpby(S* __restrict__ y, double a, const S* __restrict__ x, double b, int64_t n) {
+    const S as = (S)a, bs = (S)b;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = (S)(a * (double)y[i] + b * (double)x[i]);
+        y[i] = as * y[i] + bs * x[i];
 }
 template <class S>
 cudaError_t saxpby(const LaunchCtx& L, S* y, double a, const S* x, double b, int64_t n) {

@@ -1,0 +1,68 @@
+"""Run one kind of library call repeatedly on a seeded workload, for kernel timing and profiling.
+
+    python -m paper_2511_05233_gb300.kernel_driver --n 64 --order 1 --chem tradeoff --op jvp --reps 5
+
+Prints the mean device time per call (CUDA events on the library's stream).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--order", type=int, default=1)
+    ap.add_argument("--chem", default="tradeoff")
+    ap.add_argument("--porosity", type=float, default=0.5)
+    ap.add_argument("--op", default="jvp", choices=["residual", "jvp", "step"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--reps", type=int, default=5)
+    a = ap.parse_args()
+    import torch
+
+    from . import dgls, inputs
+
+    phase = inputs.make_structure(a.n, a.porosity, 4.0, 3)
+    chem = dgls.TRADEOFF if a.chem == "tradeoff" else dgls.REDUCED3
+    prm = dgls.default_params(chem, a.order, eps_struct=1 - a.porosity,
+                              precision=dgls.MIXED if a.precision == "mixed" else dgls.FP64)
+    ctx = dgls.Context(phase, 1e-6, prm)
+    N = ctx.n_dof
+    z0 = ctx.new_state()
+    ctx.equilibrium_state(z0)
+    noise = torch.from_numpy(inputs.uniform_noise(N, 4)).cuda()
+    nl = 6 if a.chem == "tradeoff" else 3
+    z = z0.clone()
+    z[: ctx.offsets[nl]] *= 1.0 + 0.01 * noise[: ctx.offsets[nl]]
+    v = torch.from_numpy(inputs.normal_noise(N, 5)).cuda() * (z.abs() + 1e-3)
+    out = torch.empty_like(z)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def call():
+        if a.op == "residual":
+            ctx.residual(z, z0, 1e-3, 1e-3, out)
+        elif a.op == "jvp":
+            ctx.jvp(z, 1e-3, 1e-3, v, out)
+        else:
+            ctx.step(z, out, 0.0, 1e-3, check=False)
+
+    call()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(a.reps):
+        call()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    print(json.dumps({"op": a.op, "n": a.n, "order": a.order, "chem": a.chem, "precision": a.precision,
+                      "n_dof": N, "ms_per_call": ms, "gdof_per_s": N / (ms / 1e3) / 1e9,
+                      "finite": bool(np.isfinite(out.cpu().numpy()).all())}))
+
+
+if __name__ == "__main__":
+    main()
