@@ -34,7 +34,7 @@ def parse():
     ap.add_argument("--order", type=int, default=WORKLOAD["order"])
     ap.add_argument("--chem", default=WORKLOAD["chem"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--precond", default="cpr", choices=["cpr", "bj"])
+    ap.add_argument("--precond", default="cpr", choices=["cpr", "bj", "add"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -195,7 +195,7 @@ def main():
     chem = dgls.TRADEOFF if a.chem == "tradeoff" else dgls.REDUCED3
     prm = dgls.default_params(chem, a.order, f_C=WORKLOAD["f_C"], eps_struct=1 - WORKLOAD["porosity"],
                               precision=dgls.MIXED if a.precision == "mixed" else dgls.FP64,
-                              preconditioner=1 if a.precond == "cpr" else 0)
+                              preconditioner={"bj": 0, "cpr": 1, "add": 2}[a.precond])
     stream = torch.cuda.current_stream()
     ctx = dgls.Context(phase, WORKLOAD["h"], prm, stream)
     N = ctx.n_dof

@@ -377,7 +377,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         AL(V, (int64_t)(m + 1) * N); AL(w, N); AL(u, N); AL(x, N); AL(y1, N); AL(t2, N);
         ctx->V = V; ctx->w = w; ctx->u = u; ctx->x = x; ctx->y1 = y1; ctx->t2 = t2;
     }
-    if (prm->preconditioner == 1 && mg_levels_alloc(ctx->mg, nx, ny, nz, ctx->allocs, &ctx->ws_bytes) != cudaSuccess) {
+    if (prm->preconditioner != 0 && mg_levels_alloc(ctx->mg, nx, ny, nz, ctx->allocs, &ctx->ws_bytes) != cudaSuccess) {
         free_all(ctx);
         delete ctx;
         return DG_ERR_OOM;
@@ -461,7 +461,7 @@ static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt
         if (e == cudaSuccess)
             e = ctx->P.order == 0 ? dg0_blocks<float>(ctx->L, ctx->P, ctx->G, ctx->z32, t, dt, relax, ctx->blk, ctx->gb32)
                                   : dg1_blocks<float>(ctx->L, ctx->P, ctx->G, ctx->z32, t, dt, relax, ctx->blk, ctx->gb32);
-        if (e == cudaSuccess && ctx->prm.preconditioner == 1)
+        if (e == cudaSuccess && ctx->prm.preconditioner != 0)
             e = ctx->P.order == 0 ? dg0_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb)
                                   : dg1_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb);
     } else {
@@ -472,7 +472,7 @@ static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt
     e = cudaMemsetAsync(ctx->d_bad, 0, sizeof(int), ctx->L.st);
     if (e == cudaSuccess) e = block_invert(ctx->L, ctx->blk, ctx->nblk, ctx->P.nf, ctx->blk32, ctx->d_bad);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
-    if (ctx->prm.preconditioner == 1) {
+    if (ctx->prm.preconditioner != 0) {
         e = mg_setup(ctx->L, ctx->P, ctx->G, z, ctx->gb, t, dt, relax, ctx->mg);
         if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("multigrid setup: ") + cudaGetErrorString(e));
     }
@@ -486,13 +486,19 @@ static dg_status precond_apply_(dg_ctx* ctx, const S* v, S* u, const S* zS, doub
                                 S* gbdS, const void* blkS) {
     ProfScope ps(ctx, 3);
     const int64_t N = ctx->ndof;
-    if (ctx->prm.preconditioner != 1) {
+    if (ctx->prm.preconditioner == 0) {
         CK(block_apply<S>(ctx->L, ctx->P, ctx->G, blkS, v, u));
         return DG_OK;
     }
     S* y1 = (S*)ctx->y1;
     S* t2 = (S*)ctx->t2;
     CK(cpr_stage1<S>(ctx->L, ctx->P, ctx->G, ctx->mg, ctx->prm.mg_cycles, v, y1));
+    if (ctx->prm.preconditioner == 2) {
+        // additive form: u = B^{-1} v + P MG(R v) (no Jacobian-vector product)
+        CK(block_apply<S>(ctx->L, ctx->P, ctx->G, blkS, v, u));
+        CK(saxpby<S>(ctx->L, u, 1.0, y1, 1.0, N));
+        return DG_OK;
+    }
     cudaError_t e = ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, zS, y1, t, dt, relax, dt, t2, gbS, gbdS)
                                       : dg1_jvp<S>(ctx->L, ctx->P, ctx->G, zS, y1, t, dt, relax, dt, t2, gbS, gbdS);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("jvp: ") + cudaGetErrorString(e));

@@ -149,10 +149,19 @@ template <class S> __device__ __forceinline__ Dual<S> log_act(Dual<S> c, double 
 }
 
 // {a, b}_H = 2ab/(a+b) (Eq. 45), 0 unless ab > 0
-template <class T> __device__ __forceinline__ T harm(T a, T b) {
-    typedef typename Base<T>::type S;
-    if (val(a) * val(b) > S(0)) return (S(2) * a * b) / (a + b);
-    return Make<T>::c(0.0);
+template <class S> __device__ __forceinline__ S harm(S a, S b) {
+    if (a * b > S(0)) return (S(2) * a * b) / (a + b);
+    return S(0);
+}
+// dual version with one division: dH = 2 (b^2 da + a^2 db) / (a + b)^2
+template <class S> __device__ __forceinline__ Dual<S> harm(Dual<S> a, Dual<S> b) {
+    if (a.v * b.v > S(0)) {
+        S r = S(1) / (a.v + b.v);
+        S h = S(2) * a.v * b.v * r;
+        S d = S(2) * r * r * (b.v * b.v * a.d + a.v * a.v * b.d);
+        return mkd(h, d);
+    }
+    return mkd(S(0), S(0));
 }
 
 // T_H(t) of Eq. 56

@@ -79,11 +79,11 @@ __global__ void __launch_bounds__(128) k_dg1_g(const DevParams p, const Geo g, c
         gb[(int64_t)n * p.n_cell + cell] = val(gg);
         if constexpr (TAN) gbd[(int64_t)n * p.n_cell + cell] = gg.d;
     }
-#pragma unroll 1
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-#pragma unroll 1
+#pragma unroll
         for (int side = -1; side <= 1; side += 2) {
-#pragma unroll 1
+#pragma unroll
             for (int q = 0; q < 4; ++q) {
                 int n0, n1;
                 line_nodes(d, q, n0, n1);
@@ -365,6 +365,9 @@ __device__ __forceinline__ void line_boundary(const DevParams& p, const Line<Che
     }
 }
 
+// One thread per (line, voxel) of direction d.  The fields are streamed one at a time (register
+// pressure: the whole line with both neighbours would hold ~100 dual numbers), each field's two
+// nodal outputs are read-modify-written as soon as they are complete.
 template <class Chem, class S, int MODE>    // MODE 0 residual, 1 JVP tangent
 __global__ void __launch_bounds__(128) k_dg1_lines(const DevParams p, const Geo g, const S* __restrict__ z,
                                                    const S* __restrict__ v, const S* __restrict__ gb,
@@ -373,6 +376,7 @@ __global__ void __launch_bounds__(128) k_dg1_lines(const DevParams p, const Geo 
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 4) return;
     typedef typename std::conditional<MODE == 1, Dual<S>, S>::type T;
+    typedef S Sc;
     constexpr int NL = Chem::NL;
     const bool tan = MODE == 1;
     const int q = (int)(b / p.n_cell);
@@ -384,53 +388,167 @@ __global__ void __launch_bounds__(128) k_dg1_lines(const DevParams p, const Geo 
     const int ph = g.phase[cell];
     const int sidx = g.cmap[cell];
     const bool st = ph == 1;
-    Line<Chem, T> P;
-    load_line<Chem, T, S>(p, z, v, tan, cell, sidx, st, n0, n1, -1, -1, P);
+    const Sc vol = Sc(3.0 * p.h / 8.0);
+    const Sc wf = Sc(0.25 * p.h * p.h);
+    const Sc gq = Sc(SQ3 / p.h);
+    const Sc pen = Sc(p.penalty / p.h);
+    const Sc al = Sc(ALPHA), be = Sc(BETA);
+
     auto gload = [&](int slot, int c) -> T {
         int64_t o = (int64_t)slot * p.n_cell + c;
         return Make<T>::var(gb[o], tan ? (double)gbd[o] : 0.0);
     };
-    T gN[2] = {gload(n0, cell), gload(n1, cell)};
-    T gP[2] = {gload(face_slot(d, -1, q), cell), gload(face_slot(d, +1, q), cell)};
-    Line<Chem, T> Q[2];
-    T gQ[2];
-    bool hasQ[2], stQ[2];
+    auto fld = [&](int f, int n, int idx) -> T {
+        int64_t o = p.off[f] + (int64_t)n * p.flen[f] + idx;
+        return Make<T>::var(z[o], tan ? (double)v[o] : 0.0);
+    };
+    // neighbours along d: side 0 = xi = -1 face (left), side 1 = xi = +1 face (right)
     const int coord = d == 0 ? i : d == 1 ? j : k;
     const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
     const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+    bool hasQ[2], stQ[2];
+    int qcell[2], qsidx[2];
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
         int qc = coord + (sd == 0 ? -1 : 1);
         hasQ[sd] = qc >= 0 && qc < ext;
-        stQ[sd] = false;
-        gQ[sd] = Make<T>::c(0.0);
-        if (hasQ[sd]) {
-            int qcell = cell + (sd == 0 ? -stride : stride);
-            int qph = g.phase[qcell];
-            stQ[sd] = qph == 1;
-            load_line<Chem, T, S>(p, z, v, tan, qcell, g.cmap[qcell], stQ[sd], n0, n1, -1, -1, Q[sd]);
-            gQ[sd] = gload(face_slot(d, sd == 0 ? +1 : -1, q), qcell);
-        }
+        qcell[sd] = hasQ[sd] ? cell + (sd == 0 ? -stride : stride) : cell;
+        stQ[sd] = hasQ[sd] && g.phase[qcell[sd]] == 1;
+        qsidx[sd] = hasQ[sd] ? g.cmap[qcell[sd]] : -1;
     }
-    T acc[2][NL + 2];
-    line_terms<Chem, T>(p, P, gN, gP, st, Q, gQ, hasQ, stQ, relax, acc);
-    line_boundary<Chem, T>(p, P, d, i, st, relax ? smooth_step(t) : 1.0, relax, acc);
-    const int nodes[2] = {n0, n1};
+    // transport factors: nodes, own face points, neighbour face points; face harmonic means
+    const T gN0 = gload(n0, cell), gN1 = gload(n1, cell);
+    const T gsum = gN0 + gN1;
+    T gl[2], gr[2], Hg[2];
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
+    for (int sd = 0; sd < 2; ++sd) {
+        Hg[sd] = Make<T>::c(0.0);
+        gl[sd] = gr[sd] = Make<T>::c(0.0);
+        if (!hasQ[sd]) continue;
+        T gP = gload(face_slot(d, sd == 0 ? -1 : +1, q), cell);
+        T gQ = gload(face_slot(d, sd == 0 ? +1 : -1, q), qcell[sd]);
+        gl[sd] = sd == 1 ? gP : gQ;
+        gr[sd] = sd == 1 ? gQ : gP;
+        Hg[sd] = harm(gl[sd], gr[sd]);
+    }
+    // liquid potential along the line: volume difference, face jumps (left minus right) and mean
+    // normal gradients
+    const T PL0 = fld(Chem::PHIL, n0, cell), PL1 = fld(Chem::PHIL, n1, cell);
+    const T dPhi = PL1 - PL0;
+    T jL[2], mL[2];
 #pragma unroll
-        for (int e = 0; e < NL + 2; ++e) {
-            int f = e < NL ? e : (e == NL ? Chem::PHIL : Chem::PHIS);
-            if (f == Chem::PHIS && !st) continue;
-            int64_t o = p.off[f] + (int64_t)nodes[a] * p.flen[f] + (f == Chem::PHIS ? sidx : cell);
-            if constexpr (MODE == 1) {
-                S add = acc[a][e].d;
-                if (sc_dt > 0.0) add = add * S(sc_dt * p.rscale[f]);
-                r[o] += add;
-            } else {
-                r[o] += acc[a][e];
-            }
+    for (int sd = 0; sd < 2; ++sd) {
+        jL[sd] = mL[sd] = Make<T>::c(0.0);
+        if (!hasQ[sd]) continue;
+        T Q0 = fld(Chem::PHIL, n0, qcell[sd]), Q1 = fld(Chem::PHIL, n1, qcell[sd]);
+        T tP = sd == 1 ? PL1 * al + PL0 * be : PL0 * al + PL1 * be;     // own trace at this face
+        T tN = sd == 1 ? Q0 * al + Q1 * be : Q1 * al + Q0 * be;         // neighbour trace
+        jL[sd] = sd == 1 ? tP - tN : tN - tP;
+        mL[sd] = (dPhi + (Q1 - Q0)) * (gq * Sc(0.5));
+    }
+    T accL0 = Make<T>::c(0.0), accL1 = Make<T>::c(0.0);
+    auto add_face = [&](int sd, T f, T& a0, T& a1) {
+        // left cell gets +f v-, right cell -f v+; the own near node is index sd
+        T ff = f * (sd == 1 ? wf : -wf);
+        if (sd == 1) { a1 += ff * al; a0 += ff * be; }
+        else { a0 += ff * al; a1 += ff * be; }
+    };
+    auto store = [&](int f, int idx, T a0, T a1) {
+        int64_t o0 = p.off[f] + (int64_t)n0 * p.flen[f] + idx;
+        int64_t o1 = p.off[f] + (int64_t)n1 * p.flen[f] + idx;
+        if constexpr (MODE == 1) {
+            S s0 = a0.d, s1 = a1.d;
+            if (sc_dt > 0.0) { S sc = S(sc_dt * p.rscale[f]); s0 *= sc; s1 *= sc; }
+            r[o0] += s0;
+            r[o1] += s1;
+        } else {
+            r[o0] += a0;
+            r[o1] += a1;
         }
+    };
+#pragma unroll 1
+    for (int m = 0; m < NL; ++m) {
+        const bool charged = p.zc[m] != 0.0;
+        const T C0 = fld(m, n0, cell), C1 = fld(m, n1, cell);
+        const T dc = C1 - C0;
+        T a0 = Make<T>::c(0.0), a1 = Make<T>::c(0.0);
+        // volume term of the line
+        {
+            T fl = Make<T>::c(0.0);
+            if (!relax) fl = gsum * dc * Sc(p.D0[m]);
+            if (charged) {
+                T msum = gN0 * C0 + gN1 * C1;
+                if (!relax) fl += msum * dPhi * Sc(p.kappa_m[m]);
+                T fL = (gsum * dc * Sc(p.Kd[m]) + msum * dPhi * Sc(p.Km[m])) * vol;
+                accL1 += fL;
+                accL0 -= fL;
+            }
+            fl = fl * vol;
+            a1 += fl;
+            a0 -= fl;
+        }
+        // faces
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            if (!hasQ[sd]) continue;
+            T Q0 = fld(m, n0, qcell[sd]), Q1 = fld(m, n1, qcell[sd]);
+            T tP = sd == 1 ? C1 * al + C0 * be : C0 * al + C1 * be;
+            T tN = sd == 1 ? Q0 * al + Q1 * be : Q1 * al + Q0 * be;
+            T jc = sd == 1 ? tP - tN : tN - tP;
+            T mc = (dc + (Q1 - Q0)) * (gq * Sc(0.5));
+            T dterm = (jc * pen - mc) * Hg[sd];
+            T f = Make<T>::c(0.0);
+            if (!relax) f = dterm * Sc(p.D0[m]);
+            if (charged) {
+                T cl = sd == 1 ? tP : tN;
+                T cr = sd == 1 ? tN : tP;
+                T Hm = harm(gl[sd] * cl, gr[sd] * cr);
+                T mterm = (jL[sd] * pen - mL[sd]) * Hm;
+                if (!relax) f += mterm * Sc(p.kappa_m[m]);
+                add_face(sd, dterm * Sc(p.Kd[m]) + mterm * Sc(p.Km[m]), accL0, accL1);
+            }
+            add_face(sd, f, a0, a1);
+        }
+        // anode exchange on the x = nx face (Li+ row and, below, the Phi^L row)
+        if (m == 0 && d == 0 && i == p.nx - 1) {
+            T cLi = C1 * al + C0 * be;
+            T phL = PL1 * al + PL0 * be;
+            T rA = anode_rate<T>(p, cLi, phL);
+            if (!relax) {
+                T fLi = rA * (wf * Sc(p.kAno));
+                a1 += fLi * al;
+                a0 += fLi * be;
+            }
+            T fL = rA * (wf * Sc(p.F * p.kAno));
+            accL1 += fL * al;
+            accL0 += fL * be;
+        }
+        store(m, cell, a0, a1);
+    }
+    store(Chem::PHIL, cell, accL0, accL1);
+    // solid potential (structure voxels only)
+    if (st) {
+        const T S0 = fld(Chem::PHIS, n0, sidx), S1 = fld(Chem::PHIS, n1, sidx);
+        T a0 = Make<T>::c(0.0), a1 = Make<T>::c(0.0);
+        T fs = (S1 - S0) * (Sc(2.0 * p.kappa_s) * vol);
+        a1 += fs;
+        a0 -= fs;
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            if (!hasQ[sd] || !stQ[sd]) continue;
+            T Q0 = fld(Chem::PHIS, n0, qsidx[sd]), Q1 = fld(Chem::PHIS, n1, qsidx[sd]);
+            T tP = sd == 1 ? S1 * al + S0 * be : S0 * al + S1 * be;
+            T tN = sd == 1 ? Q0 * al + Q1 * be : Q1 * al + Q0 * be;
+            T jS = sd == 1 ? tP - tN : tN - tP;
+            T mS = ((S1 - S0) + (Q1 - Q0)) * (gq * Sc(0.5));
+            add_face(sd, (jS * pen - mS) * Sc(p.kappa_s), a0, a1);
+        }
+        if (d == 0 && i == 0) {
+            double fj = 0.25 * p.h * p.h * p.j_cc * (relax ? smooth_step(t) : 1.0);
+            a0 += Make<T>::c(fj * ALPHA);
+            a1 += Make<T>::c(fj * BETA);
+        }
+        store(Chem::PHIS, sidx, a0, a1);
     }
 }
 

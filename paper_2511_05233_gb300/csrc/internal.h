@@ -28,6 +28,7 @@ struct MGLevel {
     double* x;     // [2][n]
     double* xt;    // [2][n]
     double* b;     // [2][n]
+    double* dense; // coarsest level only: [2n][4n] Gauss-Jordan workspace, right half = A^{-1}
 };
 
 // Launch counter increment hook (owned by the context).

@@ -17,7 +17,7 @@
 // Hierarchy: 2 x 2 x 2 aggregation with piecewise-constant interpolation (the Galerkin coarse
 // operator of a graph Laplacian is the aggregated graph Laplacian: coarse conductances are sums of
 // the fine conductances crossing aggregate boundaries); damped 2 x 2 block-Jacobi smoothing;
-// the coarsest level (<= 512 voxels) is relaxed by one thread block.
+// the coarsest level (<= 64 voxels) is solved exactly with a dense inverse.
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -308,26 +308,75 @@ __global__ void k_mg_prolong(MGLevel F, MGLevel C) {
     if (F.st[f]) F.x[(int64_t)F.n + f] += C.x[(int64_t)C.n + c];
 }
 
-// coarsest level: damped Jacobi sweeps by one thread block (n <= 1024)
-__global__ void __launch_bounds__(1024) k_mg_coarse(MGLevel L, int sweeps, double w) {
-    const int c = threadIdx.x;
-    const int64_t n = L.n;
-    double* x = L.x;
-    double* y = L.xt;
-    if (c < n) { x[c] = 0.0; x[n + c] = 0.0; }
+// coarsest level (n <= 64 voxels, 2n <= 128 unknowns): dense inverse by Gauss-Jordan in one
+// thread block at set-up (the operator is a symmetric M-matrix, so no pivoting is needed), one
+// dense matrix-vector product per V-cycle.
+__global__ void __launch_bounds__(128) k_mg_dense_build(MGLevel L) {
+    __shared__ double piv[256];
+    const int m = 2 * L.n;                 // unknowns: L fields 0..n-1, S fields n..2n-1
+    const int r = threadIdx.x;
+    double* A = L.dense;                   // [m][2m]: [A | I] row-major
+    if (r < m) {
+        for (int c = 0; c < 2 * m; ++c) A[r * 2 * m + c] = 0.0;
+        const int cell = r < L.n ? r : r - L.n;
+        const bool isL = r < L.n;
+        // column of A applied to unit vectors: use apply_A on basis vectors is O(m^2); build directly
+        int i, j, k;
+        ijk(cell, L.nx, L.ny, i, j, k);
+        const int64_t n = L.n;
+        const double* G = isL ? L.gL : L.gS;
+        double diag = 0.0;
+        auto nbr = [&](int q, double g) {
+            if (g == 0.0) return;
+            diag += g;
+            A[r * 2 * m + (isL ? q : n + q)] -= g;
+        };
+        if (i + 1 < L.nx) nbr(cell + 1, G[cell]);
+        if (j + 1 < L.ny) nbr(cell + L.nx, G[n + cell]);
+        if (k + 1 < L.nz) nbr(cell + L.nx * L.ny, G[2 * n + cell]);
+        if (i > 0) nbr(cell - 1, G[cell - 1]);
+        if (j > 0) nbr(cell - L.nx, G[n + cell - L.nx]);
+        if (k > 0) nbr(cell - L.nx * L.ny, G[2 * n + cell - L.nx * L.ny]);
+        const double a = L.a[cell];
+        if (isL) {
+            A[r * 2 * m + r] += diag + a + L.dL[cell];
+            A[r * 2 * m + n + cell] -= a;
+        } else if (L.st[cell]) {
+            A[r * 2 * m + r] += diag + a + L.dS[cell];
+            A[r * 2 * m + cell] -= a;
+        } else {
+            for (int c = 0; c < m; ++c) A[r * 2 * m + c] = 0.0;
+            A[r * 2 * m + r] = 1.0;
+        }
+        A[r * 2 * m + m + r] = 1.0;
+    }
     __syncthreads();
-    for (int s = 0; s < sweeps; ++s) {
-        if (c < n) {
-            double yl, ys;
-            apply_A(L, x, c, yl, ys);
-            double rl = L.b[c] - yl, rs = L.b[n + c] - ys;
-            y[c] = x[c] + w * (L.dinv[c] * rl + L.dinv[n + c] * rs);
-            y[n + c] = x[n + c] + w * (L.dinv[2 * n + c] * rl + L.dinv[3 * n + c] * rs);
+    for (int kk = 0; kk < m; ++kk) {
+        if (r < 2 * m) piv[r] = A[kk * 2 * m + r];
+        if (r + 128 < 2 * m) piv[r + 128] = A[kk * 2 * m + r + 128];
+        __syncthreads();
+        if (r < m && r != kk) {
+            double f = A[r * 2 * m + kk] / piv[kk];
+            if (f != 0.0)
+                for (int c = 0; c < 2 * m; ++c) A[r * 2 * m + c] -= f * piv[c];
         }
         __syncthreads();
-        if (c < n) { x[c] = y[c]; x[n + c] = y[n + c]; }
+        if (r == kk) {
+            double d = 1.0 / piv[kk];
+            for (int c = 0; c < 2 * m; ++c) A[r * 2 * m + c] *= d;
+        }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(128) k_mg_dense_solve(MGLevel L) {
+    const int m = 2 * L.n;
+    const int r = threadIdx.x;
+    if (r >= m) return;
+    const double* A = L.dense;
+    double acc = 0.0;
+    for (int c = 0; c < m; ++c) acc += A[r * 2 * m + m + c] * L.b[c];
+    L.x[r] = acc;
 }
 
 // ------------------------------------------------------------------ CPR restriction / prolongation
@@ -395,8 +444,10 @@ cudaError_t mg_levels_alloc(std::vector<MGLevel>& lv, int nx, int ny, int nz, st
         if ((e = al(&L.x, 2 * (int64_t)L.n)) != cudaSuccess) return e;
         if ((e = al(&L.xt, 2 * (int64_t)L.n)) != cudaSuccess) return e;
         if ((e = al(&L.b, 2 * (int64_t)L.n)) != cudaSuccess) return e;
+        const bool last = L.n <= 64 || (x == 1 && y == 1 && zz == 1);
+        if (last && (e = al(&L.dense, (int64_t)(2 * L.n) * (4 * L.n))) != cudaSuccess) return e;
         lv.push_back(L);
-        if (L.n <= 512 || (x == 1 && y == 1 && zz == 1)) break;
+        if (last) break;
         x = (x + 1) / 2;
         y = (y + 1) / 2;
         zz = (zz + 1) / 2;
@@ -423,6 +474,8 @@ cudaError_t mg_setup(const LaunchCtx& Lc, const DevParams& p, const Geo& g, cons
         k_mg_diag<<<nb(L.n, 256), 256, 0, Lc.st>>>(L);
         *Lc.counter += 1;
     }
+    k_mg_dense_build<<<1, 128, 0, Lc.st>>>(lv.back());
+    *Lc.counter += 1;
     return cudaGetLastError();
 }
 
@@ -430,7 +483,7 @@ static void vcycle(const LaunchCtx& Lc, std::vector<MGLevel>& lv, size_t l) {
     MGLevel& L = lv[l];
     const double w = 0.8;
     if (l + 1 == lv.size()) {
-        k_mg_coarse<<<1, 1024, 0, Lc.st>>>(L, 60, w);
+        k_mg_dense_solve<<<1, 128, 0, Lc.st>>>(L);
         *Lc.counter += 1;
         return;
     }
