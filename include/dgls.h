@@ -148,6 +148,21 @@ dg_status dg_relax(dg_ctx* ctx, double* z_dev, double dt, int32_t n_steps);
 dg_status dg_residual(dg_ctx* ctx, const double* z_dev, const double* zold_dev,
                       double t, double dt, double* r_dev);
 
+/* Allocation-free variant of dg_residual for DG0 contexts (the paper has no counterpart: this
+ * serves callers of this library).  It is for code that may not allocate device memory when it
+ * runs -- inside CUDA stream capture, where cudaMalloc is illegal, or in a process whose device
+ * memory belongs to an external allocator -- and that must leave the context's own workspaces
+ * untouched: it reads the context's geometry and parameters only and keeps its scratch (one
+ * transport factor per voxel) in a static device array of 2,097,152 doubles (16 MiB, 128^3
+ * voxels) that every GPU loading the library holds until the process exits.  Larger grids and
+ * DG1 contexts return DG_ERR_ARG with a message in dg_last_error().  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the array and overwrites
+ * all of it that it reads, so nothing needs clearing, but two calls that overlap on the GPU
+ * (different streams or threads) race on it.  Inputs, output and asynchrony as dg_residual. */
+dg_status dg_residual_noalloc(dg_ctx* ctx, const double* z_dev, const double* zold_dev,
+                              double t, double dt, double* r_dev);
+
 /* Jacobian-vector product J(z) v with J = dR/dz at fixed z^n, t, dt (exact forward-mode
  * linearisation of dg_residual).  Asynchronous. */
 dg_status dg_jvp(dg_ctx* ctx, const double* z_dev, double t, double dt,

@@ -947,3 +947,44 @@ extern "C" dg_status dg_discharge(dg_ctx* ctx, double* z, const dg_discharge_opt
     out->status = result;
     return result != DG_OK ? result : s;
 }
+
+// ------------------------------------------------------------------ allocation-free residual
+// For callers that must not allocate device memory at the time of the call -- code running
+// inside CUDA stream capture (cudaMalloc is not allowed there) or under an external allocator
+// that owns all device memory -- and that must not touch the context's own workspaces: the
+// DG0 residual with its transport-factor scratch in a static device array instead of the
+// context's buffer.  The array is part of the library image, so every GPU that loads the
+// library holds it (NOALLOC_MAX_VOXELS doubles = 16 MiB) until the process exits.
+namespace {
+constexpr int64_t NOALLOC_MAX_VOXELS = 2097152;   // 128^3 voxels
+__device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_VOXELS];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+}  // namespace
+
+extern "C" dg_status dg_residual_noalloc(dg_ctx* ctx, const double* z, const double* zold, double t, double dt,
+                                         double* r) {
+    if (!ctx || !z || !zold || !r || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_residual_noalloc: bad argument");
+    if (ctx->P.order != 0)
+        return fail(ctx, DG_ERR_ARG, "dg_residual_noalloc: DG0 contexts only (DG1 needs 32 scratch values per voxel)");
+    if ((int64_t)ctx->P.n_cell > NOALLOC_MAX_VOXELS)
+        return fail(ctx, DG_ERR_ARG, "dg_residual_noalloc: " + std::to_string(ctx->P.n_cell) +
+                                         " voxels exceed the static scratch of " + std::to_string(NOALLOC_MAX_VOXELS));
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(ctx, DG_ERR_ARG, "dg_residual_noalloc: device index too large");
+    if (!g_noalloc_ptr[dev]) {
+        // once per device, with that device current: the host-side name of a __device__ array is
+        // not a device address, so ask the runtime for it
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = (double*)ptr;
+    }
+    int64_t launches = 0;
+    LaunchCtx L{ctx->L.st, &launches};
+    e = dg0_residual(L, ctx->P, ctx->G, z, zold, t, dt, 0, r, g_noalloc_ptr[dev]);
+    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("dg_residual_noalloc: ") + cudaGetErrorString(e));
+    return DG_OK;
+}

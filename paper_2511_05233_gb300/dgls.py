@@ -82,6 +82,7 @@ def lib():
             "dg_equilibrium_state": (C.c_int, [_P, _P]),
             "dg_relax": (C.c_int, [_P, _P, C.c_double, C.c_int32]),
             "dg_residual": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P]),
+            "dg_residual_noalloc": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P]),
             "dg_jvp": (C.c_int, [_P, _P, C.c_double, C.c_double, _P, _P]),
             "dg_block_jacobi": (C.c_int, [_P, _P, C.c_double, C.c_double, _P, _P]),
             "dg_row_scales": (C.c_int, [_P, C.c_double, _P]),
@@ -194,6 +195,11 @@ class Context:
 
     def residual(self, z, zold, t, dt, out):
         self._check(self._lib.dg_residual(self._h, _ptr(z), _ptr(zold), t, dt, _ptr(out)))
+        return out
+
+    def residual_noalloc(self, z, zold, t, dt, out):
+        """dg_residual_noalloc: DG0 residual with static scratch (no allocation, no workspace use)."""
+        self._check(self._lib.dg_residual_noalloc(self._h, _ptr(z), _ptr(zold), t, dt, _ptr(out)))
         return out
 
     def jvp(self, z, t, dt, v, out):
