@@ -27,14 +27,15 @@ WORKLOAD = dict(n=128, order=1, chem="tradeoff", porosity=0.5, corr_len=4.0, str
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--order", type=int, default=WORKLOAD["order"])
     ap.add_argument("--chem", default=WORKLOAD["chem"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--precond", default="cpr", choices=["cpr", "bj", "add"])
+    ap.add_argument("--precond", default="add", choices=["cpr", "bj", "add"])
+    ap.add_argument("--precond-every", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -195,7 +196,8 @@ def main():
     chem = dgls.TRADEOFF if a.chem == "tradeoff" else dgls.REDUCED3
     prm = dgls.default_params(chem, a.order, f_C=WORKLOAD["f_C"], eps_struct=1 - WORKLOAD["porosity"],
                               precision=dgls.MIXED if a.precision == "mixed" else dgls.FP64,
-                              preconditioner={"bj": 0, "cpr": 1, "add": 2}[a.precond])
+                              preconditioner={"bj": 0, "cpr": 1, "add": 2}[a.precond],
+                              precond_every=a.precond_every)
     stream = torch.cuda.current_stream()
     ctx = dgls.Context(phase, WORKLOAD["h"], prm, stream)
     N = ctx.n_dof

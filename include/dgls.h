@@ -77,9 +77,11 @@ typedef struct {
     double eta_min;            /* forcing-term floor */
     int64_t hbm_budget_bytes;  /* workspace cap checked in dg_setup (0: no cap) */
     int32_t preconditioner;    /* 0: cell-block Jacobi; 1: two-stage (CPR): multigrid on the potential
-                                  block, then block Jacobi on the remainder (default); 2: the additive
-                                  form of the same two levels (no Jacobian-vector product inside) */
+                                  block, then block Jacobi on the remainder; 2: the additive form of the
+                                  same two levels, no Jacobian-vector product inside (default) */
     int32_t mg_cycles;         /* V-cycles of the potential multigrid per application (1) */
+    int32_t precond_every;     /* rebuild the preconditioner every k-th Newton iteration of a step
+                                  (0: once per step, at its first iteration) */
 } dg_params;
 
 typedef struct {

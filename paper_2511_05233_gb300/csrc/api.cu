@@ -168,8 +168,9 @@ extern "C" dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t 
     p->gmres_max_it = 600;
     p->newton_rtol = 1e-10;
     p->newton_atol = 1e-13;
-    p->preconditioner = 1;
+    p->preconditioner = 2;
     p->mg_cycles = 1;
+    p->precond_every = 0;
     p->newton_max_it = 25;
     p->eta_max = 1e-2;
     p->eta_min = 1e-12;
@@ -728,8 +729,11 @@ static dg_status newton_(dg_ctx* ctx, const double* zn, double t1, double dt, in
     for (;;) {
         if (nrm <= std::max(ctx->prm.newton_rtol * n0, floor_) || nrm == 0.0) break;
         if (it >= ctx->prm.newton_max_it) { result = fail(ctx, DG_ERR_NOCONV, "Newton: iteration limit"); break; }
-        s = build_precond(ctx, ctx->zc, t1, dt, relax);
-        if (s != DG_OK) return s;
+        const int every = ctx->prm.precond_every;
+        if (it == 0 || (every > 0 && it % every == 0)) {
+            s = build_precond(ctx, ctx->zc, t1, dt, relax);
+            if (s != DG_OK) return s;
+        }
         int its = 0;
         // forcing term never asks for more than the Newton tolerance needs
         double eta_eff = std::max(eta, 0.5 * ctx->prm.newton_rtol * n0 / nrm);

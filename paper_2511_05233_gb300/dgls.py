@@ -31,7 +31,7 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("gmres_restart", C.c_int32), ("gmres_max_it", C.c_int32),
                 ("newton_rtol", C.c_double), ("newton_atol", C.c_double), ("newton_max_it", C.c_int32),
                 ("eta_max", C.c_double), ("eta_min", C.c_double), ("hbm_budget_bytes", C.c_int64),
-                ("preconditioner", C.c_int32), ("mg_cycles", C.c_int32)]
+                ("preconditioner", C.c_int32), ("mg_cycles", C.c_int32), ("precond_every", C.c_int32)]
 
 
 class StepInfo(C.Structure):
