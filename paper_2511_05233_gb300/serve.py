@@ -1,0 +1,197 @@
+"""Continuous-batching server for discharge simulations on one GPU.
+
+Requests (structure size, porosity, correlation length, C-rate, DG order) arrive on a seeded
+Poisson clock.  Each admitted request gets a slot: a host thread with its own CUDA stream and its
+own library context (state, Krylov and preconditioner workspaces stay on the device for the whole
+simulation).  A request is admitted when a slot is free and its workspace fits in what is left of
+the HBM budget; requests that arrive while others run are admitted as slots and memory free up, so
+their kernels overlap on the device.  The library releases the GIL in every call (ctypes), and every
+reduction in it has a fixed order, so a simulation's result does not depend on what else runs.
+
+    python -m paper_2511_05233_gb300.serve --requests 16 --slots 4
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import heapq
+import json
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float              # seconds after the start of the run
+    side: int
+    porosity: float
+    corr_len: float
+    f_C: float
+    order: int
+    n_steps: int = 6            # accepted implicit steps of the discharge
+    seed: int = 0
+    start: float = 0.0
+    end: float = 0.0
+    result: dict = field(default_factory=dict)
+
+
+def make_requests(n, rate_hz, seed, side_range=(16, 40), n_steps=6, orders=(0, 1)):
+    """Seeded Poisson arrivals with mixed sizes, C-rates and orders (the request recipe)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate_hz)
+        out.append(Request(rid=i, arrival=t, side=int(rng.integers(side_range[0], side_range[1] + 1)),
+                           porosity=float(rng.uniform(0.45, 0.65)), corr_len=float(rng.uniform(2.0, 6.0)),
+                           f_C=float(np.exp(rng.uniform(np.log(0.1), np.log(2.0)))),
+                           order=int(rng.choice(orders)), n_steps=n_steps, seed=1000 + i))
+    return out
+
+
+def workspace_estimate(req):
+    """Device bytes of one context (state, Newton, Krylov, blocks) before it is created."""
+    n = req.side ** 3
+    nn = 8 if req.order == 1 else 1
+    dof = int(n * nn * (7 + 3 * (1 - req.porosity)))
+    return dof * 8 * (31 + 20) + n * nn * 100 * 8 + (64 << 20)
+
+
+def run_one(req, stream=None):
+    """Set up the cell, take the Tab. 6 equilibrium state and run the naive controller for
+    req.n_steps accepted steps; returns the curve and a checksum of the final state."""
+    import torch
+
+    from . import dgls, inputs
+
+    phase = None
+    for s in range(req.seed, req.seed + 50):
+        ph = inputs.make_structure(req.side, req.porosity, req.corr_len, s)
+        if np.any(ph[:, :, 0] == inputs.STRUCT):
+            phase = ph
+            break
+    prm = dgls.default_params(dgls.TRADEOFF, req.order, f_C=req.f_C, eps_struct=1 - req.porosity)
+    with torch.cuda.stream(stream) if stream is not None else _null():
+        ctx = dgls.Context(phase, 1e-6, prm, stream=stream or torch.cuda.current_stream())
+        z = ctx.new_state()
+        ctx.equilibrium_state(z)
+        res = ctx.discharge(z, controller=dgls.NAIVE, dt0=1e-3, max_steps=req.n_steps)
+        zh = z.cpu().numpy()
+        ctx.close()
+    return {"t": res["t"].tolist(), "dt": res["dt"].tolist(), "U_cell": res["U_cell"].tolist(),
+            "status": res["status"], "sha256": hashlib.sha256(zh.tobytes()).hexdigest(),
+            "n_dof": int(zh.size)}
+
+
+class _null:
+    def __enter__(self):
+        return None
+
+    def __exit__(self, *a):
+        return False
+
+
+def serve(requests, slots=4, hbm_budget=150 << 30, time_scale=1.0):
+    """Run the requests with continuous batching; returns them with start/end times filled."""
+    import torch
+
+    t0 = time.perf_counter()
+    pending = sorted(requests, key=lambda r: r.arrival)
+    lock = threading.Condition()
+    state = {"free_slots": slots, "budget": hbm_budget, "running": 0}
+    streams = [torch.cuda.Stream() for _ in range(slots)]
+    free_streams = list(range(slots))
+    threads = []
+
+    def worker(req, sidx, need):
+        req.start = time.perf_counter() - t0
+        try:
+            req.result = run_one(req, streams[sidx])
+        except Exception as e:  # a failed request is reported, not fatal to the server
+            req.result = {"status": f"error: {e}"}
+        req.end = time.perf_counter() - t0
+        with lock:
+            state["free_slots"] += 1
+            state["budget"] += need
+            free_streams.append(sidx)
+            lock.notify_all()
+
+    queue = []
+    i = 0
+    while i < len(pending) or queue:
+        now = time.perf_counter() - t0
+        while i < len(pending) and pending[i].arrival * time_scale <= now:
+            heapq.heappush(queue, (pending[i].arrival, pending[i].rid, pending[i]))
+            i += 1
+        admitted = False
+        with lock:
+            while queue:
+                req = queue[0][2]
+                need = workspace_estimate(req)
+                if state["free_slots"] == 0 or need > state["budget"]:
+                    break
+                heapq.heappop(queue)
+                state["free_slots"] -= 1
+                state["budget"] -= need
+                sidx = free_streams.pop()
+                th = threading.Thread(target=worker, args=(req, sidx, need), daemon=True)
+                threads.append(th)
+                th.start()
+                admitted = True
+            if not admitted:
+                wait = 0.01
+                if i < len(pending):
+                    wait = max(0.0, min(0.05, pending[i].arrival * time_scale - now))
+                lock.wait(timeout=wait if wait > 0 else 0.001)
+    for th in threads:
+        th.join()
+    return requests, time.perf_counter() - t0
+
+
+def sequential(requests, time_scale=1.0):
+    """The plain loop: one request at a time on the default stream, each starting at its arrival
+    or when the previous one is done."""
+    t0 = time.perf_counter()
+    for r in sorted(requests, key=lambda q: q.arrival):
+        now = time.perf_counter() - t0
+        if r.arrival * time_scale > now:
+            time.sleep(r.arrival * time_scale - now)
+        r.start = time.perf_counter() - t0
+        r.result = run_one(r)
+        r.end = time.perf_counter() - t0
+    return requests, time.perf_counter() - t0
+
+
+def latency_stats(reqs, wall):
+    lat = np.array([r.end - r.arrival for r in reqs])
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "sims_per_hr": len(reqs) / wall * 3600.0, "wall_s": wall}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--rate", type=float, default=4.0, help="Poisson arrival rate, requests per second")
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--steps", type=int, default=6)
+    a = ap.parse_args()
+    import copy
+
+    reqs = make_requests(a.requests, a.rate, a.seed, n_steps=a.steps)
+    served, wall = serve(copy.deepcopy(reqs), slots=a.slots)
+    seqd, wall_seq = sequential(copy.deepcopy(reqs))
+    same = all(x.result.get("U_cell") == y.result.get("U_cell") and x.result.get("sha256") == y.result.get("sha256")
+               for x, y in zip(sorted(served, key=lambda r: r.rid), sorted(seqd, key=lambda r: r.rid)))
+    print(json.dumps({"served": latency_stats(served, wall), "sequential": latency_stats(seqd, wall_seq),
+                      "identical_results_alone_and_in_mix": bool(same),
+                      "requests": len(reqs), "slots": a.slots,
+                      "statuses": sorted({r.result.get("status") for r in served})}))
+
+
+if __name__ == "__main__":
+    main()

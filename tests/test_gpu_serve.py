@@ -1,0 +1,29 @@
+"""Continuous-batching server: every simulation gives the same result alone and in the mix."""
+import copy
+
+import pytest
+
+from tests.gpu_helpers import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_built()
+
+
+def test_served_results_equal_sequential_results():
+    from paper_2511_05233_gb300 import serve
+
+    reqs = serve.make_requests(5, rate_hz=50.0, seed=3, side_range=(10, 16), n_steps=3)
+    served, wall = serve.serve(copy.deepcopy(reqs), slots=3)
+    alone, _ = serve.sequential(copy.deepcopy(reqs), time_scale=0.0)
+    by_id = {r.rid: r for r in alone}
+    for r in served:
+        assert r.result["status"] == "DG_OK", r.result
+        ref = by_id[r.rid].result
+        assert r.result["U_cell"] == ref["U_cell"]          # bitwise: fixed-order reductions
+        assert r.result["sha256"] == ref["sha256"]
+    overlap = any(a.start < b.end and b.start < a.end for a in served for b in served if a.rid < b.rid)
+    assert overlap, "no two requests ran concurrently"
