@@ -44,6 +44,9 @@ struct dg_ctx {
     void* w = nullptr;
     void* u = nullptr;
     void* x = nullptr;             // Krylov combination sum y_k V_k
+    DG1Lin lin{};                  // linearised FP64 DG1 JVP (cached derivative data)
+    bool has_lin = false;
+    bool lin_valid = false;        // lin holds the linearisation at the current Newton iterate
     void* y1 = nullptr;            // CPR: potential correction
     void* t2 = nullptr;            // CPR: remaining residual
     std::vector<MGLevel> mg;
@@ -378,6 +381,14 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         AL(V, (int64_t)(m + 1) * N); AL(w, N); AL(u, N); AL(x, N); AL(y1, N); AL(t2, N);
         ctx->V = V; ctx->w = w; ctx->u = u; ctx->x = x; ctx->y1 = y1; ctx->t2 = t2;
     }
+    if (prm->order == 1 && !mixed) {
+        int64_t njn, ngam, nface;
+        dg1_lin_sizes(P, &njn, &ngam, &nface);
+        double *jn, *gam, *face, *lgb;
+        AL(jn, njn); AL(gam, ngam); AL(face, nface); AL(lgb, ngam);
+        ctx->lin.jn = jn; ctx->lin.gam = gam; ctx->lin.face = face; ctx->lin.gb = lgb; ctx->lin.gbd = ctx->gbd;
+        ctx->has_lin = true;
+    }
     if (prm->preconditioner != 0 && mg_levels_alloc(ctx->mg, nx, ny, nz, ctx->allocs, &ctx->ws_bytes) != cudaSuccess) {
         free_all(ctx);
         delete ctx;
@@ -441,12 +452,24 @@ static dg_status residual_(dg_ctx* ctx, const double* z, const double* zn, doubl
     return DG_OK;
 }
 
+// J v through the kernels for this context: the cached linearisation when it is valid (FP64 DG1),
+// otherwise forward-mode dual numbers.
+template <class S>
+static cudaError_t jvp_kernels(dg_ctx* ctx, const S* z, const S* v, double t, double dt, int relax, double sc_dt, S* out,
+                               S* gb, S* gbd) {
+    if constexpr (std::is_same<S, double>::value) {
+        if (ctx->has_lin && ctx->lin_valid)
+            return dg1_lin_apply(ctx->L, ctx->P, ctx->G, z, v, t, relax, sc_dt, out, ctx->lin);
+    }
+    return ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd)
+                             : dg1_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd);
+}
+
 template <class S>
 static dg_status jvp_(dg_ctx* ctx, const S* z, const S* v, double t, double dt, int relax, double sc_dt, S* out,
                       S* gb, S* gbd) {
     ProfScope ps(ctx, 1);
-    cudaError_t e = ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd)
-                                      : dg1_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd);
+    cudaError_t e = jvp_kernels<S>(ctx, z, v, t, dt, relax, sc_dt, out, gb, gbd);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("jvp: ") + cudaGetErrorString(e));
     ctx->jvp_evals++;
     return DG_OK;
@@ -500,8 +523,7 @@ static dg_status precond_apply_(dg_ctx* ctx, const S* v, S* u, const S* zS, doub
         CK(saxpby<S>(ctx->L, u, 1.0, y1, 1.0, N));
         return DG_OK;
     }
-    cudaError_t e = ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, zS, y1, t, dt, relax, dt, t2, gbS, gbdS)
-                                      : dg1_jvp<S>(ctx->L, ctx->P, ctx->G, zS, y1, t, dt, relax, dt, t2, gbS, gbdS);
+    cudaError_t e = jvp_kernels<S>(ctx, zS, y1, t, dt, relax, dt, t2, gbS, gbdS);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("jvp: ") + cudaGetErrorString(e));
     ctx->jvp_evals++;
     CK(saxpby<S>(ctx->L, t2, -1.0, v, 1.0, N));
@@ -549,7 +571,13 @@ extern "C" dg_status dg_residual(dg_ctx* ctx, const double* z, const double* zol
 
 extern "C" dg_status dg_jvp(dg_ctx* ctx, const double* z, double t, double dt, const double* v, double* jv) {
     if (!ctx || !z || !v || !jv || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_jvp: bad argument");
-    return jvp_<double>(ctx, z, v, t, dt, 0, 0.0, jv, ctx->gb, ctx->gbd);
+    if (ctx->has_lin) {
+        CK(dg1_linearize(ctx->L, ctx->P, ctx->G, z, t, dt, 0, ctx->lin));
+        ctx->lin_valid = true;
+    }
+    dg_status s = jvp_<double>(ctx, z, v, t, dt, 0, 0.0, jv, ctx->gb, ctx->gbd);
+    ctx->lin_valid = false;
+    return s;
 }
 
 extern "C" dg_status dg_block_jacobi(dg_ctx* ctx, const double* z, double t, double dt, const double* v, double* out) {
@@ -734,12 +762,18 @@ static dg_status newton_(dg_ctx* ctx, const double* zn, double t1, double dt, in
             s = build_precond(ctx, ctx->zc, t1, dt, relax);
             if (s != DG_OK) return s;
         }
+        if (ctx->has_lin) {
+            ProfScope ps(ctx, 2);
+            CK(dg1_linearize(ctx->L, ctx->P, ctx->G, ctx->zc, t1, dt, relax, ctx->lin));
+            ctx->lin_valid = true;
+        }
         int its = 0;
         // forcing term never asks for more than the Newton tolerance needs
         double eta_eff = std::max(eta, 0.5 * ctx->prm.newton_rtol * n0 / nrm);
         eta_eff = std::min(eta_eff, ctx->prm.eta_max);
         s = mixed ? gmres_<float>(ctx, ctx->zc, t1, dt, relax, std::max(eta_eff, 1e-6), &its)
                   : gmres_<double>(ctx, ctx->zc, t1, dt, relax, eta_eff, &its);
+        ctx->lin_valid = false;
         if (s != DG_OK) return s;
         ctx->gmres_its += its;
         // backtracking line search on ||S R||

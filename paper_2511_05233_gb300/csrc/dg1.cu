@@ -51,6 +51,8 @@ __device__ __forceinline__ S ld(const S* z, const DevParams& p, int f, int node,
 }
 }  // namespace
 
+static inline int nblocks(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
 // ------------------------------------------------------------------ (A) transport factors
 template <class Chem, class S, bool TAN>
 __global__ void __launch_bounds__(128) k_dg1_g(const DevParams p, const Geo g, const S* __restrict__ z,
@@ -671,8 +673,452 @@ __global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, 
     }
 }
 
+// ------------------------------------------------------------------ linearised FP64 JVP
+// The FP64 JVP above recomputes, for every Krylov vector, the values and all transcendentals and
+// divisions along with the tangents; on GB300 that keeps the FP64 pipe ~85 % busy while HBM idles.
+// During one Newton iteration the linearisation point z is fixed, so the value side is computed
+// once and cached (HBM is cheap here, FP64 issue is not):
+//   jn   [8 nodes][NF x NF][voxel]  derivative of the node terms (storage + sources) w.r.t. the
+//                                    node's own unknowns;
+//   gam  [32 slots][voxel]          dg = g (gam d eps_L - visc d c_S): gam = 3/(2 eps_L) or 0;
+//   face [3 dirs x 4 lines][NFD][voxel] for the +d face of each voxel: {g}_H and its two partial
+//        derivatives, the flux brackets (pen [[psi]] - {d_n psi}) of every liquid field and of
+//        Phi^L, and per charged species {g c}_H with the coefficients of its differential;
+//        on the x = nx face: d r_Ano / d c_Li, d r_Ano / d Phi^L.
+// The apply kernels are then products of cached coefficients with tangents (FMAs only).
+template <class Chem>
+struct LinShape {
+    static constexpr int NL = Chem::NL;
+    static constexpr int NC = Chem::NL - 1;                  // charged species (all but S8(L))
+    static constexpr int NFD = 3 + NL + 1 + 5 * NC;
+    static __device__ __forceinline__ int ci(int m) { return m < 1 ? m : m - 1; }
+};
+
+template <class Chem>
+__global__ void __launch_bounds__(128) k_lin_gam(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                 double* __restrict__ gam) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    constexpr int NS = Chem::NS;
+    const int ph = g.phase[cell];
+    const int s = g.cmap[cell];
+    double es[8][2];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        es[n][0] = es[n][1] = 0.0;
+        if (NS == 2 && ph == 1) {
+            es[n][0] = ld(z, p, Chem::NL, n, s);
+            es[n][1] = ld(z, p, Chem::NL + 1, n, s);
+        }
+        double eL = liquid_fraction<Chem, double>(p, ph, es[n]);
+        gam[(int64_t)n * p.n_cell + cell] = (ph == 1 && NS == 2 && eL > 0.0) ? 1.5 / eL : 0.0;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int side = -1; side <= 1; side += 2)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int n0, n1;
+                line_nodes(d, q, n0, n1);
+                const double wn = side > 0 ? ALPHA : BETA, wf = side > 0 ? BETA : ALPHA;
+                double et[2] = {es[n1][0] * wn + es[n0][0] * wf, es[n1][1] * wn + es[n0][1] * wf};
+                double eL = liquid_fraction<Chem, double>(p, ph, et);
+                gam[(int64_t)face_slot(d, side, q) * p.n_cell + cell] = (ph == 1 && NS == 2 && eL > 0.0) ? 1.5 / eL : 0.0;
+            }
+}
+
+// node Jacobians: one thread per (node, voxel), NF seeded evaluations of the node terms
+template <class Chem>
+__global__ void __launch_bounds__(64) k_lin_nodes_build(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                        double t, double dt, int relax, double* __restrict__ jn) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 8) return;
+    typedef Dual<double> T;
+    constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
+    const int n = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)n * p.n_cell);
+    const int ph = g.phase[cell];
+    const int sidx = g.cmap[cell];
+    const bool st = ph == 1;
+    double old[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) old[f] = 0.0;
+    const double tH = smooth_step(t);
+    double* J = jn + (int64_t)n * NF * NF * p.n_cell + cell;     // [row*NF + col][voxel] within the node
+#pragma unroll 1
+    for (int col = 0; col < NF; ++col) {
+        T c[NL], es[2], phiL, phiS;
+#pragma unroll
+        for (int m = 0; m < NL; ++m) c[m] = Make<T>::var(ld(z, p, m, n, cell), col == m ? 1.0 : 0.0);
+        es[0] = es[1] = Make<T>::c(0.0);
+        phiS = Make<T>::c(0.0);
+        phiL = Make<T>::var(ld(z, p, PHIL, n, cell), col == PHIL ? 1.0 : 0.0);
+        if (st) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) es[q] = Make<T>::var(ld(z, p, NL + q, n, sidx), col == NL + q ? 1.0 : 0.0);
+            phiS = Make<T>::var(ld(z, p, PHIS, n, sidx), col == PHIS ? 1.0 : 0.0);
+        }
+        T R[NF];
+        node_terms<Chem, T>(p, ph, c, es, phiL, phiS, old, tH, dt, relax, R);
+#pragma unroll
+        for (int row = 0; row < NF; ++row) J[(int64_t)(row * NF + col) * p.n_cell] = R[row].d;
+    }
+}
+
+// face data of the +d face of every voxel (and the anode derivatives on the x = nx face)
+template <class Chem>
+__global__ void __launch_bounds__(128) k_lin_faces_build(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                         const double* __restrict__ gb, int d, double* __restrict__ face) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 4) return;
+    typedef LinShape<Chem> SH;
+    constexpr int NL = Chem::NL;
+    const int q = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)q * p.n_cell);
+    int i, j, k;
+    cell_ijk(p, cell, i, j, k);
+    int n0, n1;
+    line_nodes(d, q, n0, n1);
+    double* F = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
+    auto put = [&](int kk, double v) { F[(int64_t)kk * p.n_cell] = v; };
+    const int coord = d == 0 ? i : d == 1 ? j : k;
+    const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
+    const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+    const double pen = p.penalty / p.h, gq = SQ3 / p.h;
+    if (coord + 1 >= ext) {
+        if (d == 0) {   // anode face of the last layer: r_Ano derivatives at the face point
+            double cLi = ALPHA * ld(z, p, 0, n1, cell) + BETA * ld(z, p, 0, n0, cell);
+            double phL = ALPHA * ld(z, p, Chem::PHIL, n1, cell) + BETA * ld(z, p, Chem::PHIL, n0, cell);
+            Dual<double> r1 = anode_rate<Dual<double>>(p, mkd(cLi, 1.0), mkd(phL, 0.0));
+            Dual<double> r2 = anode_rate<Dual<double>>(p, mkd(cLi, 0.0), mkd(phL, 1.0));
+            put(0, r1.d);
+            put(1, r2.d);
+        }
+        return;
+    }
+    const int qc = cell + stride;
+    const double gl = gb[(int64_t)face_slot(d, +1, q) * p.n_cell + cell];
+    const double gr = gb[(int64_t)face_slot(d, -1, q) * p.n_cell + qc];
+    double Hg = 0.0, Ha = 0.0, Hb = 0.0;
+    if (gl * gr > 0.0) {
+        double r = 1.0 / (gl + gr);
+        Hg = 2.0 * gl * gr * r;
+        Ha = 2.0 * gr * gr * r * r;
+        Hb = 2.0 * gl * gl * r * r;
+    }
+    put(0, Hg);
+    put(1, Ha);
+    put(2, Hb);
+    {
+        double P0 = ld(z, p, Chem::PHIL, n0, cell), P1 = ld(z, p, Chem::PHIL, n1, cell);
+        double Q0 = ld(z, p, Chem::PHIL, n0, qc), Q1 = ld(z, p, Chem::PHIL, n1, qc);
+        double jL = (ALPHA * P1 + BETA * P0) - (ALPHA * Q0 + BETA * Q1);
+        double mL = 0.5 * gq * ((P1 - P0) + (Q1 - Q0));
+        put(3 + NL, jL * pen - mL);
+    }
+#pragma unroll
+    for (int m = 0; m < NL; ++m) {
+        double C0 = ld(z, p, m, n0, cell), C1 = ld(z, p, m, n1, cell);
+        double Q0 = ld(z, p, m, n0, qc), Q1 = ld(z, p, m, n1, qc);
+        double cl = ALPHA * C1 + BETA * C0, cr = ALPHA * Q0 + BETA * Q1;
+        put(3 + m, (cl - cr) * pen - 0.5 * gq * ((C1 - C0) + (Q1 - Q0)));
+        if (p.zc[m] != 0.0) {
+            const int base = 4 + NL + 5 * SH::ci(m);
+            double x = gl * cl, y = gr * cr;
+            double Hm = 0.0, Hx = 0.0, Hy = 0.0;
+            if (x * y > 0.0) {
+                double r = 1.0 / (x + y);
+                Hm = 2.0 * x * y * r;
+                Hx = 2.0 * y * y * r * r;
+                Hy = 2.0 * x * x * r * r;
+            }
+            put(base + 0, Hm);
+            put(base + 1, Hx * cl);     // coefficient of d g_l
+            put(base + 2, Hx * gl);     // coefficient of d c_l
+            put(base + 3, Hy * cr);     // coefficient of d g_r
+            put(base + 4, Hy * gr);     // coefficient of d c_r
+        }
+    }
+}
+
+// tangents of the 32 transport factors of each voxel: dg = g (gam d eps_L - visc d c_S)
+template <class Chem>
+__global__ void __launch_bounds__(128) k_lin_g(const DevParams p, const Geo g, const double* __restrict__ v,
+                                               const double* __restrict__ gb, const double* __restrict__ gam,
+                                               double* __restrict__ gbd) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    constexpr int NL = Chem::NL, NS = Chem::NS;
+    const int ph = g.phase[cell];
+    const int s = g.cmap[cell];
+    double dcs[8], del[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        double a = 0.0;
+#pragma unroll
+        for (int m = 0; m < NL; ++m)
+            if (p.wS[m] != 0.0) a += p.wS[m] * ld(v, p, m, n, cell);
+        dcs[n] = a;
+        del[n] = (NS == 2 && ph == 1) ? -(ld(v, p, NL, n, s) + ld(v, p, NL + 1, n, s)) : 0.0;
+        int64_t o = (int64_t)n * p.n_cell + cell;
+        gbd[o] = gb[o] * (gam[o] * del[n] - p.visc * dcs[n]);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int side = -1; side <= 1; side += 2)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int n0, n1;
+                line_nodes(d, q, n0, n1);
+                const double wn = side > 0 ? ALPHA : BETA, wf = side > 0 ? BETA : ALPHA;
+                int64_t o = (int64_t)face_slot(d, side, q) * p.n_cell + cell;
+                double dc = dcs[n1] * wn + dcs[n0] * wf;
+                double de = del[n1] * wn + del[n0] * wf;
+                gbd[o] = gb[o] * (gam[o] * de - p.visc * dc);
+            }
+}
+
+// node part of the JVP: out = J_node v_node (writes, the line passes add)
+template <class Chem>
+__global__ void __launch_bounds__(128) k_lin_nodes_apply(const DevParams p, const Geo g, const double* __restrict__ v,
+                                                         const double* __restrict__ jn, double sc_dt,
+                                                         double* __restrict__ out) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 8) return;
+    constexpr int NF = Chem::NF;
+    const int n = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)n * p.n_cell);
+    const int sidx = g.cmap[cell];
+    const bool st = g.phase[cell] == 1;
+    double x[NF];
+    int64_t idx[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        idx[f] = (!p.is_struct[f]) ? p.off[f] + (int64_t)n * p.flen[f] + cell
+                                   : (st ? p.off[f] + (int64_t)n * p.flen[f] + sidx : -1);
+        x[f] = idx[f] >= 0 ? v[idx[f]] : 0.0;
+    }
+    const double* J = jn + (int64_t)n * NF * NF * p.n_cell + cell;
+#pragma unroll
+    for (int r = 0; r < NF; ++r) {
+        if (idx[r] < 0) continue;
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < NF; ++c) acc += J[(int64_t)(r * NF + c) * p.n_cell] * x[c];
+        if (sc_dt > 0.0) acc *= sc_dt * p.rscale[r];
+        out[idx[r]] = acc;
+    }
+}
+
+// line part of the JVP (one pass per direction, one thread per (line, voxel))
+template <class Chem>
+__global__ void __launch_bounds__(128) k_lin_lines_apply(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                         const double* __restrict__ v, const double* __restrict__ gb,
+                                                         const double* __restrict__ gbd, const double* __restrict__ face,
+                                                         int d, double t, int relax, double sc_dt,
+                                                         double* __restrict__ out) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 4) return;
+    typedef LinShape<Chem> SH;
+    constexpr int NL = Chem::NL;
+    const int q = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)q * p.n_cell);
+    int i, j, k;
+    cell_ijk(p, cell, i, j, k);
+    int n0, n1;
+    line_nodes(d, q, n0, n1);
+    const int sidx = g.cmap[cell];
+    const bool st = g.phase[cell] == 1;
+    const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h, gq = SQ3 / p.h, pen = p.penalty / p.h;
+    const int coord = d == 0 ? i : d == 1 ? j : k;
+    const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
+    const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+    bool hasQ[2];
+    int qcell[2];
+    hasQ[0] = coord > 0;
+    hasQ[1] = coord + 1 < ext;
+    qcell[0] = hasQ[0] ? cell - stride : cell;
+    qcell[1] = hasQ[1] ? cell + stride : cell;
+    // face data of the two faces: side 1 = own +d face, side 0 = the -d neighbour's +d face
+    const double* Fd[2];
+    Fd[1] = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
+    Fd[0] = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + qcell[0];
+    auto F = [&](int sd, int kk) { return Fd[sd][(int64_t)kk * p.n_cell]; };
+    auto V = [&](int f, int n, int idx) { return v[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
+    auto Z = [&](int f, int n, int idx) { return z[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
+    // tangents of the face transport factors (left, right) of both faces
+    double dgl[2] = {0.0, 0.0}, dgr[2] = {0.0, 0.0}, gl[2] = {0.0, 0.0}, gr[2] = {0.0, 0.0};
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        if (!hasQ[sd]) continue;
+        const int L = sd == 1 ? cell : qcell[0], R = sd == 1 ? qcell[1] : cell;
+        int64_t ol = (int64_t)face_slot(d, +1, q) * p.n_cell + L, orr = (int64_t)face_slot(d, -1, q) * p.n_cell + R;
+        gl[sd] = gb[ol];
+        gr[sd] = gb[orr];
+        dgl[sd] = gbd[ol];
+        dgr[sd] = gbd[orr];
+    }
+    const double gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
+    const double dgN0 = gbd[(int64_t)n0 * p.n_cell + cell], dgN1 = gbd[(int64_t)n1 * p.n_cell + cell];
+    // Phi^L: values for the volume term, tangents and the tangent of the face brackets
+    const double P0 = Z(Chem::PHIL, n0, cell), P1 = Z(Chem::PHIL, n1, cell);
+    const double dP0 = V(Chem::PHIL, n0, cell), dP1 = V(Chem::PHIL, n1, cell);
+    double dBL[2] = {0.0, 0.0}, BL[2] = {0.0, 0.0}, dHg[2] = {0.0, 0.0}, Hg[2] = {0.0, 0.0};
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        if (!hasQ[sd]) continue;
+        const int Qc = qcell[sd];
+        double q0 = V(Chem::PHIL, n0, Qc), q1 = V(Chem::PHIL, n1, Qc);
+        // left/right roles: sd = 1 own is left
+        double l0 = sd == 1 ? dP0 : q0, l1 = sd == 1 ? dP1 : q1, r0 = sd == 1 ? q0 : dP0, r1 = sd == 1 ? q1 : dP1;
+        double dj = (ALPHA * l1 + BETA * l0) - (ALPHA * r0 + BETA * r1);
+        double dm = 0.5 * gq * ((l1 - l0) + (r1 - r0));
+        dBL[sd] = dj * pen - dm;
+        BL[sd] = F(sd, 3 + NL);
+        Hg[sd] = F(sd, 0);
+        dHg[sd] = F(sd, 1) * dgl[sd] + F(sd, 2) * dgr[sd];
+    }
+    double aL0 = 0.0, aL1 = 0.0;
+    auto add_face = [&](int sd, double f, double& a0, double& a1) {
+        double ff = f * (sd == 1 ? wf : -wf);
+        if (sd == 1) { a1 += ff * ALPHA; a0 += ff * BETA; }
+        else { a0 += ff * ALPHA; a1 += ff * BETA; }
+    };
+    auto store = [&](int f, int idx, double a0, double a1) {
+        if (sc_dt > 0.0) { double sc = sc_dt * p.rscale[f]; a0 *= sc; a1 *= sc; }
+        out[p.off[f] + (int64_t)n0 * p.flen[f] + idx] += a0;
+        out[p.off[f] + (int64_t)n1 * p.flen[f] + idx] += a1;
+    };
+    const double dPhi = P1 - P0, ddPhi = dP1 - dP0;
+    const double gsum = gN0 + gN1, dgsum = dgN0 + dgN1;
+#pragma unroll 1
+    for (int m = 0; m < NL; ++m) {
+        const bool charged = p.zc[m] != 0.0;
+        const double C0 = Z(m, n0, cell), C1 = Z(m, n1, cell);
+        const double dC0 = V(m, n0, cell), dC1 = V(m, n1, cell);
+        const double dc = C1 - C0, ddc = dC1 - dC0;
+        double a0 = 0.0, a1 = 0.0;
+        {
+            double fl = 0.0;
+            if (!relax) fl = (dgsum * dc + gsum * ddc) * p.D0[m];
+            if (charged) {
+                double msum = gN0 * C0 + gN1 * C1;
+                double dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
+                if (!relax) fl += (dmsum * dPhi + msum * ddPhi) * p.kappa_m[m];
+                double fL = ((dgsum * dc + gsum * ddc) * p.Kd[m] + (dmsum * dPhi + msum * ddPhi) * p.Km[m]) * vol;
+                aL1 += fL;
+                aL0 -= fL;
+            }
+            fl *= vol;
+            a1 += fl;
+            a0 -= fl;
+        }
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            if (!hasQ[sd]) continue;
+            const int Qc = qcell[sd];
+            double q0 = V(m, n0, Qc), q1 = V(m, n1, Qc);
+            double l0 = sd == 1 ? dC0 : q0, l1 = sd == 1 ? dC1 : q1, r0 = sd == 1 ? q0 : dC0, r1 = sd == 1 ? q1 : dC1;
+            double dcl = ALPHA * l1 + BETA * l0, dcr = ALPHA * r0 + BETA * r1;
+            double dB = (dcl - dcr) * pen - 0.5 * gq * ((l1 - l0) + (r1 - r0));
+            double B = F(sd, 3 + m);
+            double dterm = dHg[sd] * B + Hg[sd] * dB;
+            double f = relax ? 0.0 : dterm * p.D0[m];
+            if (charged) {
+                const int base = 4 + NL + 5 * SH::ci(m);
+                double Hm = F(sd, base);
+                double dHm = F(sd, base + 1) * dgl[sd] + F(sd, base + 2) * dcl + F(sd, base + 3) * dgr[sd] +
+                             F(sd, base + 4) * dcr;
+                double mterm = dHm * BL[sd] + Hm * dBL[sd];
+                if (!relax) f += mterm * p.kappa_m[m];
+                add_face(sd, dterm * p.Kd[m] + mterm * p.Km[m], aL0, aL1);
+            }
+            add_face(sd, f, a0, a1);
+        }
+        if (m == 0 && d == 0 && i == p.nx - 1) {
+            double dcLi = ALPHA * dC1 + BETA * dC0, dphL = ALPHA * dP1 + BETA * dP0;
+            double drA = F(1, 0) * dcLi + F(1, 1) * dphL;
+            if (!relax) {
+                double fLi = drA * wf * p.kAno;
+                a1 += fLi * ALPHA;
+                a0 += fLi * BETA;
+            }
+            double fL = drA * wf * p.F * p.kAno;
+            aL1 += fL * ALPHA;
+            aL0 += fL * BETA;
+        }
+        store(m, cell, a0, a1);
+    }
+    store(Chem::PHIL, cell, aL0, aL1);
+    if (st) {
+        const double S0 = V(Chem::PHIS, n0, sidx), S1 = V(Chem::PHIS, n1, sidx);
+        double a0 = 0.0, a1 = 0.0;
+        double fs = (S1 - S0) * 2.0 * p.kappa_s * vol;
+        a1 += fs;
+        a0 -= fs;
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            if (!hasQ[sd] || g.phase[qcell[sd]] != 1) continue;
+            const int qs = g.cmap[qcell[sd]];
+            double q0 = V(Chem::PHIS, n0, qs), q1 = V(Chem::PHIS, n1, qs);
+            double l0 = sd == 1 ? S0 : q0, l1 = sd == 1 ? S1 : q1, r0 = sd == 1 ? q0 : S0, r1 = sd == 1 ? q1 : S1;
+            double dj = (ALPHA * l1 + BETA * l0) - (ALPHA * r0 + BETA * r1);
+            double dm = 0.5 * gq * ((l1 - l0) + (r1 - r0));
+            add_face(sd, (dj * pen - dm) * p.kappa_s, a0, a1);
+        }
+        store(Chem::PHIS, sidx, a0, a1);
+    }
+}
+
+int64_t dg1_lin_sizes(const DevParams& p, int64_t* jn, int64_t* gam, int64_t* face) {
+    const int nf = p.nf;
+    const int nl = p.nl;
+    const int nfd = 3 + nl + 1 + 5 * (nl - 1);
+    *jn = (int64_t)8 * nf * nf * p.n_cell;
+    *gam = (int64_t)NG * p.n_cell;
+    *face = (int64_t)12 * nfd * p.n_cell;
+    return (*jn + *gam + *face) * 8;
+}
+
+template <class Chem>
+static cudaError_t linearize_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t,
+                                  double dt, int relax, const DG1Lin& lin) {
+    k_dg1_g<Chem, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, lin.gb, lin.gb);
+    k_lin_gam<Chem><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, lin.gam);
+    k_lin_nodes_build<Chem><<<nblocks((int64_t)p.n_cell * 8, 64), 64, 0, L.st>>>(p, g, z, t, dt, relax, lin.jn);
+    for (int d = 0; d < 3; ++d)
+        k_lin_faces_build<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, lin.gb, d, lin.face);
+    *L.counter += 6;
+    return cudaGetLastError();
+}
+
+cudaError_t dg1_linearize(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t, double dt,
+                          int relax, const DG1Lin& lin) {
+    return p.nf == 10 ? linearize_impl<ChemTO>(L, p, g, z, t, dt, relax, lin)
+                      : linearize_impl<ChemR3>(L, p, g, z, t, dt, relax, lin);
+}
+
+template <class Chem>
+static cudaError_t lin_apply_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
+                                  double t, int relax, double sc_dt, double* out, const DG1Lin& lin) {
+    k_lin_g<Chem><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, v, lin.gb, lin.gam, lin.gbd);
+    k_lin_nodes_apply<Chem><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, g, v, lin.jn, sc_dt, out);
+    for (int d = 0; d < 3; ++d)
+        k_lin_lines_apply<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, v, lin.gb, lin.gbd,
+                                                                                        lin.face, d, t, relax, sc_dt, out);
+    *L.counter += 5;
+    return cudaGetLastError();
+}
+
+cudaError_t dg1_lin_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
+                          double t, int relax, double sc_dt, double* out, const DG1Lin& lin) {
+    return p.nf == 10 ? lin_apply_impl<ChemTO>(L, p, g, z, v, t, relax, sc_dt, out, lin)
+                      : lin_apply_impl<ChemR3>(L, p, g, z, v, t, relax, sc_dt, out, lin);
+}
+
 // ------------------------------------------------------------------ launchers
-static inline int nblocks(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
 int64_t dg1_face_buffer_len(const DevParams& p) { return (int64_t)NG * p.n_cell; }
 

@@ -61,6 +61,19 @@ cudaError_t dg1_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, con
                        double t, double dt, int relax, double* blk, S* fbuf);
 cudaError_t dg1_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double* fbuf);
 int64_t dg1_face_buffer_len(const DevParams& p);
+// Linearised FP64 DG1 JVP: cached derivative data at a fixed linearisation point.
+struct DG1Lin {
+    double* jn;     // [8][NF*NF][n_cell] node Jacobians
+    double* gam;    // [32][n_cell] 3/(2 eps_L) per transport-factor slot
+    double* face;   // [12][NFD][n_cell] face data of the + faces
+    double* gb;     // [32][n_cell] transport factors at the linearisation point
+    double* gbd;    // [32][n_cell] their tangents (apply scratch)
+};
+int64_t dg1_lin_sizes(const DevParams& p, int64_t* jn, int64_t* gam, int64_t* face);
+cudaError_t dg1_linearize(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t, double dt,
+                          int relax, const DG1Lin& lin);
+cudaError_t dg1_lin_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
+                          double t, int relax, double sc_dt, double* out, const DG1Lin& lin);
 
 // ------------------------------------------------------------------ linear algebra (la.cu)
 // Block-Jacobi: invert nblk blocks of nf x nf (row-major) in place; identity rows for absent
