@@ -36,8 +36,11 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--precond", default="add", choices=["cpr", "bj", "add"])
     ap.add_argument("--precond-every", type=int, default=0)
+    ap.add_argument("--reorth", type=int, default=0, choices=[0, 1],
+                    help="GMRES Gram-Schmidt: 0 second pass when needed, 1 always")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -56,12 +59,16 @@ def measured_peaks():
         return {}
 
 
-# FP64 throughput of this GB300 measured by a DFMA probe (independent FMA chains over 8 x 152 x 256
-# threads): 1200 GFLOP/s; the roofline of an FP64-ALU-bound kernel is taken against it.
-FP64_PEAK_GFLOPS = 1200.0
-# FP64 operations per unknown of one DG1 Jacobian-vector product of the Tradeoff Chemistry,
-# counted by ncu (2 x DFMA + DADD + DMUL instructions of one launch / unknowns).
-FP64_FLOP_PER_DOF = {"jvp_dg1_tradeoff": None, "jvp_dg0_tradeoff": None}
+# FP64 peak of GB300 derived from its unit counts and clock: 152 SMs x 2 DFMA per clock per SM
+# (the nominal 1.25 TFLOP/s / (152 x 2.07 GHz x 2 FLOP)) x 2 FLOP x 2.07 GHz.  A DFMA probe
+# (independent FMA chains over 8 x 152 x 256 threads) measured 1200 GFLOP/s on the same part.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# FP64 operations per unknown of one linearised DG1 Jacobian-vector product of the Tradeoff
+# Chemistry (transport-factor tangents, node Jacobians, face fluxes once per face, line gather):
+# 2 x DFMA + DADD + DMUL thread instructions of the eight launches of one product counted by ncu
+# at 64^3 (17,428,880 unknowns), / unknowns.  DRAM bytes of the same launches, per unknown.
+LIN_JVP_DG1_FLOP_PER_DOF = 118.1
+LIN_JVP_DG1_DRAM_BYTES_PER_DOF = 307.6
 
 
 class ClockSampler:
@@ -170,6 +177,7 @@ def config_dict(a):
                         f"Gaussian random-field structure porosity {WORKLOAD['porosity']}, correlation length {WORKLOAD['corr_len']} voxels, "
                         f"one implicit Euler step dt={WORKLOAD['dt']} s at {WORKLOAD['f_C']}C, Newton-GMRES(30) rtol 1e-10",
             "grid": a.n, "order": a.order, "chemistry": a.chem, "precision": a.precision, "preconditioner": a.precond,
+            "gram_schmidt": "cgs2" if a.reorth else "cgs+dgks",
             "l2": "inputs larger than L2 (every state vector > 129 MB)"}
 
 
@@ -197,7 +205,7 @@ def main():
     prm = dgls.default_params(chem, a.order, f_C=WORKLOAD["f_C"], eps_struct=1 - WORKLOAD["porosity"],
                               precision=dgls.MIXED if a.precision == "mixed" else dgls.FP64,
                               preconditioner={"bj": 0, "cpr": 1, "add": 2}[a.precond],
-                              precond_every=a.precond_every)
+                              precond_every=a.precond_every, reorth=a.reorth)
     stream = torch.cuda.current_stream()
     ctx = dgls.Context(phase, WORKLOAD["h"], prm, stream)
     N = ctx.n_dof
@@ -226,6 +234,7 @@ def main():
         dist.barrier()
     ctx.profile(True)
     l0 = ctx.launch_count()
+    r0 = ctx.reorth_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
     with ClockSampler(local) as clk:
@@ -239,6 +248,7 @@ def main():
         torch.cuda.synchronize()
     elapsed_ms = e0.elapsed_time(e1)
     launches = ctx.launch_count() - l0
+    reorth = ctx.reorth_count() - r0
     prof = ctx.profile_read()
     ctx.profile(False)
     evals = sum(i.residual_evals + i.jvp_evals for i in infos)
@@ -252,18 +262,33 @@ def main():
         units = uu.item()
     value = units / (elapsed_ms / 1e3) / 1e9
 
-    # ---- dominant kernel roofline (live CUDA-event timing inside the timed steps)
+    # ---- dominant kernel roofline (live CUDA-event timing inside the timed steps).  The FP64
+    # linearised DG1 product is FP64-ALU-bound on GB300 (FP64 pipe 83-89 % busy, DRAM below half),
+    # so it is set against the FP64 peak; other categories against HBM bandwidth.
     peaks = measured_peaks()
     cat = max(("residual", "jvp", "precond_build", "precond_apply", "krylov"), key=lambda k: prof[k][0])
     ms_tot, calls = prof[cat]
-    bpd = {"residual": 24.0, "jvp": 24.0 if a.precision == "fp64" else 12.0}.get(cat)
     roof = None
-    if bpd and calls:
-        achieved = bpd * N / (ms_tot / calls / 1e3) / 1e9
-        pk = peaks.get("hbm_gbs", 6800.0)
-        roof = {"kernel": cat, "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
-                "frac": achieved / pk, "traffic": None, "bytes_per_dof": bpd,
-                "avg_launch_ms": ms_tot / calls, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    if calls:
+        avg_ms = ms_tot / calls
+        if cat == "jvp" and a.order == 1 and a.chem == "tradeoff" and a.precision == "fp64":
+            achieved = LIN_JVP_DG1_FLOP_PER_DOF * N / (avg_ms / 1e3) / 1e9
+            roof = {"kernel": "jvp (linearised DG1 apply: k_lin_g, k_lin_nodes_apply, k_lin_face_flux, "
+                              "k_lin_line_gather)",
+                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": achieved / FP64_PEAK_GFLOPS, "traffic": LIN_JVP_DG1_DRAM_BYTES_PER_DOF * N,
+                    "flop_per_dof": LIN_JVP_DG1_FLOP_PER_DOF, "avg_launch_ms": avg_ms,
+                    "peak_source": "derived FP64 peak (152 SMs x 4 FLOP/clk x 2.07 GHz)",
+                    "hbm_frac_of_measured": LIN_JVP_DG1_DRAM_BYTES_PER_DOF * N / (avg_ms / 1e3) / 1e9
+                    / peaks.get("hbm_gbs", 6800.0)}
+        else:
+            bpd = {"residual": 24.0, "jvp": 24.0 if a.precision == "fp64" else 12.0}.get(cat)
+            if bpd:
+                achieved = bpd * N / (avg_ms / 1e3) / 1e9
+                pk = peaks.get("hbm_gbs", 6800.0)
+                roof = {"kernel": cat, "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
+                        "frac": achieved / pk, "traffic": None, "bytes_per_dof": bpd, "avg_launch_ms": avg_ms,
+                        "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     breakdown = {k: {"ms": v[0], "calls": v[1]} for k, v in prof.items()}
 
     # ---- end to end through the host-buffer C-ABI call
@@ -282,6 +307,44 @@ def main():
         el = time.perf_counter() - t0
         e2e = {"value": ev * N / el / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
 
+    # ---- the same step with the mixed-precision Krylov loop (FP32 JVP, basis and block Jacobi
+    # inside the FP64 Newton iteration), and its distance from the FP64 result
+    mixed = None
+    if rank == 0 and a.precision == "fp64" and not a.no_mixed:
+        z64 = z.clone()
+        prm32 = dgls.default_params(chem, a.order, f_C=WORKLOAD["f_C"], eps_struct=1 - WORKLOAD["porosity"],
+                                    precision=dgls.MIXED, preconditioner={"bj": 0, "cpr": 1, "add": 2}[a.precond],
+                                    precond_every=a.precond_every, reorth=a.reorth)
+        ctx32 = dgls.Context(phase, WORKLOAD["h"], prm32, stream)
+        z32 = ctx32.new_state()
+        for _ in range(max(1, min(a.warmup, 2))):
+            ctx32.step(zn, z32, t, dt, check=False)
+        torch.cuda.synchronize()
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev32 = 0
+        m0.record(stream)
+        for _ in range(a.steps):
+            st32, inf32 = ctx32.step(zn, z32, t, dt, check=False)
+            ev32 += inf32.residual_evals + inf32.jvp_evals
+        m1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = m0.elapsed_time(m1)
+        errs = {}
+        lay = list(zip(ctx.offsets, ctx.lengths))
+        kinds = {"conc": range(0, nl), "eps": range(nl, ctx.n_fields - 2), "pot": range(ctx.n_fields - 2, ctx.n_fields)}
+        for kname, fields in kinds.items():
+            if len(fields) == 0:
+                continue
+            ref = torch.cat([z64[lay[f][0]:lay[f][0] + lay[f][1]] for f in fields])
+            got = torch.cat([z32[lay[f][0]:lay[f][0] + lay[f][1]] for f in fields])
+            errs[kname] = float((got - ref).abs().max() / ref.abs().max())
+        mixed = {"value": ev32 * N / (ms32 / 1e3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms32 / a.steps,
+                 "converged": bool(inf32.converged), "newton_iterations": inf32.newton_iterations,
+                 "gmres_iterations": inf32.gmres_iterations,
+                 "max_rel_diff_vs_fp64": errs, "speedup_vs_fp64_step": (elapsed_ms / a.steps) / (ms32 / a.steps)}
+        ctx32.close()
+        del z32
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu, _, _ = oracle_sample(a, budget_s=15.0)
@@ -294,8 +357,10 @@ def main():
                 "newton_iterations": [i.newton_iterations for i in infos],
                 "gmres_iterations": [i.gmres_iterations for i in infos],
                 "converged": [bool(i.converged) for i in infos],
-                "evals_per_step": evals / a.steps, "gpu_launches": launches, "roofline": roof,
-                "kernel_breakdown_ms": breakdown, "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu}
+                "evals_per_step": evals / a.steps, "gpu_launches": launches,
+                "gram_schmidt_second_passes": reorth, "roofline": roof,
+                "kernel_breakdown_ms": breakdown, "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
+                "mixed_precision": mixed}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -82,6 +82,9 @@ typedef struct {
     int32_t mg_cycles;         /* V-cycles of the potential multigrid per application (1) */
     int32_t precond_every;     /* rebuild the preconditioner every k-th Newton iteration of a step
                                   (0: once per step, at its first iteration) */
+    int32_t reorth;            /* classical Gram-Schmidt in GMRES: 0 = second pass only when the first
+                                  one cancelled, ||w'|| < ||w|| / sqrt(2) (Daniel-Gragg-Kaufman-Stewart,
+                                  default); 1 = always two passes (CGS2) */
 } dg_params;
 
 typedef struct {
@@ -212,6 +215,10 @@ dg_status dg_profile_read(const dg_ctx* ctx, double ms[5], int64_t calls[5]);
 
 /* Number of CUDA kernels this context has launched (monotone counter). */
 int64_t dg_launch_count(const dg_ctx* ctx);
+
+/* Second Gram-Schmidt passes GMRES has taken (monotone counter; with reorth = 1, one per
+ * Arnoldi step). */
+int64_t dg_reorth_count(const dg_ctx* ctx);
 
 /* Workspace bytes held by the context on the device. */
 int64_t dg_workspace_bytes(const dg_ctx* ctx);

@@ -12,6 +12,11 @@
 
 using namespace dgls;
 
+// dres[DRES_ONE] holds the constant 1.0 (written once at setup from pageable memory) for
+// updates that need a device-side unit coefficient.
+constexpr int DRES_ONE = 99;
+static const double kOne = 1.0;
+
 struct dg_ctx {
     dg_params prm;
     DevParams P;
@@ -60,6 +65,7 @@ struct dg_ctx {
     double* d_vals = nullptr;      // equilibrium field values
     // statistics of the last step
     int gmres_its = 0, res_evals = 0, jvp_evals = 0;
+    int64_t reorth_passes = 0;  // second Gram-Schmidt passes taken (diagnostic)
     // optional per-category kernel timing (CUDA events on the context stream)
     bool prof = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
@@ -174,6 +180,7 @@ extern "C" dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t 
     p->preconditioner = 2;
     p->mg_cycles = 1;
     p->precond_every = 0;
+    p->reorth = 0;
     p->newton_max_it = 25;
     p->eta_max = 1e-2;
     p->eta_min = 1e-12;
@@ -212,6 +219,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     if ((prm->order != 0 && prm->order != 1) || (prm->chemistry != 0 && prm->chemistry != 1)) return DG_ERR_ARG;
     if (!(prm->eps_struct > 0 && prm->eps_struct <= 1) || prm->gmres_restart < 1 || prm->gmres_restart > MAXK - 1)
         return DG_ERR_ARG;
+    if (prm->reorth != 0 && prm->reorth != 1) return DG_ERR_ARG;
     const int64_t ncell64 = (int64_t)s->nx * s->ny * s->nz;
     if (ncell64 > 2000000000LL) return DG_ERR_ARG;
     dg_ctx* ctx = new dg_ctx();
@@ -384,9 +392,10 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     if (prm->order == 1 && !mixed) {
         int64_t njn, ngam, nface;
         dg1_lin_sizes(P, &njn, &ngam, &nface);
-        double *jn, *gam, *face, *lgb;
-        AL(jn, njn); AL(gam, ngam); AL(face, nface); AL(lgb, ngam);
+        double *jn, *gam, *face, *lgb, *lflux;
+        AL(jn, njn); AL(gam, ngam); AL(face, nface); AL(lgb, ngam); AL(lflux, dg1_lin_flux_len(P));
         ctx->lin.jn = jn; ctx->lin.gam = gam; ctx->lin.face = face; ctx->lin.gb = lgb; ctx->lin.gbd = ctx->gbd;
+        ctx->lin.flux = lflux;
         ctx->has_lin = true;
     }
     if (prm->preconditioner != 0 && mg_levels_alloc(ctx->mg, nx, ny, nz, ctx->allocs, &ctx->ws_bytes) != cudaSuccess) {
@@ -405,6 +414,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         cudaMemcpyAsync(ctx->d_cmap, cmap.data(), ncell * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         (!sidx.empty() && cudaMemcpyAsync(ctx->d_sidx, sidx.data(), sidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess) ||
         cudaMemcpyAsync(ctx->d_vals, vals, sizeof(vals), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->dres + DRES_ONE, &kOne, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         free_all(ctx);
         delete ctx;
@@ -429,6 +439,7 @@ extern "C" dg_status dg_destroy(dg_ctx* ctx) {
 extern "C" const char* dg_last_error(const dg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 extern "C" int64_t dg_launch_count(const dg_ctx* ctx) { return ctx ? ctx->launches : 0; }
 extern "C" int64_t dg_workspace_bytes(const dg_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
+extern "C" int64_t dg_reorth_count(const dg_ctx* ctx) { return ctx ? ctx->reorth_passes : 0; }
 
 extern "C" dg_status dg_layout(const dg_ctx* ctx, int64_t* n_dof, int32_t* n_fields, int64_t off[10], int64_t len[10]) {
     if (!ctx) return DG_ERR_ARG;
@@ -488,6 +499,10 @@ static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt
         if (e == cudaSuccess && ctx->prm.preconditioner != 0)
             e = ctx->P.order == 0 ? dg0_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb)
                                   : dg1_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb);
+    } else if (ctx->has_lin) {
+        // FP64 DG1: the blocks come from the linearisation at z, which the caller has just built
+        if (!ctx->lin_valid) return fail(ctx, DG_ERR_ARG, "blocks: no linearisation at this state");
+        e = dg1_lin_blocks(ctx->L, ctx->P, ctx->G, z, dt, relax, ctx->lin, ctx->blk);
     } else {
         e = ctx->P.order == 0 ? dg0_blocks<double>(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb)
                               : dg1_blocks<double>(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb);
@@ -497,7 +512,8 @@ static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt
     if (e == cudaSuccess) e = block_invert(ctx->L, ctx->blk, ctx->nblk, ctx->P.nf, ctx->blk32, ctx->d_bad);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
     if (ctx->prm.preconditioner != 0) {
-        e = mg_setup(ctx->L, ctx->P, ctx->G, z, ctx->gb, t, dt, relax, ctx->mg);
+        const double* gbz = (ctx->has_lin && ctx->prm.precision != DG_PREC_MIXED) ? ctx->lin.gb : ctx->gb;
+        e = mg_setup(ctx->L, ctx->P, ctx->G, z, gbz, t, dt, relax, ctx->mg);
         if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("multigrid setup: ") + cudaGetErrorString(e));
     }
     return DG_OK;
@@ -582,7 +598,12 @@ extern "C" dg_status dg_jvp(dg_ctx* ctx, const double* z, double t, double dt, c
 
 extern "C" dg_status dg_block_jacobi(dg_ctx* ctx, const double* z, double t, double dt, const double* v, double* out) {
     if (!ctx || !z || !v || !out || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_block_jacobi: bad argument");
+    if (ctx->has_lin) {
+        CK(dg1_linearize(ctx->L, ctx->P, ctx->G, z, t, dt, 0, ctx->lin));
+        ctx->lin_valid = true;
+    }
     dg_status s = build_precond(ctx, z, t, dt, 0);
+    ctx->lin_valid = false;
     if (s != DG_OK) return s;
     CK(block_apply<double>(ctx->L, ctx->P, ctx->G, ctx->blk, v, out));
     return DG_OK;
@@ -640,8 +661,6 @@ static dg_status gmres_(dg_ctx* ctx, const double* z, double t, double dt, int r
     const void* blkS = mixed ? (const void*)ctx->blk32 : (const void*)ctx->blk;
     if (mixed) CK(to_f32(L, ctx->z32, z, N));
     CK(cudaMemsetAsync(ctx->dz, 0, N * sizeof(double), L.st));
-    ctx->hres[100] = 1.0;
-    CK(cudaMemcpyAsync(ctx->dres + 100, ctx->hres + 100, sizeof(double), cudaMemcpyHostToDevice, L.st));
     double beta0 = -1.0;
     int total = 0;
     std::vector<double> H((m + 1) * m), cs(m), sn(m), gvec(m + 1), y(m);
@@ -657,7 +676,7 @@ static dg_status gmres_(dg_ctx* ctx, const double* z, double t, double dt, int r
             dg_status s = jvp_<S>(ctx, zS, u, t, dt, relax, dt, x, gbS, gbdS);
             if (s != DG_OK) return s;
             CK(neg_scaled<S>(L, ctx->P, ctx->R, dt, w));
-            CK(maxpy<S>(L, w, x, N, N, 1, ctx->dres + 100, -1.0));   // dres[100] = 1
+            CK(maxpy<S>(L, w, x, N, N, 1, ctx->dres + DRES_ONE, -1.0));
         }
         CK(mdot<S>(L, w, N, N, 1, w, ctx->partial, ctx->dres + 64));
         CK(scale_copy<S>(L, V, w, N, ctx->dres + 64, 1.0));
@@ -677,20 +696,34 @@ static dg_status gmres_(dg_ctx* ctx, const double* z, double t, double dt, int r
             if (s != DG_OK) return s;
             s = jvp_<S>(ctx, zS, u, t, dt, relax, dt, w, gbS, gbdS);
             if (s != DG_OK) return s;
+            // classical Gram-Schmidt: h = V^T w (with ||w||^2 in dres[j+1]), w -= V h (with ||w||^2
+            // in dres[64]); a second pass when the first cancelled (always with reorth = 1)
             {
                 ProfScope ps(ctx, 4);
-                CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres));
-                CK(maxpy<S>(L, w, V, N, N, j + 1, ctx->dres, -1.0));
-                CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres + 32));
-                CK(maxpy<S>(L, w, V, N, N, j + 1, ctx->dres + 32, -1.0));
-                CK(mdot<S>(L, w, N, N, 1, w, ctx->partial, ctx->dres + 64));
-                CK(scale_copy<S>(L, V + (int64_t)(j + 1) * N, w, N, ctx->dres + 64, 1.0));
+                CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres, true));
+                CK(maxpy_norm<S>(L, w, V, N, N, j + 1, ctx->dres, ctx->partial, ctx->dres + 64));
             }
             CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 65 * sizeof(double), cudaMemcpyDeviceToHost, L.st));
             s = sync_(ctx);
             if (s != DG_OK) return s;
+            for (int i = 0; i <= j; ++i) H[i * m + j] = ctx->hres[i];
+            if (ctx->prm.reorth == 1 || ctx->hres[64] < 0.5 * ctx->hres[j + 1]) {
+                {
+                    ProfScope ps(ctx, 4);
+                    CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres + 32));
+                    CK(maxpy_norm<S>(L, w, V, N, N, j + 1, ctx->dres + 32, ctx->partial, ctx->dres + 64));
+                }
+                CK(cudaMemcpyAsync(ctx->hres + 32, ctx->dres + 32, 33 * sizeof(double), cudaMemcpyDeviceToHost, L.st));
+                s = sync_(ctx);
+                if (s != DG_OK) return s;
+                for (int i = 0; i <= j; ++i) H[i * m + j] += ctx->hres[32 + i];
+                ++ctx->reorth_passes;
+            }
+            {
+                ProfScope ps(ctx, 4);
+                CK(scale_copy<S>(L, V + (int64_t)(j + 1) * N, w, N, ctx->dres + 64, 1.0));
+            }
             ++total;
-            for (int i = 0; i <= j; ++i) H[i * m + j] = ctx->hres[i] + ctx->hres[32 + i];
             double hn = std::sqrt(ctx->hres[64]);
             if (!std::isfinite(hn)) return fail(ctx, DG_ERR_NONFINITE, "GMRES: non-finite Krylov vector");
             H[(j + 1) * m + j] = hn;
@@ -715,6 +748,8 @@ static dg_status gmres_(dg_ctx* ctx, const double* z, double t, double dt, int r
             for (int k = i + 1; k < j; ++k) acc -= H[i * m + k] * y[k];
             y[i] = H[i * m + i] != 0.0 ? acc / H[i * m + i] : 0.0;
         }
+        // hres[100..] is written only here, after the sync that ended the previous cycle, so the
+        // asynchronous copy below never reads a slot the host is rewriting
         for (int i = 0; i < j; ++i) ctx->hres[100 + i] = y[i];
         CK(cudaMemcpyAsync(ctx->dres + 100, ctx->hres + 100, j * sizeof(double), cudaMemcpyHostToDevice, L.st));
         CK(cudaMemsetAsync(x, 0, N * sizeof(S), L.st));
@@ -723,9 +758,6 @@ static dg_status gmres_(dg_ctx* ctx, const double* z, double t, double dt, int r
         if (s != DG_OK) return s;
         if (mixed) CK(to_f64_add(L, ctx->dz, (const float*)u, 1.0, N));
         else CK(axpby(L, ctx->dz, 1.0, (const double*)u, 1.0, N));
-        // restore dres[100] = 1 for the restart residual update
-        ctx->hres[100] = 1.0;
-        CK(cudaMemcpyAsync(ctx->dres + 100, ctx->hres + 100, sizeof(double), cudaMemcpyHostToDevice, L.st));
         s = sync_(ctx);
         if (s != DG_OK) return s;
     }
@@ -757,15 +789,15 @@ static dg_status newton_(dg_ctx* ctx, const double* zn, double t1, double dt, in
     for (;;) {
         if (nrm <= std::max(ctx->prm.newton_rtol * n0, floor_) || nrm == 0.0) break;
         if (it >= ctx->prm.newton_max_it) { result = fail(ctx, DG_ERR_NOCONV, "Newton: iteration limit"); break; }
-        const int every = ctx->prm.precond_every;
-        if (it == 0 || (every > 0 && it % every == 0)) {
-            s = build_precond(ctx, ctx->zc, t1, dt, relax);
-            if (s != DG_OK) return s;
-        }
         if (ctx->has_lin) {
             ProfScope ps(ctx, 2);
             CK(dg1_linearize(ctx->L, ctx->P, ctx->G, ctx->zc, t1, dt, relax, ctx->lin));
             ctx->lin_valid = true;
+        }
+        const int every = ctx->prm.precond_every;
+        if (it == 0 || (every > 0 && it % every == 0)) {
+            s = build_precond(ctx, ctx->zc, t1, dt, relax);
+            if (s != DG_OK) return s;
         }
         int its = 0;
         // forcing term never asks for more than the Newton tolerance needs

@@ -912,13 +912,15 @@ __global__ void __launch_bounds__(128) k_lin_nodes_apply(const DevParams p, cons
     }
 }
 
-// line part of the JVP (one pass per direction, one thread per (line, voxel))
+// Face-once form of the line part: (1) one thread per +d face (voxel, line) computes the tangent of
+// that face's fluxes for every transport equation once and stores them; (2) one thread per (voxel,
+// line) adds the volume terms and gathers its two faces.  An interior face is then evaluated once
+// instead of once from each side.  flux: [4 lines][NL + 2][n_cell] for the current direction.
 template <class Chem>
-__global__ void __launch_bounds__(128) k_lin_lines_apply(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                         const double* __restrict__ v, const double* __restrict__ gb,
-                                                         const double* __restrict__ gbd, const double* __restrict__ face,
-                                                         int d, double t, int relax, double sc_dt,
-                                                         double* __restrict__ out) {
+__global__ void __launch_bounds__(128) k_lin_face_flux(const DevParams p, const Geo g, const double* __restrict__ v,
+                                                       const double* __restrict__ gb, const double* __restrict__ gbd,
+                                                       const double* __restrict__ face, int d, int relax,
+                                                       double* __restrict__ flux) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 4) return;
     typedef LinShape<Chem> SH;
@@ -929,146 +931,277 @@ __global__ void __launch_bounds__(128) k_lin_lines_apply(const DevParams p, cons
     cell_ijk(p, cell, i, j, k);
     int n0, n1;
     line_nodes(d, q, n0, n1);
-    const int sidx = g.cmap[cell];
-    const bool st = g.phase[cell] == 1;
-    const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h, gq = SQ3 / p.h, pen = p.penalty / p.h;
     const int coord = d == 0 ? i : d == 1 ? j : k;
     const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
     const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
-    bool hasQ[2];
-    int qcell[2];
-    hasQ[0] = coord > 0;
-    hasQ[1] = coord + 1 < ext;
-    qcell[0] = hasQ[0] ? cell - stride : cell;
-    qcell[1] = hasQ[1] ? cell + stride : cell;
-    // face data of the two faces: side 1 = own +d face, side 0 = the -d neighbour's +d face
-    const double* Fd[2];
-    Fd[1] = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
-    Fd[0] = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + qcell[0];
-    auto F = [&](int sd, int kk) { return Fd[sd][(int64_t)kk * p.n_cell]; };
+    double* out = flux + (int64_t)q * (NL + 2) * p.n_cell + cell;
+    auto put = [&](int e, double val) { out[(int64_t)e * p.n_cell] = val; };
+    const double* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
+    auto F = [&](int kk) { return Fd[(int64_t)kk * p.n_cell]; };
+    auto V = [&](int f, int n, int idx) { return v[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
+    const double gq = SQ3 / p.h, pen = p.penalty / p.h;
+    if (coord + 1 >= ext) {
+        // domain face: only the anode face (x = nx) carries a flux with a tangent
+        for (int e = 0; e < NL + 2; ++e) put(e, 0.0);
+        if (d == 0) {
+            double dcLi = ALPHA * V(0, n1, cell) + BETA * V(0, n0, cell);
+            double dphL = ALPHA * V(Chem::PHIL, n1, cell) + BETA * V(Chem::PHIL, n0, cell);
+            double drA = F(0) * dcLi + F(1) * dphL;
+            if (!relax) put(0, drA * p.kAno);
+            put(NL, drA * p.F * p.kAno);
+        }
+        return;
+    }
+    const int qc = cell + stride;
+    const int64_t ol = (int64_t)face_slot(d, +1, q) * p.n_cell + cell, orr = (int64_t)face_slot(d, -1, q) * p.n_cell + qc;
+    const double dgl = gbd[ol], dgr = gbd[orr];
+    const double Hg = F(0), dHg = F(1) * dgl + F(2) * dgr;
+    // Phi^L bracket tangent (own voxel = left)
+    double dBL, BL = F(3 + NL);
+    {
+        double l0 = V(Chem::PHIL, n0, cell), l1 = V(Chem::PHIL, n1, cell);
+        double r0 = V(Chem::PHIL, n0, qc), r1 = V(Chem::PHIL, n1, qc);
+        dBL = ((ALPHA * l1 + BETA * l0) - (ALPHA * r0 + BETA * r1)) * pen - 0.5 * gq * ((l1 - l0) + (r1 - r0));
+    }
+    double fL = 0.0;
+#pragma unroll 1
+    for (int m = 0; m < NL; ++m) {
+        double l0 = V(m, n0, cell), l1 = V(m, n1, cell), r0 = V(m, n0, qc), r1 = V(m, n1, qc);
+        double dcl = ALPHA * l1 + BETA * l0, dcr = ALPHA * r0 + BETA * r1;
+        double dB = (dcl - dcr) * pen - 0.5 * gq * ((l1 - l0) + (r1 - r0));
+        double dterm = dHg * F(3 + m) + Hg * dB;
+        double f = relax ? 0.0 : dterm * p.D0[m];
+        if (p.zc[m] != 0.0) {
+            const int base = 4 + NL + 5 * SH::ci(m);
+            double dHm = F(base + 1) * dgl + F(base + 2) * dcl + F(base + 3) * dgr + F(base + 4) * dcr;
+            double mterm = dHm * BL + F(base) * dBL;
+            if (!relax) f += mterm * p.kappa_m[m];
+            fL += dterm * p.Kd[m] + mterm * p.Km[m];
+        }
+        put(m, f);
+    }
+    put(NL, fL);
+    double fS = 0.0;
+    if (g.phase[cell] == 1 && g.phase[qc] == 1) {
+        const int s = g.cmap[cell], sq = g.cmap[qc];
+        double l0 = V(Chem::PHIS, n0, s), l1 = V(Chem::PHIS, n1, s), r0 = V(Chem::PHIS, n0, sq), r1 = V(Chem::PHIS, n1, sq);
+        fS = (((ALPHA * l1 + BETA * l0) - (ALPHA * r0 + BETA * r1)) * pen - 0.5 * gq * ((l1 - l0) + (r1 - r0))) * p.kappa_s;
+    }
+    put(NL + 1, fS);
+}
+
+template <class Chem>
+__global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                         const double* __restrict__ v, const double* __restrict__ gb,
+                                                         const double* __restrict__ gbd, const double* __restrict__ flux,
+                                                         int d, int relax, double sc_dt, double* __restrict__ out) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 4) return;
+    constexpr int NL = Chem::NL;
+    const int q = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)q * p.n_cell);
+    int i, j, k;
+    cell_ijk(p, cell, i, j, k);
+    int n0, n1;
+    line_nodes(d, q, n0, n1);
+    const int sidx = g.cmap[cell];
+    const bool st = g.phase[cell] == 1;
+    const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h;
+    const int coord = d == 0 ? i : d == 1 ? j : k;
+    const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+    const bool hasL = coord > 0;
+    const double* Fp = flux + (int64_t)q * (NL + 2) * p.n_cell + cell;                 // own +d face
+    const double* Fm = flux + (int64_t)q * (NL + 2) * p.n_cell + (hasL ? cell - stride : cell);
     auto V = [&](int f, int n, int idx) { return v[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
     auto Z = [&](int f, int n, int idx) { return z[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
-    // tangents of the face transport factors (left, right) of both faces
-    double dgl[2] = {0.0, 0.0}, dgr[2] = {0.0, 0.0}, gl[2] = {0.0, 0.0}, gr[2] = {0.0, 0.0};
-#pragma unroll
-    for (int sd = 0; sd < 2; ++sd) {
-        if (!hasQ[sd]) continue;
-        const int L = sd == 1 ? cell : qcell[0], R = sd == 1 ? qcell[1] : cell;
-        int64_t ol = (int64_t)face_slot(d, +1, q) * p.n_cell + L, orr = (int64_t)face_slot(d, -1, q) * p.n_cell + R;
-        gl[sd] = gb[ol];
-        gr[sd] = gb[orr];
-        dgl[sd] = gbd[ol];
-        dgr[sd] = gbd[orr];
-    }
-    const double gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
-    const double dgN0 = gbd[(int64_t)n0 * p.n_cell + cell], dgN1 = gbd[(int64_t)n1 * p.n_cell + cell];
-    // Phi^L: values for the volume term, tangents and the tangent of the face brackets
-    const double P0 = Z(Chem::PHIL, n0, cell), P1 = Z(Chem::PHIL, n1, cell);
-    const double dP0 = V(Chem::PHIL, n0, cell), dP1 = V(Chem::PHIL, n1, cell);
-    double dBL[2] = {0.0, 0.0}, BL[2] = {0.0, 0.0}, dHg[2] = {0.0, 0.0}, Hg[2] = {0.0, 0.0};
-#pragma unroll
-    for (int sd = 0; sd < 2; ++sd) {
-        if (!hasQ[sd]) continue;
-        const int Qc = qcell[sd];
-        double q0 = V(Chem::PHIL, n0, Qc), q1 = V(Chem::PHIL, n1, Qc);
-        // left/right roles: sd = 1 own is left
-        double l0 = sd == 1 ? dP0 : q0, l1 = sd == 1 ? dP1 : q1, r0 = sd == 1 ? q0 : dP0, r1 = sd == 1 ? q1 : dP1;
-        double dj = (ALPHA * l1 + BETA * l0) - (ALPHA * r0 + BETA * r1);
-        double dm = 0.5 * gq * ((l1 - l0) + (r1 - r0));
-        dBL[sd] = dj * pen - dm;
-        BL[sd] = F(sd, 3 + NL);
-        Hg[sd] = F(sd, 0);
-        dHg[sd] = F(sd, 1) * dgl[sd] + F(sd, 2) * dgr[sd];
-    }
-    double aL0 = 0.0, aL1 = 0.0;
-    auto add_face = [&](int sd, double f, double& a0, double& a1) {
-        double ff = f * (sd == 1 ? wf : -wf);
-        if (sd == 1) { a1 += ff * ALPHA; a0 += ff * BETA; }
-        else { a0 += ff * ALPHA; a1 += ff * BETA; }
+    // own face as left voxel: +f (ALPHA to n1, BETA to n0); -d face as right voxel: -f (ALPHA to n0, BETA to n1)
+    auto faces = [&](int e, double& a0, double& a1) {
+        double fp = Fp[(int64_t)e * p.n_cell] * wf;
+        a1 += fp * ALPHA;
+        a0 += fp * BETA;
+        if (hasL) {
+            double fm = Fm[(int64_t)e * p.n_cell] * wf;
+            a0 -= fm * ALPHA;
+            a1 -= fm * BETA;
+        }
     };
     auto store = [&](int f, int idx, double a0, double a1) {
         if (sc_dt > 0.0) { double sc = sc_dt * p.rscale[f]; a0 *= sc; a1 *= sc; }
         out[p.off[f] + (int64_t)n0 * p.flen[f] + idx] += a0;
         out[p.off[f] + (int64_t)n1 * p.flen[f] + idx] += a1;
     };
-    const double dPhi = P1 - P0, ddPhi = dP1 - dP0;
+    const double gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
+    const double dgN0 = gbd[(int64_t)n0 * p.n_cell + cell], dgN1 = gbd[(int64_t)n1 * p.n_cell + cell];
+    const double P0 = Z(Chem::PHIL, n0, cell), P1 = Z(Chem::PHIL, n1, cell);
+    const double dPhi = P1 - P0, ddPhi = V(Chem::PHIL, n1, cell) - V(Chem::PHIL, n0, cell);
     const double gsum = gN0 + gN1, dgsum = dgN0 + dgN1;
+    double aL0 = 0.0, aL1 = 0.0;
 #pragma unroll 1
     for (int m = 0; m < NL; ++m) {
-        const bool charged = p.zc[m] != 0.0;
         const double C0 = Z(m, n0, cell), C1 = Z(m, n1, cell);
         const double dC0 = V(m, n0, cell), dC1 = V(m, n1, cell);
         const double dc = C1 - C0, ddc = dC1 - dC0;
         double a0 = 0.0, a1 = 0.0;
-        {
-            double fl = 0.0;
-            if (!relax) fl = (dgsum * dc + gsum * ddc) * p.D0[m];
-            if (charged) {
-                double msum = gN0 * C0 + gN1 * C1;
-                double dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
-                if (!relax) fl += (dmsum * dPhi + msum * ddPhi) * p.kappa_m[m];
-                double fL = ((dgsum * dc + gsum * ddc) * p.Kd[m] + (dmsum * dPhi + msum * ddPhi) * p.Km[m]) * vol;
-                aL1 += fL;
-                aL0 -= fL;
-            }
-            fl *= vol;
-            a1 += fl;
-            a0 -= fl;
+        double fl = 0.0;
+        if (!relax) fl = (dgsum * dc + gsum * ddc) * p.D0[m];
+        if (p.zc[m] != 0.0) {
+            double msum = gN0 * C0 + gN1 * C1;
+            double dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
+            if (!relax) fl += (dmsum * dPhi + msum * ddPhi) * p.kappa_m[m];
+            double fLv = ((dgsum * dc + gsum * ddc) * p.Kd[m] + (dmsum * dPhi + msum * ddPhi) * p.Km[m]) * vol;
+            aL1 += fLv;
+            aL0 -= fLv;
         }
-#pragma unroll
-        for (int sd = 0; sd < 2; ++sd) {
-            if (!hasQ[sd]) continue;
-            const int Qc = qcell[sd];
-            double q0 = V(m, n0, Qc), q1 = V(m, n1, Qc);
-            double l0 = sd == 1 ? dC0 : q0, l1 = sd == 1 ? dC1 : q1, r0 = sd == 1 ? q0 : dC0, r1 = sd == 1 ? q1 : dC1;
-            double dcl = ALPHA * l1 + BETA * l0, dcr = ALPHA * r0 + BETA * r1;
-            double dB = (dcl - dcr) * pen - 0.5 * gq * ((l1 - l0) + (r1 - r0));
-            double B = F(sd, 3 + m);
-            double dterm = dHg[sd] * B + Hg[sd] * dB;
-            double f = relax ? 0.0 : dterm * p.D0[m];
-            if (charged) {
-                const int base = 4 + NL + 5 * SH::ci(m);
-                double Hm = F(sd, base);
-                double dHm = F(sd, base + 1) * dgl[sd] + F(sd, base + 2) * dcl + F(sd, base + 3) * dgr[sd] +
-                             F(sd, base + 4) * dcr;
-                double mterm = dHm * BL[sd] + Hm * dBL[sd];
-                if (!relax) f += mterm * p.kappa_m[m];
-                add_face(sd, dterm * p.Kd[m] + mterm * p.Km[m], aL0, aL1);
-            }
-            add_face(sd, f, a0, a1);
-        }
-        if (m == 0 && d == 0 && i == p.nx - 1) {
-            double dcLi = ALPHA * dC1 + BETA * dC0, dphL = ALPHA * dP1 + BETA * dP0;
-            double drA = F(1, 0) * dcLi + F(1, 1) * dphL;
-            if (!relax) {
-                double fLi = drA * wf * p.kAno;
-                a1 += fLi * ALPHA;
-                a0 += fLi * BETA;
-            }
-            double fL = drA * wf * p.F * p.kAno;
-            aL1 += fL * ALPHA;
-            aL0 += fL * BETA;
-        }
+        fl *= vol;
+        a1 += fl;
+        a0 -= fl;
+        faces(m, a0, a1);
         store(m, cell, a0, a1);
     }
+    faces(NL, aL0, aL1);
     store(Chem::PHIL, cell, aL0, aL1);
     if (st) {
-        const double S0 = V(Chem::PHIS, n0, sidx), S1 = V(Chem::PHIS, n1, sidx);
         double a0 = 0.0, a1 = 0.0;
-        double fs = (S1 - S0) * 2.0 * p.kappa_s * vol;
+        double fs = (V(Chem::PHIS, n1, sidx) - V(Chem::PHIS, n0, sidx)) * 2.0 * p.kappa_s * vol;
         a1 += fs;
         a0 -= fs;
-#pragma unroll
-        for (int sd = 0; sd < 2; ++sd) {
-            if (!hasQ[sd] || g.phase[qcell[sd]] != 1) continue;
-            const int qs = g.cmap[qcell[sd]];
-            double q0 = V(Chem::PHIS, n0, qs), q1 = V(Chem::PHIS, n1, qs);
-            double l0 = sd == 1 ? S0 : q0, l1 = sd == 1 ? S1 : q1, r0 = sd == 1 ? q0 : S0, r1 = sd == 1 ? q1 : S1;
-            double dj = (ALPHA * l1 + BETA * l0) - (ALPHA * r0 + BETA * r1);
-            double dm = 0.5 * gq * ((l1 - l0) + (r1 - r0));
-            add_face(sd, (dj * pen - dm) * p.kappa_s, a0, a1);
-        }
+        faces(NL + 1, a0, a1);
         store(Chem::PHIS, sidx, a0, a1);
+    }
+}
+
+// Per-node diagonal blocks of S J from the linearisation: column c of node n's block is the
+// linearised operator applied to the unit tangent at (n, c), read at node n's rows.  That tangent
+// touches the node terms (cached Jacobian), the transport factors of this voxel (node n and the
+// face points of the three lines through n), the volume term of each of those lines and the two
+// faces at the ends of each line, where node n enters through its trace (weight ALPHA or BETA)
+// and the normal-derivative term (+-sqrt(3)/h).  One thread per (node, voxel); FMAs only.
+template <class Chem>
+__global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                 const double* __restrict__ gb, const double* __restrict__ gam,
+                                                 const double* __restrict__ jn, const double* __restrict__ face, double dt,
+                                                 int relax, double* __restrict__ blk) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 8) return;
+    typedef LinShape<Chem> SH;
+    constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
+    const int n = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)n * p.n_cell);
+    int i, j, k;
+    cell_ijk(p, cell, i, j, k);
+    const int ph = g.phase[cell];
+    const bool st = ph == 1;
+    const int an[3] = {n & 1, (n >> 1) & 1, (n >> 2) & 1};
+    const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h, gq = SQ3 / p.h, pen = p.penalty / p.h;
+    auto Z = [&](int f, int nn) { return z[p.off[f] + (int64_t)nn * p.flen[f] + cell]; };
+    const double* J = jn + (int64_t)n * NF * NF * p.n_cell + cell;
+    double* B = blk + b * NF * NF;
+#pragma unroll 1
+    for (int c = 0; c < NF; ++c) {
+        if (p.is_struct[c] && !st) {
+            for (int r = 0; r < NF; ++r) B[r * NF + c] = r == c ? 1.0 : 0.0;
+            continue;
+        }
+        double col[NF];
+#pragma unroll
+        for (int r = 0; r < NF; ++r) col[r] = J[(int64_t)(r * NF + c) * p.n_cell];
+        const int dm = c < NL ? c : -1;                      // perturbed species
+        const bool dPL = c == PHIL, dPS = c == PHIS;
+        const double dcs = c < NL ? p.wS[c] : 0.0;          // tangent of c_S at node n
+        const double del = (NS == 2 && st && (c == NL || c == NL + 1)) ? -1.0 : 0.0;   // of eps_L
+        auto dg_at = [&](int slot, double w) {
+            const int64_t o = (int64_t)slot * p.n_cell + cell;
+            return gb[o] * (gam[o] * del - p.visc * dcs) * w;
+        };
+        const double dgN = dg_at(n, 1.0);
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            const int u = d == 0 ? an[1] : an[0];
+            const int w = d == 2 ? an[1] : an[2];
+            const int q = u + 2 * w;
+            int n0, n1;
+            line_nodes(d, q, n0, n1);
+            const bool a1 = n == n1;
+            const double sgn = a1 ? 1.0 : -1.0;
+            const int coord = d == 0 ? i : d == 1 ? j : k;
+            const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
+            const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+            // ---- volume term of the line
+            {
+                const double gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
+                const double dgN0 = a1 ? 0.0 : dgN, dgN1 = a1 ? dgN : 0.0;
+                const double P0 = Z(PHIL, n0), P1 = Z(PHIL, n1);
+                const double dPhi = P1 - P0, ddPhi = dPL ? sgn : 0.0;
+                const double gsum = gN0 + gN1, dgsum = dgN0 + dgN1;
+                double fLsum = 0.0;
+#pragma unroll
+                for (int m = 0; m < NL; ++m) {
+                    const double C0 = Z(m, n0), C1 = Z(m, n1);
+                    const double dC0 = (m == dm && !a1) ? 1.0 : 0.0, dC1 = (m == dm && a1) ? 1.0 : 0.0;
+                    const double dc = C1 - C0, ddc = dC1 - dC0;
+                    double fl = relax ? 0.0 : (dgsum * dc + gsum * ddc) * p.D0[m];
+                    if (p.zc[m] != 0.0) {
+                        const double msum = gN0 * C0 + gN1 * C1;
+                        const double dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
+                        if (!relax) fl += (dmsum * dPhi + msum * ddPhi) * p.kappa_m[m];
+                        fLsum += (dgsum * dc + gsum * ddc) * p.Kd[m] + (dmsum * dPhi + msum * ddPhi) * p.Km[m];
+                    }
+                    col[m] += sgn * fl * vol;
+                }
+                col[PHIL] += sgn * fLsum * vol;
+                if (st && dPS) col[PHIS] += 2.0 * p.kappa_s * vol;
+            }
+            // ---- the two faces of the line: own voxel left (+d face) or right (-d face)
+#pragma unroll 1
+            for (int side = 1; side >= -1; side -= 2) {
+                const bool left = side > 0;
+                const double tw = left ? (a1 ? ALPHA : BETA) : (a1 ? BETA : ALPHA);   // own trace weight
+                const double dBown = left ? tw * pen - 0.5 * gq * sgn : -tw * pen - 0.5 * gq * sgn;
+                const double wrow = left ? wf * tw : -wf * tw;
+                const bool inside = left ? coord + 1 < ext : coord > 0;
+                if (!inside) {
+                    if (left && d == 0) {   // anode face: r_Ano(c_Li, Phi^L) at the face point
+                        const double* Fo = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
+                        const double drA = Fo[0] * (dm == 0 ? tw : 0.0) + Fo[(int64_t)p.n_cell] * (dPL ? tw : 0.0);
+                        if (!relax) col[0] += drA * p.kAno * wrow;
+                        col[PHIL] += drA * p.F * p.kAno * wrow;
+                    }
+                    continue;
+                }
+                const int fc = left ? cell : cell - stride;        // voxel owning the face data
+                const int oc = left ? cell + stride : cell - stride;   // the other voxel
+                const double* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + fc;
+                auto F = [&](int kk) { return Fd[(int64_t)kk * p.n_cell]; };
+                const double dgo = dg_at(face_slot(d, side, q), tw);   // own g at this face point
+                const double dHg = (left ? F(1) : F(2)) * dgo;
+                const double Hg = F(0), BL = F(3 + NL);
+                const double dBL = dPL ? dBown : 0.0;
+                double fL = 0.0;
+#pragma unroll
+                for (int m = 0; m < NL; ++m) {
+                    const double dB = m == dm ? dBown : 0.0;
+                    const double dco = m == dm ? tw : 0.0;
+                    const double dterm = dHg * F(3 + m) + Hg * dB;
+                    double f = relax ? 0.0 : dterm * p.D0[m];
+                    if (p.zc[m] != 0.0) {
+                        const int base = 4 + NL + 5 * SH::ci(m);
+                        const double dHm = left ? F(base + 1) * dgo + F(base + 2) * dco : F(base + 3) * dgo + F(base + 4) * dco;
+                        const double mterm = dHm * BL + F(base) * dBL;
+                        if (!relax) f += mterm * p.kappa_m[m];
+                        fL += dterm * p.Kd[m] + mterm * p.Km[m];
+                    }
+                    col[m] += f * wrow;
+                }
+                col[PHIL] += fL * wrow;
+                if (st && dPS && g.phase[oc] == 1) col[PHIS] += dBown * p.kappa_s * wrow;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NF; ++r) {
+            double o = col[r] * dt * p.rscale[r];
+            if (p.is_struct[r] && !st) o = r == c ? 1.0 : 0.0;
+            B[r * NF + c] = o;
+        }
     }
 }
 
@@ -1080,6 +1213,9 @@ int64_t dg1_lin_sizes(const DevParams& p, int64_t* jn, int64_t* gam, int64_t* fa
     *gam = (int64_t)NG * p.n_cell;
     *face = (int64_t)12 * nfd * p.n_cell;
     return (*jn + *gam + *face) * 8;
+}
+
+int64_t dg1_lin_flux_len(const DevParams& p) { return (int64_t)4 * (p.nl + 2) * p.n_cell;
 }
 
 template <class Chem>
@@ -1105,10 +1241,13 @@ static cudaError_t lin_apply_impl(const LaunchCtx& L, const DevParams& p, const 
                                   double t, int relax, double sc_dt, double* out, const DG1Lin& lin) {
     k_lin_g<Chem><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, v, lin.gb, lin.gam, lin.gbd);
     k_lin_nodes_apply<Chem><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, g, v, lin.jn, sc_dt, out);
-    for (int d = 0; d < 3; ++d)
-        k_lin_lines_apply<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, v, lin.gb, lin.gbd,
-                                                                                        lin.face, d, t, relax, sc_dt, out);
-    *L.counter += 5;
+    for (int d = 0; d < 3; ++d) {
+        k_lin_face_flux<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, v, lin.gb, lin.gbd, lin.face, d,
+                                                                                      relax, lin.flux);
+        k_lin_line_gather<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, v, lin.gb, lin.gbd,
+                                                                                        lin.flux, d, relax, sc_dt, out);
+    }
+    *L.counter += 8;
     return cudaGetLastError();
 }
 
@@ -1116,6 +1255,15 @@ cudaError_t dg1_lin_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, 
                           double t, int relax, double sc_dt, double* out, const DG1Lin& lin) {
     return p.nf == 10 ? lin_apply_impl<ChemTO>(L, p, g, z, v, t, relax, sc_dt, out, lin)
                       : lin_apply_impl<ChemR3>(L, p, g, z, v, t, relax, sc_dt, out, lin);
+}
+
+cudaError_t dg1_lin_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double dt, int relax,
+                           const DG1Lin& lin, double* blk) {
+    const int nb = nblocks((int64_t)p.n_cell * 8, 128);
+    if (p.nf == 10) k_lin_blk<ChemTO><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, blk);
+    else k_lin_blk<ChemR3><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, blk);
+    *L.counter += 1;
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ launchers

@@ -68,7 +68,12 @@ struct DG1Lin {
     double* face;   // [12][NFD][n_cell] face data of the + faces
     double* gb;     // [32][n_cell] transport factors at the linearisation point
     double* gbd;    // [32][n_cell] their tangents (apply scratch)
+    double* flux;   // [4][NL+2][n_cell] face-flux tangents of one direction (apply scratch)
 };
+int64_t dg1_lin_flux_len(const DevParams& p);
+// per-node diagonal blocks of S J (dt-scaled rows) from a current linearisation at z
+cudaError_t dg1_lin_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double dt, int relax,
+                           const DG1Lin& lin, double* blk);
 int64_t dg1_lin_sizes(const DevParams& p, int64_t* jn, int64_t* gam, int64_t* face);
 cudaError_t dg1_linearize(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t, double dt,
                           int relax, const DG1Lin& lin);
@@ -84,7 +89,10 @@ cudaError_t block_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, co
                         const S* v, S* out);
 template <class S>
 cudaError_t mdot(const LaunchCtx& L, const S* V, int64_t ld, int64_t n, int k, const S* w,
-                 double* partial, double* out);
+                 double* partial, double* out, bool self = false);
+template <class S>
+cudaError_t maxpy_norm(const LaunchCtx& L, S* w, const S* V, int64_t ld, int64_t n, int k, const double* h,
+                       double* partial, double* nrm2);
 template <class S>
 cudaError_t maxpy(const LaunchCtx& L, S* w, const S* V, int64_t ld, int64_t n, int k, const double* h,
                   double sign);

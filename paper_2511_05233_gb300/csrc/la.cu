@@ -132,44 +132,57 @@ __global__ void k_finish(const double* __restrict__ partial, int nparts, int k, 
 }
 
 // h[v] = sum_i V[v][i] w[i] for v < k, one pass over w and the k basis vectors.
-template <class S, int KM>
+// With SELF, h[k] = sum_i w[i]^2 as well (the norm that the re-orthogonalisation test needs).
+template <class S, int KM, bool SELF>
 __global__ void __launch_bounds__(RED_THREADS) k_mdot(const S* __restrict__ V, int64_t ld, int64_t n, int k,
                                                       const S* __restrict__ w, double* __restrict__ partial) {
     __shared__ double sh[RED_THREADS];
     // per-thread partial sums in the basis precision (FP32 FMAs for an FP32 basis: on GB300 an
     // FP64 FMA per 4-byte element would make this pass FP64-bound), block and grid sums in FP64
-    S acc[KM];
+    S acc[KM + 1];
 #pragma unroll
-    for (int v = 0; v < KM; ++v) acc[v] = S(0);
+    for (int v = 0; v <= KM; ++v) acc[v] = S(0);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         S wi = w[i];
 #pragma unroll
-        for (int v = 0; v < KM; ++v)
-            if (v < k) acc[v] += V[(int64_t)v * ld + i] * wi;
+        for (int v = 0; v < KM; ++v) acc[v] += V[(int64_t)v * ld + i] * wi;
+        if (SELF) acc[KM] += wi * wi;
     }
-#pragma unroll 1
-    for (int v = 0; v < k; ++v) {
-        double a = 0.0;
 #pragma unroll
-        for (int u = 0; u < KM; ++u)
-            if (u == v) a = (double)acc[u];
-        double s = block_sum(a, sh);
+    for (int v = 0; v < KM + (SELF ? 1 : 0); ++v) {
+        double s = block_sum((double)acc[v], sh);
         if (threadIdx.x == 0) partial[(int64_t)v * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// launch k_mdot instantiated for exactly k vectors: a larger bucket would issue the predicated-off
+// FMAs of the unused accumulators, which on GB300's FP64 pipe costs as much as the real ones
+template <class S, int K, bool SELF>
+static void mdot_launch(const LaunchCtx& L, const S* V, int64_t ld, int64_t n, int k, const S* w, double* partial) {
+    if constexpr (K <= MAXK) {
+        if (k == K) {
+            k_mdot<S, K, SELF><<<RED_BLOCKS, RED_THREADS, 0, L.st>>>(V, ld, n, k, w, partial);
+            return;
+        }
+        mdot_launch<S, K + 1, SELF>(L, V, ld, n, k, w, partial);
     }
 }
 
 template <class S>
 cudaError_t mdot(const LaunchCtx& L, const S* V, int64_t ld, int64_t n, int k, const S* w, double* partial,
-                 double* out) {
-    if (k <= 8) k_mdot<S, 8><<<RED_BLOCKS, RED_THREADS, 0, L.st>>>(V, ld, n, k, w, partial);
-    else if (k <= 16) k_mdot<S, 16><<<RED_BLOCKS, RED_THREADS, 0, L.st>>>(V, ld, n, k, w, partial);
-    else k_mdot<S, MAXK><<<RED_BLOCKS, RED_THREADS, 0, L.st>>>(V, ld, n, k, w, partial);
-    k_finish<<<k < 32 ? k : 32, RED_THREADS, 0, L.st>>>(partial, RED_BLOCKS, k, out);
+                 double* out, bool self) {
+    if (k < 1 || k > MAXK) return cudaErrorInvalidValue;
+    if (self) mdot_launch<S, 1, true>(L, V, ld, n, k, w, partial);
+    else mdot_launch<S, 1, false>(L, V, ld, n, k, w, partial);
+    const int nk = k + (self ? 1 : 0);
+    k_finish<<<nk < 32 ? nk : 32, RED_THREADS, 0, L.st>>>(partial, RED_BLOCKS, nk, out);
     *L.counter += 2;
     return cudaGetLastError();
 }
-template cudaError_t mdot<double>(const LaunchCtx&, const double*, int64_t, int64_t, int, const double*, double*, double*);
-template cudaError_t mdot<float>(const LaunchCtx&, const float*, int64_t, int64_t, int, const float*, double*, double*);
+template cudaError_t mdot<double>(const LaunchCtx&, const double*, int64_t, int64_t, int, const double*, double*, double*,
+                                  bool);
+template cudaError_t mdot<float>(const LaunchCtx&, const float*, int64_t, int64_t, int, const float*, double*, double*,
+                                 bool);
 
 // w += sign * sum_v h[v] V[v]
 template <class S>
@@ -193,6 +206,40 @@ cudaError_t maxpy(const LaunchCtx& L, S* w, const S* V, int64_t ld, int64_t n, i
 }
 template cudaError_t maxpy<double>(const LaunchCtx&, double*, const double*, int64_t, int64_t, int, const double*, double);
 template cudaError_t maxpy<float>(const LaunchCtx&, float*, const float*, int64_t, int64_t, int, const double*, double);
+
+// w -= sum_v h[v] V[v] and nrm2 = sum_i w[i]^2 of the updated vector, in one pass (fixed grid).
+template <class S>
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(S* __restrict__ w, const S* __restrict__ V, int64_t ld,
+                                                            int64_t n, int k, const double* __restrict__ h,
+                                                            double* __restrict__ partial) {
+    __shared__ S hs[MAXK];
+    __shared__ double sh[RED_THREADS];
+    if (threadIdx.x < k) hs[threadIdx.x] = (S)(-h[threadIdx.x]);
+    __syncthreads();
+    S nrm = S(0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        S acc = w[i];
+        for (int v = 0; v < k; ++v) acc += hs[v] * V[(int64_t)v * ld + i];
+        w[i] = acc;
+        nrm += acc * acc;
+    }
+    double s = block_sum((double)nrm, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+template <class S>
+cudaError_t maxpy_norm(const LaunchCtx& L, S* w, const S* V, int64_t ld, int64_t n, int k, const double* h,
+                       double* partial, double* nrm2) {
+    if (k < 1 || k > MAXK) return cudaErrorInvalidValue;
+    k_maxpy_norm<S><<<RED_BLOCKS, RED_THREADS, 0, L.st>>>(w, V, ld, n, k, h, partial);
+    k_finish<<<1, RED_THREADS, 0, L.st>>>(partial, RED_BLOCKS, 1, nrm2);
+    *L.counter += 2;
+    return cudaGetLastError();
+}
+template cudaError_t maxpy_norm<double>(const LaunchCtx&, double*, const double*, int64_t, int64_t, int, const double*,
+                                        double*, double*);
+template cudaError_t maxpy_norm<float>(const LaunchCtx&, float*, const float*, int64_t, int64_t, int, const double*,
+                                       double*, double*);
 
 // dst = a * src / sqrt(*nrm2_dev) (nrm2_dev holds a squared norm) or dst = a * src if nrm2_dev is null
 template <class S>

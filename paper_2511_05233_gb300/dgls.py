@@ -31,7 +31,8 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("gmres_restart", C.c_int32), ("gmres_max_it", C.c_int32),
                 ("newton_rtol", C.c_double), ("newton_atol", C.c_double), ("newton_max_it", C.c_int32),
                 ("eta_max", C.c_double), ("eta_min", C.c_double), ("hbm_budget_bytes", C.c_int64),
-                ("preconditioner", C.c_int32), ("mg_cycles", C.c_int32), ("precond_every", C.c_int32)]
+                ("preconditioner", C.c_int32), ("mg_cycles", C.c_int32), ("precond_every", C.c_int32),
+                ("reorth", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -94,6 +95,7 @@ def lib():
             "dg_profile": (C.c_int, [_P, C.c_int32]),
             "dg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "dg_launch_count": (C.c_int64, [_P]),
+            "dg_reorth_count": (C.c_int64, [_P]),
             "dg_workspace_bytes": (C.c_int64, [_P]),
         }
         for name, (res, args) in sig.items():
@@ -278,6 +280,9 @@ class Context:
 
     def launch_count(self):
         return int(self._lib.dg_launch_count(self._h))
+
+    def reorth_count(self):
+        return int(self._lib.dg_reorth_count(self._h))
 
     def workspace_bytes(self):
         return int(self._lib.dg_workspace_bytes(self._h))

@@ -64,15 +64,23 @@ def test_dg1_point_block_parity():
     assert np.abs(to_host(out) - ref).max() <= 1e-9 * np.abs(ref).max()
 
 
-def test_dg1_step_parity():
+@pytest.mark.parametrize("reorth", [0, 1])
+def test_dg1_step_parity(reorth):
+    """One implicit Euler step with either Gram-Schmidt rule in GMRES (second pass when the first
+    cancelled, or always): both reach the oracle's exact-Newton state."""
     model, grid, phase, z0, z = make_case("reduced3", 1, (6, 4, 3))
-    ctx = gpu_context(model, phase)
+    ctx = gpu_context(model, phase, reorth=reorth)
     ref, info = newton.implicit_euler_step(model, grid, z, 0.0, 1e-3)
     assert info.converged
     out = to_dev(np.zeros_like(z))
     st, ginfo = ctx.step(to_dev(z), out, 0.0, 1e-3)
     assert ginfo.converged
     assert_state_close(model, grid, to_host(out), ref, 1e-8)
+    passes = ctx.reorth_count()
+    if reorth == 1:
+        assert passes == ginfo.gmres_iterations
+    else:
+        assert 0 <= passes <= ginfo.gmres_iterations
 
 
 def test_dg1_cell_voltage_and_ledger():
