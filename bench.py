@@ -36,8 +36,9 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--precond", default="add", choices=["cpr", "bj", "add"])
     ap.add_argument("--precond-every", type=int, default=0)
-    ap.add_argument("--reorth", type=int, default=0, choices=[0, 1],
-                    help="GMRES Gram-Schmidt: 0 second pass when needed, 1 always")
+    ap.add_argument("--reorth", type=int, default=2, choices=[0, 1, 2],
+                    help="GMRES Gram-Schmidt: 2 one pass (default), 0 second pass when needed, 1 always")
+    ap.add_argument("--mg-cycles", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
@@ -66,9 +67,10 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # FP64 operations per unknown of one linearised DG1 Jacobian-vector product of the Tradeoff
 # Chemistry (transport-factor tangents, node Jacobians, face fluxes once per face, line gather):
 # 2 x DFMA + DADD + DMUL thread instructions of the eight launches of one product counted by ncu
-# at 64^3 (17,428,880 unknowns), / unknowns.  DRAM bytes of the same launches, per unknown.
-LIN_JVP_DG1_FLOP_PER_DOF = 118.1
-LIN_JVP_DG1_DRAM_BYTES_PER_DOF = 307.6
+# at 64^3 (17,428,880 unknowns), / unknowns.  DRAM bytes of the same launches per unknown, or
+# None when the kernels have changed since the counters were taken.
+LIN_JVP_DG1_FLOP_PER_DOF = 90.6
+LIN_JVP_DG1_DRAM_BYTES_PER_DOF = None
 
 
 class ClockSampler:
@@ -177,7 +179,7 @@ def config_dict(a):
                         f"Gaussian random-field structure porosity {WORKLOAD['porosity']}, correlation length {WORKLOAD['corr_len']} voxels, "
                         f"one implicit Euler step dt={WORKLOAD['dt']} s at {WORKLOAD['f_C']}C, Newton-GMRES(30) rtol 1e-10",
             "grid": a.n, "order": a.order, "chemistry": a.chem, "precision": a.precision, "preconditioner": a.precond,
-            "gram_schmidt": "cgs2" if a.reorth else "cgs+dgks",
+            "gram_schmidt": ["cgs+dgks", "cgs2", "cgs"][a.reorth], "mg_cycles": a.mg_cycles,
             "l2": "inputs larger than L2 (every state vector > 129 MB)"}
 
 
@@ -205,7 +207,7 @@ def main():
     prm = dgls.default_params(chem, a.order, f_C=WORKLOAD["f_C"], eps_struct=1 - WORKLOAD["porosity"],
                               precision=dgls.MIXED if a.precision == "mixed" else dgls.FP64,
                               preconditioner={"bj": 0, "cpr": 1, "add": 2}[a.precond],
-                              precond_every=a.precond_every, reorth=a.reorth)
+                              precond_every=a.precond_every, reorth=a.reorth, mg_cycles=a.mg_cycles)
     stream = torch.cuda.current_stream()
     ctx = dgls.Context(phase, WORKLOAD["h"], prm, stream)
     N = ctx.n_dof
@@ -276,11 +278,12 @@ def main():
             roof = {"kernel": "jvp (linearised DG1 apply: k_lin_g, k_lin_nodes_apply, k_lin_face_flux, "
                               "k_lin_line_gather)",
                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": achieved / FP64_PEAK_GFLOPS, "traffic": LIN_JVP_DG1_DRAM_BYTES_PER_DOF * N,
+                    "frac": achieved / FP64_PEAK_GFLOPS,
+                    "traffic": LIN_JVP_DG1_DRAM_BYTES_PER_DOF * N if LIN_JVP_DG1_DRAM_BYTES_PER_DOF else None,
                     "flop_per_dof": LIN_JVP_DG1_FLOP_PER_DOF, "avg_launch_ms": avg_ms,
                     "peak_source": "derived FP64 peak (152 SMs x 4 FLOP/clk x 2.07 GHz)",
-                    "hbm_frac_of_measured": LIN_JVP_DG1_DRAM_BYTES_PER_DOF * N / (avg_ms / 1e3) / 1e9
-                    / peaks.get("hbm_gbs", 6800.0)}
+                    "hbm_frac_of_measured": (LIN_JVP_DG1_DRAM_BYTES_PER_DOF * N / (avg_ms / 1e3) / 1e9
+                                             / peaks.get("hbm_gbs", 6800.0)) if LIN_JVP_DG1_DRAM_BYTES_PER_DOF else None}
         else:
             bpd = {"residual": 24.0, "jvp": 24.0 if a.precision == "fp64" else 12.0}.get(cat)
             if bpd:
@@ -314,7 +317,7 @@ def main():
         z64 = z.clone()
         prm32 = dgls.default_params(chem, a.order, f_C=WORKLOAD["f_C"], eps_struct=1 - WORKLOAD["porosity"],
                                     precision=dgls.MIXED, preconditioner={"bj": 0, "cpr": 1, "add": 2}[a.precond],
-                                    precond_every=a.precond_every, reorth=a.reorth)
+                                    precond_every=a.precond_every, reorth=a.reorth, mg_cycles=a.mg_cycles)
         ctx32 = dgls.Context(phase, WORKLOAD["h"], prm32, stream)
         z32 = ctx32.new_state()
         for _ in range(max(1, min(a.warmup, 2))):

@@ -82,9 +82,10 @@ typedef struct {
     int32_t mg_cycles;         /* V-cycles of the potential multigrid per application (1) */
     int32_t precond_every;     /* rebuild the preconditioner every k-th Newton iteration of a step
                                   (0: once per step, at its first iteration) */
-    int32_t reorth;            /* classical Gram-Schmidt in GMRES: 0 = second pass only when the first
-                                  one cancelled, ||w'|| < ||w|| / sqrt(2) (Daniel-Gragg-Kaufman-Stewart,
-                                  default); 1 = always two passes (CGS2) */
+    int32_t reorth;            /* classical Gram-Schmidt in GMRES: 2 = one pass (PETSc's default GMRES
+                                  orthogonalisation, the solver of Sec. 2.7; default); 0 = a second
+                                  pass when the first cancelled, ||w'|| < ||w|| / sqrt(2)
+                                  (Daniel-Gragg-Kaufman-Stewart); 1 = always two passes (CGS2) */
 } dg_params;
 
 typedef struct {

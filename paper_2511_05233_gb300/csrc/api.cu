@@ -180,7 +180,7 @@ extern "C" dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t 
     p->preconditioner = 2;
     p->mg_cycles = 1;
     p->precond_every = 0;
-    p->reorth = 0;
+    p->reorth = 2;
     p->newton_max_it = 25;
     p->eta_max = 1e-2;
     p->eta_min = 1e-12;
@@ -219,7 +219,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     if ((prm->order != 0 && prm->order != 1) || (prm->chemistry != 0 && prm->chemistry != 1)) return DG_ERR_ARG;
     if (!(prm->eps_struct > 0 && prm->eps_struct <= 1) || prm->gmres_restart < 1 || prm->gmres_restart > MAXK - 1)
         return DG_ERR_ARG;
-    if (prm->reorth != 0 && prm->reorth != 1) return DG_ERR_ARG;
+    if (prm->reorth < 0 || prm->reorth > 2) return DG_ERR_ARG;
     const int64_t ncell64 = (int64_t)s->nx * s->ny * s->nz;
     if (ncell64 > 2000000000LL) return DG_ERR_ARG;
     dg_ctx* ctx = new dg_ctx();
@@ -470,7 +470,7 @@ static cudaError_t jvp_kernels(dg_ctx* ctx, const S* z, const S* v, double t, do
                                S* gb, S* gbd) {
     if constexpr (std::is_same<S, double>::value) {
         if (ctx->has_lin && ctx->lin_valid)
-            return dg1_lin_apply(ctx->L, ctx->P, ctx->G, z, v, t, relax, sc_dt, out, ctx->lin);
+            return dg1_lin_apply(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, ctx->lin);
     }
     return ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd)
                              : dg1_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd);
@@ -697,7 +697,7 @@ static dg_status gmres_(dg_ctx* ctx, const double* z, double t, double dt, int r
             s = jvp_<S>(ctx, zS, u, t, dt, relax, dt, w, gbS, gbdS);
             if (s != DG_OK) return s;
             // classical Gram-Schmidt: h = V^T w (with ||w||^2 in dres[j+1]), w -= V h (with ||w||^2
-            // in dres[64]); a second pass when the first cancelled (always with reorth = 1)
+            // in dres[64]); a second pass when the first cancelled (reorth = 0) or always (reorth = 1)
             {
                 ProfScope ps(ctx, 4);
                 CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres, true));
@@ -707,7 +707,7 @@ static dg_status gmres_(dg_ctx* ctx, const double* z, double t, double dt, int r
             s = sync_(ctx);
             if (s != DG_OK) return s;
             for (int i = 0; i <= j; ++i) H[i * m + j] = ctx->hres[i];
-            if (ctx->prm.reorth == 1 || ctx->hres[64] < 0.5 * ctx->hres[j + 1]) {
+            if (ctx->prm.reorth == 1 || (ctx->prm.reorth == 0 && ctx->hres[64] < 0.5 * ctx->hres[j + 1])) {
                 {
                     ProfScope ps(ctx, 4);
                     CK(mdot<S>(L, V, N, N, j + 1, w, ctx->partial, ctx->dres + 32));

@@ -678,8 +678,9 @@ __global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, 
 // divisions along with the tangents; on GB300 that keeps the FP64 pipe ~85 % busy while HBM idles.
 // During one Newton iteration the linearisation point z is fixed, so the value side is computed
 // once and cached (HBM is cheap here, FP64 issue is not):
-//   jn   [8 nodes][NF x NF][voxel]  derivative of the node terms (storage + sources) w.r.t. the
-//                                    node's own unknowns;
+//   jn   [8 nodes][NF x NF][structure voxel]  derivative of the node terms (storage + sources)
+//                                    w.r.t. the node's own unknowns (pore and separator voxels:
+//                                    the storage diagonal, computed where it is needed);
 //   gam  [32 slots][voxel]          dg = g (gam d eps_L - visc d c_S): gam = 3/(2 eps_L) or 0;
 //   face [3 dirs x 4 lines][NFD][voxel] for the +d face of each voxel: {g}_H and its two partial
 //        derivatives, the flux brackets (pen [[psi]] - {d_n psi}) of every liquid field and of
@@ -728,42 +729,55 @@ __global__ void __launch_bounds__(128) k_lin_gam(const DevParams p, const Geo g,
             }
 }
 
-// node Jacobians: one thread per (node, voxel), NF seeded evaluations of the node terms
+// node Jacobians of the structure voxels: one thread per (node, structure voxel), NF seeded
+// evaluations of the node terms.  Elsewhere (pore, separator) the node terms are the storage terms
+// alone and their Jacobian is the diagonal that make_node_diag gives, so nothing is stored there.
 template <class Chem>
 __global__ void __launch_bounds__(64) k_lin_nodes_build(const DevParams p, const Geo g, const double* __restrict__ z,
                                                         double t, double dt, int relax, double* __restrict__ jn) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= (int64_t)p.n_cell * 8) return;
+    if (b >= (int64_t)p.n_struct * 8) return;
     typedef Dual<double> T;
     constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
-    const int n = (int)(b / p.n_cell);
-    const int cell = (int)(b - (int64_t)n * p.n_cell);
-    const int ph = g.phase[cell];
-    const int sidx = g.cmap[cell];
-    const bool st = ph == 1;
+    const int n = (int)(b / p.n_struct);
+    const int sidx = (int)(b - (int64_t)n * p.n_struct);
+    const int cell = g.sidx[sidx];
     double old[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) old[f] = 0.0;
     const double tH = smooth_step(t);
-    double* J = jn + (int64_t)n * NF * NF * p.n_cell + cell;     // [row*NF + col][voxel] within the node
+    double* J = jn + (int64_t)n * NF * NF * p.n_struct + sidx;    // [row*NF + col][structure voxel]
 #pragma unroll 1
     for (int col = 0; col < NF; ++col) {
         T c[NL], es[2], phiL, phiS;
 #pragma unroll
         for (int m = 0; m < NL; ++m) c[m] = Make<T>::var(ld(z, p, m, n, cell), col == m ? 1.0 : 0.0);
-        es[0] = es[1] = Make<T>::c(0.0);
-        phiS = Make<T>::c(0.0);
         phiL = Make<T>::var(ld(z, p, PHIL, n, cell), col == PHIL ? 1.0 : 0.0);
-        if (st) {
+        es[0] = es[1] = Make<T>::c(0.0);
 #pragma unroll
-            for (int q = 0; q < NS; ++q) es[q] = Make<T>::var(ld(z, p, NL + q, n, sidx), col == NL + q ? 1.0 : 0.0);
-            phiS = Make<T>::var(ld(z, p, PHIS, n, sidx), col == PHIS ? 1.0 : 0.0);
-        }
+        for (int q = 0; q < NS; ++q) es[q] = Make<T>::var(ld(z, p, NL + q, n, sidx), col == NL + q ? 1.0 : 0.0);
+        phiS = Make<T>::var(ld(z, p, PHIS, n, sidx), col == PHIS ? 1.0 : 0.0);
         T R[NF];
-        node_terms<Chem, T>(p, ph, c, es, phiL, phiS, old, tH, dt, relax, R);
+        node_terms<Chem, T>(p, 1, c, es, phiL, phiS, old, tH, dt, relax, R);
 #pragma unroll
-        for (int row = 0; row < NF; ++row) J[(int64_t)(row * NF + col) * p.n_cell] = R[row].d;
+        for (int row = 0; row < NF; ++row) J[(int64_t)(row * NF + col) * p.n_struct] = R[row].d;
     }
+}
+
+// Diagonal node Jacobian of a pore or separator voxel (node terms without sources):
+// d R_m / d c_m = eps_L M / dt (M / dt while relaxing) and d R_PhiL / d Phi^L = M / dt while
+// relaxing, 0 otherwise.  Computed on the host once per call (no FP64 division per thread).
+struct NodeDiag {
+    double c_pore, c_sep, phi;
+};
+
+static NodeDiag make_node_diag(const DevParams& p, double dt, int relax) {
+    const double Mdt = (p.V / 8.0) / dt;
+    NodeDiag nd;
+    nd.c_pore = relax ? Mdt : 1.0 * Mdt;
+    nd.c_sep = relax ? Mdt : p.eps_sep * Mdt;
+    nd.phi = relax ? Mdt : 0.0;
+    return nd;
 }
 
 // face data of the +d face of every voxel (and the anode derivatives on the x = nx face)
@@ -882,44 +896,92 @@ __global__ void __launch_bounds__(128) k_lin_g(const DevParams p, const Geo g, c
 
 // node part of the JVP: out = J_node v_node (writes, the line passes add)
 template <class Chem>
-__global__ void __launch_bounds__(128) k_lin_nodes_apply(const DevParams p, const Geo g, const double* __restrict__ v,
-                                                         const double* __restrict__ jn, double sc_dt,
-                                                         double* __restrict__ out) {
+__global__ void __launch_bounds__(128) k_lin_nodes_apply(const DevParams p, const NodeDiag nd, const Geo g,
+                                                         const double* __restrict__ v, const double* __restrict__ jn,
+                                                         double sc_dt, double* __restrict__ out) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 8) return;
-    constexpr int NF = Chem::NF;
+    constexpr int NF = Chem::NF, NL = Chem::NL, PHIL = Chem::PHIL;
     const int n = (int)(b / p.n_cell);
     const int cell = (int)(b - (int64_t)n * p.n_cell);
+    const int ph = g.phase[cell];
+    if (ph != 1) {
+        const double dc = ph == 2 ? nd.c_sep : nd.c_pore, dphi = nd.phi;
+#pragma unroll
+        for (int f = 0; f <= PHIL; ++f) {
+            if (f >= NL && f != PHIL) continue;     // solid fields do not live here
+            const int64_t idx = p.off[f] + (int64_t)n * p.flen[f] + cell;
+            double acc = (f == PHIL ? dphi : dc) * v[idx];
+            if (sc_dt > 0.0) acc *= sc_dt * p.rscale[f];
+            out[idx] = acc;
+        }
+        return;
+    }
     const int sidx = g.cmap[cell];
-    const bool st = g.phase[cell] == 1;
     double x[NF];
     int64_t idx[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        idx[f] = (!p.is_struct[f]) ? p.off[f] + (int64_t)n * p.flen[f] + cell
-                                   : (st ? p.off[f] + (int64_t)n * p.flen[f] + sidx : -1);
-        x[f] = idx[f] >= 0 ? v[idx[f]] : 0.0;
+        idx[f] = p.off[f] + (int64_t)n * p.flen[f] + (p.is_struct[f] ? sidx : cell);
+        x[f] = v[idx[f]];
     }
-    const double* J = jn + (int64_t)n * NF * NF * p.n_cell + cell;
+    const double* J = jn + (int64_t)n * NF * NF * p.n_struct + sidx;
 #pragma unroll
     for (int r = 0; r < NF; ++r) {
-        if (idx[r] < 0) continue;
         double acc = 0.0;
 #pragma unroll
-        for (int c = 0; c < NF; ++c) acc += J[(int64_t)(r * NF + c) * p.n_cell] * x[c];
+        for (int c = 0; c < NF; ++c) acc += J[(int64_t)(r * NF + c) * p.n_struct] * x[c];
         if (sc_dt > 0.0) acc *= sc_dt * p.rscale[r];
         out[idx[r]] = acc;
     }
 }
 
+// Per-call constants of the linearised line part, with the area / volume weights and the row
+// scales (sc_dt * rscale, or 1 for the unscaled product) folded in, so that the two kernels below
+// spend their FP64 issue slots on the tangents only.  While relaxing, the species rows carry no
+// transport and no anode term.
+struct LinK {
+    double fD[6], fK[6], fKd[6], fKm[6];   // face: D0 and kappa_m (species row), K^d and K^m (Phi^L row)
+    double vD[6], vK[6], vKd[6], vKm[6];   // volume: the same with the volume weight
+    double fS, vS;                         // Phi^S: kappa_s at faces, 2 kappa_s in the volume
+    double aLi, aL;                        // anode: k_Ano (Li+ row), F k_Ano (Phi^L row)
+    double cl0, cl1, cr0, cr1;             // pen [[psi]] - {d_n psi} as weights of the four line values
+};
+
+static LinK make_link(const DevParams& p, int nl, int philf, int phisf, int relax, double sc_dt) {
+    LinK k;
+    const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h, h2 = 0.5 * SQ3 / p.h, pen = p.penalty / p.h;
+    auto sc = [&](int f) { return sc_dt > 0.0 ? sc_dt * p.rscale[f] : 1.0; };
+    const double sL = sc(philf), sS = sc(phisf);
+    for (int m = 0; m < 6; ++m) {
+        const bool on = m < nl;
+        const double sm = on ? sc(m) : 0.0;
+        const double D0 = on && !relax ? p.D0[m] : 0.0, km = on && !relax ? p.kappa_m[m] : 0.0;
+        const double Kd = on ? p.Kd[m] : 0.0, Km = on ? p.Km[m] : 0.0;
+        k.fD[m] = D0 * wf * sm; k.fK[m] = km * wf * sm; k.fKd[m] = Kd * wf * sL; k.fKm[m] = Km * wf * sL;
+        k.vD[m] = D0 * vol * sm; k.vK[m] = km * vol * sm; k.vKd[m] = Kd * vol * sL; k.vKm[m] = Km * vol * sL;
+    }
+    k.fS = p.kappa_s * wf * sS;
+    k.vS = 2.0 * p.kappa_s * vol * sS;
+    k.aLi = relax ? 0.0 : p.kAno * wf * sc(0);
+    k.aL = p.F * p.kAno * wf * sL;
+    // (ALPHA l1 + BETA l0 - ALPHA r0 - BETA r1) pen - h2 ((l1 - l0) + (r1 - r0))
+    k.cl1 = ALPHA * pen - h2;
+    k.cl0 = BETA * pen + h2;
+    k.cr0 = -ALPHA * pen + h2;
+    k.cr1 = -BETA * pen - h2;
+    return k;
+}
+
 // Face-once form of the line part: (1) one thread per +d face (voxel, line) computes the tangent of
-// that face's fluxes for every transport equation once and stores them; (2) one thread per (voxel,
-// line) adds the volume terms and gathers its two faces.  An interior face is then evaluated once
-// instead of once from each side.  flux: [4 lines][NL + 2][n_cell] for the current direction.
+// that face's fluxes for every transport equation once and stores them, already weighted and
+// row-scaled; (2) one thread per (voxel, line) adds the volume terms and gathers its two faces.
+// An interior face is evaluated once instead of once from each side.
+// flux: [4 lines][NL + 2][n_cell] for the current direction.
 template <class Chem>
-__global__ void __launch_bounds__(128) k_lin_face_flux(const DevParams p, const Geo g, const double* __restrict__ v,
-                                                       const double* __restrict__ gb, const double* __restrict__ gbd,
-                                                       const double* __restrict__ face, int d, int relax,
+__global__ void __launch_bounds__(128) k_lin_face_flux(const DevParams p, const LinK K, const Geo g,
+                                                       const double* __restrict__ v, const double* __restrict__ gbd,
+                                                       const double* __restrict__ face, int d,
                                                        double* __restrict__ flux) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 4) return;
@@ -939,44 +1001,44 @@ __global__ void __launch_bounds__(128) k_lin_face_flux(const DevParams p, const 
     const double* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
     auto F = [&](int kk) { return Fd[(int64_t)kk * p.n_cell]; };
     auto V = [&](int f, int n, int idx) { return v[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
-    const double gq = SQ3 / p.h, pen = p.penalty / p.h;
     if (coord + 1 >= ext) {
         // domain face: only the anode face (x = nx) carries a flux with a tangent
-        for (int e = 0; e < NL + 2; ++e) put(e, 0.0);
+        double fLi = 0.0, fL = 0.0;
         if (d == 0) {
             double dcLi = ALPHA * V(0, n1, cell) + BETA * V(0, n0, cell);
             double dphL = ALPHA * V(Chem::PHIL, n1, cell) + BETA * V(Chem::PHIL, n0, cell);
             double drA = F(0) * dcLi + F(1) * dphL;
-            if (!relax) put(0, drA * p.kAno);
-            put(NL, drA * p.F * p.kAno);
+            fLi = drA * K.aLi;
+            fL = drA * K.aL;
         }
+        put(0, fLi);
+        for (int e = 1; e < NL + 2; ++e) put(e, e == NL ? fL : 0.0);
         return;
     }
     const int qc = cell + stride;
     const int64_t ol = (int64_t)face_slot(d, +1, q) * p.n_cell + cell, orr = (int64_t)face_slot(d, -1, q) * p.n_cell + qc;
     const double dgl = gbd[ol], dgr = gbd[orr];
     const double Hg = F(0), dHg = F(1) * dgl + F(2) * dgr;
-    // Phi^L bracket tangent (own voxel = left)
-    double dBL, BL = F(3 + NL);
-    {
-        double l0 = V(Chem::PHIL, n0, cell), l1 = V(Chem::PHIL, n1, cell);
-        double r0 = V(Chem::PHIL, n0, qc), r1 = V(Chem::PHIL, n1, qc);
-        dBL = ((ALPHA * l1 + BETA * l0) - (ALPHA * r0 + BETA * r1)) * pen - 0.5 * gq * ((l1 - l0) + (r1 - r0));
-    }
+    auto bracket = [&](double l0, double l1, double r0, double r1) {
+        return K.cl1 * l1 + K.cl0 * l0 + K.cr0 * r0 + K.cr1 * r1;
+    };
+    const double BL = F(3 + NL);
+    const double dBL = bracket(V(Chem::PHIL, n0, cell), V(Chem::PHIL, n1, cell), V(Chem::PHIL, n0, qc),
+                               V(Chem::PHIL, n1, qc));
     double fL = 0.0;
-#pragma unroll 1
+#pragma unroll
     for (int m = 0; m < NL; ++m) {
-        double l0 = V(m, n0, cell), l1 = V(m, n1, cell), r0 = V(m, n0, qc), r1 = V(m, n1, qc);
-        double dcl = ALPHA * l1 + BETA * l0, dcr = ALPHA * r0 + BETA * r1;
-        double dB = (dcl - dcr) * pen - 0.5 * gq * ((l1 - l0) + (r1 - r0));
-        double dterm = dHg * F(3 + m) + Hg * dB;
-        double f = relax ? 0.0 : dterm * p.D0[m];
+        const double l0 = V(m, n0, cell), l1 = V(m, n1, cell), r0 = V(m, n0, qc), r1 = V(m, n1, qc);
+        const double dterm = dHg * F(3 + m) + Hg * bracket(l0, l1, r0, r1);
+        double f = dterm * K.fD[m];
         if (p.zc[m] != 0.0) {
+            fL += dterm * K.fKd[m];
             const int base = 4 + NL + 5 * SH::ci(m);
-            double dHm = F(base + 1) * dgl + F(base + 2) * dcl + F(base + 3) * dgr + F(base + 4) * dcr;
-            double mterm = dHm * BL + F(base) * dBL;
-            if (!relax) f += mterm * p.kappa_m[m];
-            fL += dterm * p.Kd[m] + mterm * p.Km[m];
+            const double dcl = ALPHA * l1 + BETA * l0, dcr = ALPHA * r0 + BETA * r1;
+            const double dHm = F(base + 1) * dgl + F(base + 2) * dcl + F(base + 3) * dgr + F(base + 4) * dcr;
+            const double mterm = dHm * BL + F(base) * dBL;
+            f += mterm * K.fK[m];
+            fL += mterm * K.fKm[m];
         }
         put(m, f);
     }
@@ -984,17 +1046,17 @@ __global__ void __launch_bounds__(128) k_lin_face_flux(const DevParams p, const 
     double fS = 0.0;
     if (g.phase[cell] == 1 && g.phase[qc] == 1) {
         const int s = g.cmap[cell], sq = g.cmap[qc];
-        double l0 = V(Chem::PHIS, n0, s), l1 = V(Chem::PHIS, n1, s), r0 = V(Chem::PHIS, n0, sq), r1 = V(Chem::PHIS, n1, sq);
-        fS = (((ALPHA * l1 + BETA * l0) - (ALPHA * r0 + BETA * r1)) * pen - 0.5 * gq * ((l1 - l0) + (r1 - r0))) * p.kappa_s;
+        fS = bracket(V(Chem::PHIS, n0, s), V(Chem::PHIS, n1, s), V(Chem::PHIS, n0, sq), V(Chem::PHIS, n1, sq)) * K.fS;
     }
     put(NL + 1, fS);
 }
 
 template <class Chem>
-__global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                         const double* __restrict__ v, const double* __restrict__ gb,
-                                                         const double* __restrict__ gbd, const double* __restrict__ flux,
-                                                         int d, int relax, double sc_dt, double* __restrict__ out) {
+__global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, const LinK K, const Geo g,
+                                                         const double* __restrict__ z, const double* __restrict__ v,
+                                                         const double* __restrict__ gb, const double* __restrict__ gbd,
+                                                         const double* __restrict__ flux, int d,
+                                                         double* __restrict__ out) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 4) return;
     constexpr int NL = Chem::NL;
@@ -1004,9 +1066,6 @@ __global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, cons
     cell_ijk(p, cell, i, j, k);
     int n0, n1;
     line_nodes(d, q, n0, n1);
-    const int sidx = g.cmap[cell];
-    const bool st = g.phase[cell] == 1;
-    const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h;
     const int coord = d == 0 ? i : d == 1 ? j : k;
     const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
     const bool hasL = coord > 0;
@@ -1014,59 +1073,42 @@ __global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, cons
     const double* Fm = flux + (int64_t)q * (NL + 2) * p.n_cell + (hasL ? cell - stride : cell);
     auto V = [&](int f, int n, int idx) { return v[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
     auto Z = [&](int f, int n, int idx) { return z[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
-    // own face as left voxel: +f (ALPHA to n1, BETA to n0); -d face as right voxel: -f (ALPHA to n0, BETA to n1)
-    auto faces = [&](int e, double& a0, double& a1) {
-        double fp = Fp[(int64_t)e * p.n_cell] * wf;
-        a1 += fp * ALPHA;
-        a0 += fp * BETA;
-        if (hasL) {
-            double fm = Fm[(int64_t)e * p.n_cell] * wf;
-            a0 -= fm * ALPHA;
-            a1 -= fm * BETA;
-        }
-    };
-    auto store = [&](int f, int idx, double a0, double a1) {
-        if (sc_dt > 0.0) { double sc = sc_dt * p.rscale[f]; a0 *= sc; a1 *= sc; }
-        out[p.off[f] + (int64_t)n0 * p.flen[f] + idx] += a0;
-        out[p.off[f] + (int64_t)n1 * p.flen[f] + idx] += a1;
+    // own face as left voxel adds +f (ALPHA to n1, BETA to n0); the -d face, where this voxel is the
+    // right one, adds -f (ALPHA to n0, BETA to n1); fl is the volume flux along the line
+    auto gather = [&](int e, int f, int idx, double fl) {
+        const double fp = Fp[(int64_t)e * p.n_cell];
+        const double fm = hasL ? Fm[(int64_t)e * p.n_cell] : 0.0;
+        const double o1 = fl + ALPHA * fp - BETA * fm;
+        const double o0 = -fl + BETA * fp - ALPHA * fm;
+        out[p.off[f] + (int64_t)n0 * p.flen[f] + idx] += o0;
+        out[p.off[f] + (int64_t)n1 * p.flen[f] + idx] += o1;
     };
     const double gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
     const double dgN0 = gbd[(int64_t)n0 * p.n_cell + cell], dgN1 = gbd[(int64_t)n1 * p.n_cell + cell];
-    const double P0 = Z(Chem::PHIL, n0, cell), P1 = Z(Chem::PHIL, n1, cell);
-    const double dPhi = P1 - P0, ddPhi = V(Chem::PHIL, n1, cell) - V(Chem::PHIL, n0, cell);
+    const double dPhi = Z(Chem::PHIL, n1, cell) - Z(Chem::PHIL, n0, cell);
+    const double ddPhi = V(Chem::PHIL, n1, cell) - V(Chem::PHIL, n0, cell);
     const double gsum = gN0 + gN1, dgsum = dgN0 + dgN1;
-    double aL0 = 0.0, aL1 = 0.0;
-#pragma unroll 1
+    double flL = 0.0;
+#pragma unroll
     for (int m = 0; m < NL; ++m) {
         const double C0 = Z(m, n0, cell), C1 = Z(m, n1, cell);
         const double dC0 = V(m, n0, cell), dC1 = V(m, n1, cell);
-        const double dc = C1 - C0, ddc = dC1 - dC0;
-        double a0 = 0.0, a1 = 0.0;
-        double fl = 0.0;
-        if (!relax) fl = (dgsum * dc + gsum * ddc) * p.D0[m];
+        const double A = dgsum * (C1 - C0) + gsum * (dC1 - dC0);     // tangent of g_sum dc
+        double fl = A * K.vD[m];
         if (p.zc[m] != 0.0) {
-            double msum = gN0 * C0 + gN1 * C1;
-            double dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
-            if (!relax) fl += (dmsum * dPhi + msum * ddPhi) * p.kappa_m[m];
-            double fLv = ((dgsum * dc + gsum * ddc) * p.Kd[m] + (dmsum * dPhi + msum * ddPhi) * p.Km[m]) * vol;
-            aL1 += fLv;
-            aL0 -= fLv;
+            flL += A * K.vKd[m];
+            const double msum = gN0 * C0 + gN1 * C1;
+            const double dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
+            const double B = dmsum * dPhi + msum * ddPhi;             // tangent of (g c)_sum dPhi
+            fl += B * K.vK[m];
+            flL += B * K.vKm[m];
         }
-        fl *= vol;
-        a1 += fl;
-        a0 -= fl;
-        faces(m, a0, a1);
-        store(m, cell, a0, a1);
+        gather(m, m, cell, fl);
     }
-    faces(NL, aL0, aL1);
-    store(Chem::PHIL, cell, aL0, aL1);
-    if (st) {
-        double a0 = 0.0, a1 = 0.0;
-        double fs = (V(Chem::PHIS, n1, sidx) - V(Chem::PHIS, n0, sidx)) * 2.0 * p.kappa_s * vol;
-        a1 += fs;
-        a0 -= fs;
-        faces(NL + 1, a0, a1);
-        store(Chem::PHIS, sidx, a0, a1);
+    gather(NL, Chem::PHIL, cell, flL);
+    if (g.phase[cell] == 1) {
+        const int sidx = g.cmap[cell];
+        gather(NL + 1, Chem::PHIS, sidx, (V(Chem::PHIS, n1, sidx) - V(Chem::PHIS, n0, sidx)) * K.vS);
     }
 }
 
@@ -1080,7 +1122,7 @@ template <class Chem>
 __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g, const double* __restrict__ z,
                                                  const double* __restrict__ gb, const double* __restrict__ gam,
                                                  const double* __restrict__ jn, const double* __restrict__ face, double dt,
-                                                 int relax, double* __restrict__ blk) {
+                                                 int relax, const NodeDiag nd, double* __restrict__ blk) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 8) return;
     typedef LinShape<Chem> SH;
@@ -1094,7 +1136,8 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
     const int an[3] = {n & 1, (n >> 1) & 1, (n >> 2) & 1};
     const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h, gq = SQ3 / p.h, pen = p.penalty / p.h;
     auto Z = [&](int f, int nn) { return z[p.off[f] + (int64_t)nn * p.flen[f] + cell]; };
-    const double* J = jn + (int64_t)n * NF * NF * p.n_cell + cell;
+    const double* J = st ? jn + (int64_t)n * NF * NF * p.n_struct + g.cmap[cell] : nullptr;
+    const double ddc = ph == 2 ? nd.c_sep : nd.c_pore, ddphi = nd.phi;
     double* B = blk + b * NF * NF;
 #pragma unroll 1
     for (int c = 0; c < NF; ++c) {
@@ -1103,8 +1146,13 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
             continue;
         }
         double col[NF];
+        if (st) {
 #pragma unroll
-        for (int r = 0; r < NF; ++r) col[r] = J[(int64_t)(r * NF + c) * p.n_cell];
+            for (int r = 0; r < NF; ++r) col[r] = J[(int64_t)(r * NF + c) * p.n_struct];
+        } else {
+#pragma unroll
+            for (int r = 0; r < NF; ++r) col[r] = r != c ? 0.0 : (r < NL ? ddc : (r == PHIL ? ddphi : 0.0));
+        }
         const int dm = c < NL ? c : -1;                      // perturbed species
         const bool dPL = c == PHIL, dPS = c == PHIS;
         const double dcs = c < NL ? p.wS[c] : 0.0;          // tangent of c_S at node n
@@ -1209,7 +1257,7 @@ int64_t dg1_lin_sizes(const DevParams& p, int64_t* jn, int64_t* gam, int64_t* fa
     const int nf = p.nf;
     const int nl = p.nl;
     const int nfd = 3 + nl + 1 + 5 * (nl - 1);
-    *jn = (int64_t)8 * nf * nf * p.n_cell;
+    *jn = (int64_t)8 * nf * nf * (p.n_struct > 0 ? p.n_struct : 1);
     *gam = (int64_t)NG * p.n_cell;
     *face = (int64_t)12 * nfd * p.n_cell;
     return (*jn + *gam + *face) * 8;
@@ -1223,7 +1271,8 @@ static cudaError_t linearize_impl(const LaunchCtx& L, const DevParams& p, const 
                                   double dt, int relax, const DG1Lin& lin) {
     k_dg1_g<Chem, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, lin.gb, lin.gb);
     k_lin_gam<Chem><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, lin.gam);
-    k_lin_nodes_build<Chem><<<nblocks((int64_t)p.n_cell * 8, 64), 64, 0, L.st>>>(p, g, z, t, dt, relax, lin.jn);
+    if (p.n_struct > 0)
+        k_lin_nodes_build<Chem><<<nblocks((int64_t)p.n_struct * 8, 64), 64, 0, L.st>>>(p, g, z, t, dt, relax, lin.jn);
     for (int d = 0; d < 3; ++d)
         k_lin_faces_build<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, lin.gb, d, lin.face);
     *L.counter += 6;
@@ -1238,30 +1287,33 @@ cudaError_t dg1_linearize(const LaunchCtx& L, const DevParams& p, const Geo& g, 
 
 template <class Chem>
 static cudaError_t lin_apply_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
-                                  double t, int relax, double sc_dt, double* out, const DG1Lin& lin) {
+                                  double t, double dt, int relax, double sc_dt, double* out, const DG1Lin& lin) {
     k_lin_g<Chem><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, v, lin.gb, lin.gam, lin.gbd);
-    k_lin_nodes_apply<Chem><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, g, v, lin.jn, sc_dt, out);
+    k_lin_nodes_apply<Chem><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, make_node_diag(p, dt, relax), g, v,
+                                                                                    lin.jn, sc_dt, out);
+    const LinK K = make_link(p, Chem::NL, Chem::PHIL, Chem::PHIS, relax, sc_dt);
     for (int d = 0; d < 3; ++d) {
-        k_lin_face_flux<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, v, lin.gb, lin.gbd, lin.face, d,
-                                                                                      relax, lin.flux);
-        k_lin_line_gather<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, v, lin.gb, lin.gbd,
-                                                                                        lin.flux, d, relax, sc_dt, out);
+        k_lin_face_flux<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, K, g, v, lin.gbd, lin.face, d,
+                                                                                      lin.flux);
+        k_lin_line_gather<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, K, g, z, v, lin.gb, lin.gbd,
+                                                                                        lin.flux, d, out);
     }
     *L.counter += 8;
     return cudaGetLastError();
 }
 
 cudaError_t dg1_lin_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
-                          double t, int relax, double sc_dt, double* out, const DG1Lin& lin) {
-    return p.nf == 10 ? lin_apply_impl<ChemTO>(L, p, g, z, v, t, relax, sc_dt, out, lin)
-                      : lin_apply_impl<ChemR3>(L, p, g, z, v, t, relax, sc_dt, out, lin);
+                          double t, double dt, int relax, double sc_dt, double* out, const DG1Lin& lin) {
+    return p.nf == 10 ? lin_apply_impl<ChemTO>(L, p, g, z, v, t, dt, relax, sc_dt, out, lin)
+                      : lin_apply_impl<ChemR3>(L, p, g, z, v, t, dt, relax, sc_dt, out, lin);
 }
 
 cudaError_t dg1_lin_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double dt, int relax,
                            const DG1Lin& lin, double* blk) {
     const int nb = nblocks((int64_t)p.n_cell * 8, 128);
-    if (p.nf == 10) k_lin_blk<ChemTO><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, blk);
-    else k_lin_blk<ChemR3><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, blk);
+    const NodeDiag nd = make_node_diag(p, dt, relax);
+    if (p.nf == 10) k_lin_blk<ChemTO><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);
+    else k_lin_blk<ChemR3><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);
     *L.counter += 1;
     return cudaGetLastError();
 }

@@ -63,7 +63,7 @@ cudaError_t dg1_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, co
 int64_t dg1_face_buffer_len(const DevParams& p);
 // Linearised FP64 DG1 JVP: cached derivative data at a fixed linearisation point.
 struct DG1Lin {
-    double* jn;     // [8][NF*NF][n_cell] node Jacobians
+    double* jn;     // [8][NF*NF][n_struct] node Jacobians of the structure voxels
     double* gam;    // [32][n_cell] 3/(2 eps_L) per transport-factor slot
     double* face;   // [12][NFD][n_cell] face data of the + faces
     double* gb;     // [32][n_cell] transport factors at the linearisation point
@@ -78,7 +78,7 @@ int64_t dg1_lin_sizes(const DevParams& p, int64_t* jn, int64_t* gam, int64_t* fa
 cudaError_t dg1_linearize(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t, double dt,
                           int relax, const DG1Lin& lin);
 cudaError_t dg1_lin_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
-                          double t, int relax, double sc_dt, double* out, const DG1Lin& lin);
+                          double t, double dt, int relax, double sc_dt, double* out, const DG1Lin& lin);
 
 // ------------------------------------------------------------------ linear algebra (la.cu)
 // Block-Jacobi: invert nblk blocks of nf x nf (row-major) in place; identity rows for absent

@@ -64,10 +64,10 @@ def test_dg1_point_block_parity():
     assert np.abs(to_host(out) - ref).max() <= 1e-9 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("reorth", [0, 1])
+@pytest.mark.parametrize("reorth", [0, 1, 2])
 def test_dg1_step_parity(reorth):
-    """One implicit Euler step with either Gram-Schmidt rule in GMRES (second pass when the first
-    cancelled, or always): both reach the oracle's exact-Newton state."""
+    """One implicit Euler step with each Gram-Schmidt rule in GMRES (second pass when the first
+    cancelled, always, never): all reach the oracle's exact-Newton state."""
     model, grid, phase, z0, z = make_case("reduced3", 1, (6, 4, 3))
     ctx = gpu_context(model, phase, reorth=reorth)
     ref, info = newton.implicit_euler_step(model, grid, z, 0.0, 1e-3)
@@ -79,6 +79,8 @@ def test_dg1_step_parity(reorth):
     passes = ctx.reorth_count()
     if reorth == 1:
         assert passes == ginfo.gmres_iterations
+    elif reorth == 2:
+        assert passes == 0
     else:
         assert 0 <= passes <= ginfo.gmres_iterations
 
