@@ -70,7 +70,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # at 64^3 (17,428,880 unknowns), / unknowns.  DRAM bytes of the same launches per unknown, or
 # None when the kernels have changed since the counters were taken.
 LIN_JVP_DG1_FLOP_PER_DOF = 89.44
-LIN_JVP_DG1_DRAM_BYTES_PER_DOF = 257.9
+LIN_JVP_DG1_DRAM_BYTES_PER_DOF = None
 
 
 class ClockSampler:

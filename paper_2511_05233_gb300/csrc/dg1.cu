@@ -894,30 +894,20 @@ __global__ void __launch_bounds__(128) k_lin_g(const DevParams p, const Geo g, c
             }
 }
 
-// node part of the JVP: out = J_node v_node (writes, the line passes add)
+// node part of the JVP: out = J_node v_node (writes; the line passes add).  Structure voxels and
+// the others run in separate kernels so that no warp mixes the 10 x 10 product with the diagonal
+// (on GB300 an FP64 instruction costs its issue slots whether or not all lanes take it).
+// (a) one thread per (node, structure voxel), over the compact structure list
 template <class Chem>
-__global__ void __launch_bounds__(128) k_lin_nodes_apply(const DevParams p, const NodeDiag nd, const Geo g,
-                                                         const double* __restrict__ v, const double* __restrict__ jn,
-                                                         double sc_dt, double* __restrict__ out) {
+__global__ void __launch_bounds__(128) k_lin_nodes_apply(const DevParams p, const Geo g, const double* __restrict__ v,
+                                                         const double* __restrict__ jn, double sc_dt,
+                                                         double* __restrict__ out) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= (int64_t)p.n_cell * 8) return;
-    constexpr int NF = Chem::NF, NL = Chem::NL, PHIL = Chem::PHIL;
-    const int n = (int)(b / p.n_cell);
-    const int cell = (int)(b - (int64_t)n * p.n_cell);
-    const int ph = g.phase[cell];
-    if (ph != 1) {
-        const double dc = ph == 2 ? nd.c_sep : nd.c_pore, dphi = nd.phi;
-#pragma unroll
-        for (int f = 0; f <= PHIL; ++f) {
-            if (f >= NL && f != PHIL) continue;     // solid fields do not live here
-            const int64_t idx = p.off[f] + (int64_t)n * p.flen[f] + cell;
-            double acc = (f == PHIL ? dphi : dc) * v[idx];
-            if (sc_dt > 0.0) acc *= sc_dt * p.rscale[f];
-            out[idx] = acc;
-        }
-        return;
-    }
-    const int sidx = g.cmap[cell];
+    if (b >= (int64_t)p.n_struct * 8) return;
+    constexpr int NF = Chem::NF;
+    const int n = (int)(b / p.n_struct);
+    const int sidx = (int)(b - (int64_t)n * p.n_struct);
+    const int cell = g.sidx[sidx];
     double x[NF];
     int64_t idx[NF];
 #pragma unroll
@@ -933,6 +923,29 @@ __global__ void __launch_bounds__(128) k_lin_nodes_apply(const DevParams p, cons
         for (int c = 0; c < NF; ++c) acc += J[(int64_t)(r * NF + c) * p.n_struct] * x[c];
         if (sc_dt > 0.0) acc *= sc_dt * p.rscale[r];
         out[idx[r]] = acc;
+    }
+}
+
+// (b) one thread per (node, voxel): the storage diagonal of pore and separator voxels
+template <class Chem>
+__global__ void __launch_bounds__(128) k_lin_nodes_diag(const DevParams p, const NodeDiag nd, const Geo g,
+                                                        const double* __restrict__ v, double sc_dt,
+                                                        double* __restrict__ out) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 8) return;
+    constexpr int NL = Chem::NL, PHIL = Chem::PHIL;
+    const int n = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)n * p.n_cell);
+    const int ph = g.phase[cell];
+    if (ph == 1) return;
+    const double dc = ph == 2 ? nd.c_sep : nd.c_pore, dphi = nd.phi;
+#pragma unroll
+    for (int f = 0; f <= PHIL; ++f) {
+        if (f >= NL && f != PHIL) continue;     // solid fields do not live here
+        const int64_t idx = p.off[f] + (int64_t)n * p.flen[f] + cell;
+        double acc = (f == PHIL ? dphi : dc) * v[idx];
+        if (sc_dt > 0.0) acc *= sc_dt * p.rscale[f];
+        out[idx] = acc;
     }
 }
 
@@ -1289,8 +1302,10 @@ template <class Chem>
 static cudaError_t lin_apply_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
                                   double t, double dt, int relax, double sc_dt, double* out, const DG1Lin& lin) {
     k_lin_g<Chem><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, v, lin.gb, lin.gam, lin.gbd);
-    k_lin_nodes_apply<Chem><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, make_node_diag(p, dt, relax), g, v,
-                                                                                    lin.jn, sc_dt, out);
+    if (p.n_struct > 0)
+        k_lin_nodes_apply<Chem><<<nblocks((int64_t)p.n_struct * 8, 128), 128, 0, L.st>>>(p, g, v, lin.jn, sc_dt, out);
+    k_lin_nodes_diag<Chem><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, make_node_diag(p, dt, relax), g, v,
+                                                                                   sc_dt, out);
     const LinK K = make_link(p, Chem::NL, Chem::PHIL, Chem::PHIS, relax, sc_dt);
     for (int d = 0; d < 3; ++d) {
         k_lin_face_flux<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, K, g, v, lin.gbd, lin.face, d,
@@ -1298,7 +1313,7 @@ static cudaError_t lin_apply_impl(const LaunchCtx& L, const DevParams& p, const 
         k_lin_line_gather<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, K, g, z, v, lin.gb, lin.gbd,
                                                                                         lin.flux, d, out);
     }
-    *L.counter += 8;
+    *L.counter += 9;
     return cudaGetLastError();
 }
 
