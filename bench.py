@@ -325,6 +325,7 @@ def main():
         torch.cuda.synchronize()
         m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev32 = 0
+        ctx32.profile(True)
         m0.record(stream)
         for _ in range(a.steps):
             st32, inf32 = ctx32.step(zn, z32, t, dt, check=False)
@@ -332,6 +333,8 @@ def main():
         m1.record(stream)
         torch.cuda.synchronize()
         ms32 = m0.elapsed_time(m1)
+        prof32 = ctx32.profile_read()
+        ctx32.profile(False)
         errs = {}
         lay = list(zip(ctx.offsets, ctx.lengths))
         kinds = {"conc": range(0, nl), "eps": range(nl, ctx.n_fields - 2), "pot": range(ctx.n_fields - 2, ctx.n_fields)}
@@ -344,7 +347,8 @@ def main():
         mixed = {"value": ev32 * N / (ms32 / 1e3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms32 / a.steps,
                  "converged": bool(inf32.converged), "newton_iterations": inf32.newton_iterations,
                  "gmres_iterations": inf32.gmres_iterations,
-                 "max_rel_diff_vs_fp64": errs, "speedup_vs_fp64_step": (elapsed_ms / a.steps) / (ms32 / a.steps)}
+                 "max_rel_diff_vs_fp64": errs, "speedup_vs_fp64_step": (elapsed_ms / a.steps) / (ms32 / a.steps),
+                 "kernel_breakdown_ms": {k: {"ms": v[0], "calls": v[1]} for k, v in prof32.items()}}
         ctx32.close()
         del z32
 

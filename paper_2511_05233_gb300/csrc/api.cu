@@ -351,6 +351,11 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     int64_t need = ncell * (1 + 4 + 4) + N * 8 * (6 + 4) + scratch * 8 * 2 +
                    ctx->nblk * P.nf * P.nf * 8 + (int64_t)(m + 1) * N * (mixed ? 4 : 8) + 3 * N * (mixed ? 4 : 8) +
                    N * 8 + (mixed ? (N * 4 + scratch * 4 * 2 + ctx->nblk * P.nf * P.nf * 4) : 0);
+    if (prm->order == 1) {   // the linearisation (FP64, or FP32 for the mixed-precision product)
+        int64_t njn, ngam, nface;
+        dg1_lin_sizes(P, &njn, &ngam, &nface);
+        need += (njn + 2 * ngam + nface + dg1_lin_flux_len(P)) * (mixed ? 4 : 8);
+    }
     if (prm->hbm_budget_bytes > 0 && need > prm->hbm_budget_bytes) {
         dg_status st = fail(ctx, DG_ERR_OOM, "workspace of " + std::to_string(need) + " bytes exceeds hbm_budget_bytes");
         delete ctx;
@@ -389,13 +394,25 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         AL(V, (int64_t)(m + 1) * N); AL(w, N); AL(u, N); AL(x, N); AL(y1, N); AL(t2, N);
         ctx->V = V; ctx->w = w; ctx->u = u; ctx->x = x; ctx->y1 = y1; ctx->t2 = t2;
     }
-    if (prm->order == 1 && !mixed) {
+    if (prm->order == 1) {
         int64_t njn, ngam, nface;
         dg1_lin_sizes(P, &njn, &ngam, &nface);
-        double *jn, *gam, *face, *lgb, *lflux;
-        AL(jn, njn); AL(gam, ngam); AL(face, nface); AL(lgb, ngam); AL(lflux, dg1_lin_flux_len(P));
-        ctx->lin.jn = jn; ctx->lin.gam = gam; ctx->lin.face = face; ctx->lin.gb = lgb; ctx->lin.gbd = ctx->gbd;
-        ctx->lin.flux = lflux;
+        if (!mixed) {
+            double *jn, *gam, *face, *lgb, *lflux;
+            AL(jn, njn); AL(gam, ngam); AL(face, nface); AL(lgb, ngam); AL(lflux, dg1_lin_flux_len(P));
+            ctx->lin.jn = jn; ctx->lin.gam = gam; ctx->lin.face = face; ctx->lin.gb = lgb; ctx->lin.gbd = ctx->gbd;
+            ctx->lin.flux = lflux;
+        } else {
+            // FP32 copy of the linearisation for the FP32 product; the FP64 transport factors it is
+            // built from live in the residual's scratch, read only by the preconditioner build that
+            // follows each linearisation, before any further residual evaluation
+            float *jn, *gam, *face, *lgb, *lflux;
+            AL(jn, njn); AL(gam, ngam); AL(face, nface); AL(lgb, ngam); AL(lflux, dg1_lin_flux_len(P));
+            ctx->lin.f32 = true;
+            ctx->lin.jn32 = jn; ctx->lin.gam32 = gam; ctx->lin.face32 = face; ctx->lin.gb32 = lgb;
+            ctx->lin.gbd32 = ctx->gbd32; ctx->lin.flux32 = lflux;
+            ctx->lin.gb = ctx->gb;
+        }
         ctx->has_lin = true;
     }
     if (prm->preconditioner != 0 && mg_levels_alloc(ctx->mg, nx, ny, nz, ctx->allocs, &ctx->ws_bytes) != cudaSuccess) {
@@ -463,15 +480,13 @@ static dg_status residual_(dg_ctx* ctx, const double* z, const double* zn, doubl
     return DG_OK;
 }
 
-// J v through the kernels for this context: the cached linearisation when it is valid (FP64 DG1),
-// otherwise forward-mode dual numbers.
+// J v through the kernels for this context: the cached linearisation when it is valid and stored in
+// the product's precision (DG1), otherwise forward-mode dual numbers.
 template <class S>
 static cudaError_t jvp_kernels(dg_ctx* ctx, const S* z, const S* v, double t, double dt, int relax, double sc_dt, S* out,
                                S* gb, S* gbd) {
-    if constexpr (std::is_same<S, double>::value) {
-        if (ctx->has_lin && ctx->lin_valid)
-            return dg1_lin_apply(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, ctx->lin);
-    }
+    if (ctx->has_lin && ctx->lin_valid && std::is_same<S, float>::value == ctx->lin.f32)
+        return dg1_lin_apply<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, ctx->lin);
     return ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd)
                              : dg1_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd);
 }
@@ -491,17 +506,19 @@ static dg_status jvp_(dg_ctx* ctx, const S* z, const S* v, double t, double dt, 
 static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt, int relax) {
     ProfScope ps(ctx, 2);
     cudaError_t e;
+    if (ctx->has_lin && !ctx->lin_valid) return fail(ctx, DG_ERR_ARG, "blocks: no linearisation at this state");
     if (ctx->prm.precision == DG_PREC_MIXED) {
         e = to_f32(ctx->L, ctx->z32, z, ctx->ndof);
-        if (e == cudaSuccess)
-            e = ctx->P.order == 0 ? dg0_blocks<float>(ctx->L, ctx->P, ctx->G, ctx->z32, t, dt, relax, ctx->blk, ctx->gb32)
-                                  : dg1_blocks<float>(ctx->L, ctx->P, ctx->G, ctx->z32, t, dt, relax, ctx->blk, ctx->gb32);
-        if (e == cudaSuccess && ctx->prm.preconditioner != 0)
-            e = ctx->P.order == 0 ? dg0_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb)
-                                  : dg1_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb);
+        if (e == cudaSuccess) {
+            if (ctx->has_lin)   // DG1: FP64 blocks from the FP32 linearisation, inverted to FP32 below
+                e = dg1_lin_blocks(ctx->L, ctx->P, ctx->G, z, dt, relax, ctx->lin, ctx->blk);
+            else
+                e = dg0_blocks<float>(ctx->L, ctx->P, ctx->G, ctx->z32, t, dt, relax, ctx->blk, ctx->gb32);
+        }
+        if (e == cudaSuccess && ctx->prm.preconditioner != 0 && !ctx->has_lin)
+            e = dg0_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb);
     } else if (ctx->has_lin) {
         // FP64 DG1: the blocks come from the linearisation at z, which the caller has just built
-        if (!ctx->lin_valid) return fail(ctx, DG_ERR_ARG, "blocks: no linearisation at this state");
         e = dg1_lin_blocks(ctx->L, ctx->P, ctx->G, z, dt, relax, ctx->lin, ctx->blk);
     } else {
         e = ctx->P.order == 0 ? dg0_blocks<double>(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb)
@@ -512,7 +529,7 @@ static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt
     if (e == cudaSuccess) e = block_invert(ctx->L, ctx->blk, ctx->nblk, ctx->P.nf, ctx->blk32, ctx->d_bad);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
     if (ctx->prm.preconditioner != 0) {
-        const double* gbz = (ctx->has_lin && ctx->prm.precision != DG_PREC_MIXED) ? ctx->lin.gb : ctx->gb;
+        const double* gbz = ctx->has_lin ? ctx->lin.gb : ctx->gb;
         e = mg_setup(ctx->L, ctx->P, ctx->G, z, gbz, t, dt, relax, ctx->mg);
         if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("multigrid setup: ") + cudaGetErrorString(e));
     }
@@ -587,7 +604,7 @@ extern "C" dg_status dg_residual(dg_ctx* ctx, const double* z, const double* zol
 
 extern "C" dg_status dg_jvp(dg_ctx* ctx, const double* z, double t, double dt, const double* v, double* jv) {
     if (!ctx || !z || !v || !jv || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_jvp: bad argument");
-    if (ctx->has_lin) {
+    if (ctx->has_lin && !ctx->lin.f32) {   // FP64 product from the FP64 linearisation (else dual numbers)
         CK(dg1_linearize(ctx->L, ctx->P, ctx->G, z, t, dt, 0, ctx->lin));
         ctx->lin_valid = true;
     }

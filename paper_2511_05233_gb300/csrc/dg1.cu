@@ -695,9 +695,9 @@ struct LinShape {
     static __device__ __forceinline__ int ci(int m) { return m < 1 ? m : m - 1; }
 };
 
-template <class Chem>
+template <class Chem, class LT>
 __global__ void __launch_bounds__(128) k_lin_gam(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                 double* __restrict__ gam) {
+                                                 LT* __restrict__ gam) {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= p.n_cell) return;
     constexpr int NS = Chem::NS;
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(128) k_lin_gam(const DevParams p, const Geo g,
             es[n][1] = ld(z, p, Chem::NL + 1, n, s);
         }
         double eL = liquid_fraction<Chem, double>(p, ph, es[n]);
-        gam[(int64_t)n * p.n_cell + cell] = (ph == 1 && NS == 2 && eL > 0.0) ? 1.5 / eL : 0.0;
+        gam[(int64_t)n * p.n_cell + cell] = LT((ph == 1 && NS == 2 && eL > 0.0) ? 1.5 / eL : 0.0);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d)
@@ -725,16 +725,16 @@ __global__ void __launch_bounds__(128) k_lin_gam(const DevParams p, const Geo g,
                 const double wn = side > 0 ? ALPHA : BETA, wf = side > 0 ? BETA : ALPHA;
                 double et[2] = {es[n1][0] * wn + es[n0][0] * wf, es[n1][1] * wn + es[n0][1] * wf};
                 double eL = liquid_fraction<Chem, double>(p, ph, et);
-                gam[(int64_t)face_slot(d, side, q) * p.n_cell + cell] = (ph == 1 && NS == 2 && eL > 0.0) ? 1.5 / eL : 0.0;
+                gam[(int64_t)face_slot(d, side, q) * p.n_cell + cell] = LT((ph == 1 && NS == 2 && eL > 0.0) ? 1.5 / eL : 0.0);
             }
 }
 
 // node Jacobians of the structure voxels: one thread per (node, structure voxel), NF seeded
 // evaluations of the node terms.  Elsewhere (pore, separator) the node terms are the storage terms
 // alone and their Jacobian is the diagonal that make_node_diag gives, so nothing is stored there.
-template <class Chem>
+template <class Chem, class LT>
 __global__ void __launch_bounds__(64) k_lin_nodes_build(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                        double t, double dt, int relax, double* __restrict__ jn) {
+                                                        double t, double dt, int relax, LT* __restrict__ jn) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_struct * 8) return;
     typedef Dual<double> T;
@@ -746,7 +746,7 @@ __global__ void __launch_bounds__(64) k_lin_nodes_build(const DevParams p, const
 #pragma unroll
     for (int f = 0; f < NF; ++f) old[f] = 0.0;
     const double tH = smooth_step(t);
-    double* J = jn + (int64_t)n * NF * NF * p.n_struct + sidx;    // [row*NF + col][structure voxel]
+    LT* J = jn + (int64_t)n * NF * NF * p.n_struct + sidx;    // [row*NF + col][structure voxel]
 #pragma unroll 1
     for (int col = 0; col < NF; ++col) {
         T c[NL], es[2], phiL, phiS;
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(64) k_lin_nodes_build(const DevParams p, const
         T R[NF];
         node_terms<Chem, T>(p, 1, c, es, phiL, phiS, old, tH, dt, relax, R);
 #pragma unroll
-        for (int row = 0; row < NF; ++row) J[(int64_t)(row * NF + col) * p.n_struct] = R[row].d;
+        for (int row = 0; row < NF; ++row) J[(int64_t)(row * NF + col) * p.n_struct] = LT(R[row].d);
     }
 }
 
@@ -781,9 +781,9 @@ static NodeDiag make_node_diag(const DevParams& p, double dt, int relax) {
 }
 
 // face data of the +d face of every voxel (and the anode derivatives on the x = nx face)
-template <class Chem>
+template <class Chem, class LT>
 __global__ void __launch_bounds__(128) k_lin_faces_build(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                         const double* __restrict__ gb, int d, double* __restrict__ face) {
+                                                         const double* __restrict__ gb, int d, LT* __restrict__ face) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 4) return;
     typedef LinShape<Chem> SH;
@@ -794,8 +794,8 @@ __global__ void __launch_bounds__(128) k_lin_faces_build(const DevParams p, cons
     cell_ijk(p, cell, i, j, k);
     int n0, n1;
     line_nodes(d, q, n0, n1);
-    double* F = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
-    auto put = [&](int kk, double v) { F[(int64_t)kk * p.n_cell] = v; };
+    LT* F = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
+    auto put = [&](int kk, double v) { F[(int64_t)kk * p.n_cell] = LT(v); };
     const int coord = d == 0 ? i : d == 1 ? j : k;
     const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
     const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
@@ -856,27 +856,82 @@ __global__ void __launch_bounds__(128) k_lin_faces_build(const DevParams p, cons
     }
 }
 
+// Per-call constants of the linearised apply, in the arithmetic type S of the product, with the
+// area / volume weights and the row scales (sc_dt * rscale, or 1 for the unscaled product) folded
+// in, so that the kernels below spend their issue slots on the tangents only (and, for S = float,
+// never leave the FP32 pipe).  While relaxing, the species rows carry no transport and no anode term.
+template <class S>
+struct LinKT {
+    S fD[6], fK[6], fKd[6], fKm[6];   // face: D0 and kappa_m (species row), K^d and K^m (Phi^L row)
+    S vD[6], vK[6], vKd[6], vKm[6];   // volume: the same with the volume weight
+    S fS, vS;                         // Phi^S: kappa_s at faces, 2 kappa_s in the volume
+    S aLi, aL;                        // anode: k_Ano (Li+ row), F k_Ano (Phi^L row)
+    S cl0, cl1, cr0, cr1;             // pen [[psi]] - {d_n psi} as weights of the four line values
+    S rs[10];                         // row scales of the node part
+    S c_pore, c_sep, phi;             // node diagonal of pore and separator voxels
+    S wS[6], visc;                    // c_S weights and the viscosity coefficient (transport-factor tangents)
+    int charged, sulfur;              // bit m: species m is charged / counts in c_S
+};
+
+template <class S>
+static LinKT<S> make_link(const DevParams& p, int nl, int nf, int philf, int phisf, int relax, double dt,
+                          double sc_dt) {
+    LinKT<S> k;
+    const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h, h2 = 0.5 * SQ3 / p.h, pen = p.penalty / p.h;
+    auto sc = [&](int f) { return sc_dt > 0.0 ? sc_dt * p.rscale[f] : 1.0; };
+    const double sL = sc(philf), sS = sc(phisf);
+    k.charged = 0;
+    k.sulfur = 0;
+    for (int m = 0; m < 6; ++m) {
+        const bool on = m < nl;
+        const double sm = on ? sc(m) : 0.0;
+        const double D0 = on && !relax ? p.D0[m] : 0.0, km = on && !relax ? p.kappa_m[m] : 0.0;
+        const double Kd = on ? p.Kd[m] : 0.0, Km = on ? p.Km[m] : 0.0;
+        k.fD[m] = S(D0 * wf * sm); k.fK[m] = S(km * wf * sm); k.fKd[m] = S(Kd * wf * sL); k.fKm[m] = S(Km * wf * sL);
+        k.vD[m] = S(D0 * vol * sm); k.vK[m] = S(km * vol * sm); k.vKd[m] = S(Kd * vol * sL); k.vKm[m] = S(Km * vol * sL);
+        k.wS[m] = S(on ? p.wS[m] : 0.0);
+        if (on && p.zc[m] != 0.0) k.charged |= 1 << m;
+        if (on && p.wS[m] != 0.0) k.sulfur |= 1 << m;
+    }
+    k.fS = S(p.kappa_s * wf * sS);
+    k.vS = S(2.0 * p.kappa_s * vol * sS);
+    k.aLi = S(relax ? 0.0 : p.kAno * wf * sc(0));
+    k.aL = S(p.F * p.kAno * wf * sL);
+    // (ALPHA l1 + BETA l0 - ALPHA r0 - BETA r1) pen - h2 ((l1 - l0) + (r1 - r0))
+    k.cl1 = S(ALPHA * pen - h2);
+    k.cl0 = S(BETA * pen + h2);
+    k.cr0 = S(-ALPHA * pen + h2);
+    k.cr1 = S(-BETA * pen - h2);
+    for (int f = 0; f < 10; ++f) k.rs[f] = S(f < nf ? sc(f) : 1.0);
+    const NodeDiag nd = make_node_diag(p, dt, relax);
+    k.c_pore = S(nd.c_pore);
+    k.c_sep = S(nd.c_sep);
+    k.phi = S(nd.phi);
+    k.visc = S(p.visc);
+    return k;
+}
+
 // tangents of the 32 transport factors of each voxel: dg = g (gam d eps_L - visc d c_S)
-template <class Chem>
-__global__ void __launch_bounds__(128) k_lin_g(const DevParams p, const Geo g, const double* __restrict__ v,
-                                               const double* __restrict__ gb, const double* __restrict__ gam,
-                                               double* __restrict__ gbd) {
+template <class Chem, class S>
+__global__ void __launch_bounds__(128) k_lin_g(const DevParams p, const LinKT<S> K, const Geo g,
+                                               const S* __restrict__ v, const S* __restrict__ gb,
+                                               const S* __restrict__ gam, S* __restrict__ gbd) {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= p.n_cell) return;
     constexpr int NL = Chem::NL, NS = Chem::NS;
     const int ph = g.phase[cell];
     const int s = g.cmap[cell];
-    double dcs[8], del[8];
+    S dcs[8], del[8];
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-        double a = 0.0;
+        S a = S(0);
 #pragma unroll
         for (int m = 0; m < NL; ++m)
-            if (p.wS[m] != 0.0) a += p.wS[m] * ld(v, p, m, n, cell);
+            if ((K.sulfur >> m) & 1) a += K.wS[m] * ld(v, p, m, n, cell);
         dcs[n] = a;
-        del[n] = (NS == 2 && ph == 1) ? -(ld(v, p, NL, n, s) + ld(v, p, NL + 1, n, s)) : 0.0;
+        del[n] = (NS == 2 && ph == 1) ? -(ld(v, p, NL, n, s) + ld(v, p, NL + 1, n, s)) : S(0);
         int64_t o = (int64_t)n * p.n_cell + cell;
-        gbd[o] = gb[o] * (gam[o] * del[n] - p.visc * dcs[n]);
+        gbd[o] = gb[o] * (gam[o] * del[n] - K.visc * dcs[n]);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d)
@@ -886,11 +941,11 @@ __global__ void __launch_bounds__(128) k_lin_g(const DevParams p, const Geo g, c
             for (int q = 0; q < 4; ++q) {
                 int n0, n1;
                 line_nodes(d, q, n0, n1);
-                const double wn = side > 0 ? ALPHA : BETA, wf = side > 0 ? BETA : ALPHA;
+                const S wn = side > 0 ? S(ALPHA) : S(BETA), wf = side > 0 ? S(BETA) : S(ALPHA);
                 int64_t o = (int64_t)face_slot(d, side, q) * p.n_cell + cell;
-                double dc = dcs[n1] * wn + dcs[n0] * wf;
-                double de = del[n1] * wn + del[n0] * wf;
-                gbd[o] = gb[o] * (gam[o] * de - p.visc * dc);
+                S dc = dcs[n1] * wn + dcs[n0] * wf;
+                S de = del[n1] * wn + del[n0] * wf;
+                gbd[o] = gb[o] * (gam[o] * de - K.visc * dc);
             }
 }
 
@@ -898,39 +953,37 @@ __global__ void __launch_bounds__(128) k_lin_g(const DevParams p, const Geo g, c
 // the others run in separate kernels so that no warp mixes the 10 x 10 product with the diagonal
 // (on GB300 an FP64 instruction costs its issue slots whether or not all lanes take it).
 // (a) one thread per (node, structure voxel), over the compact structure list
-template <class Chem>
-__global__ void __launch_bounds__(128) k_lin_nodes_apply(const DevParams p, const Geo g, const double* __restrict__ v,
-                                                         const double* __restrict__ jn, double sc_dt,
-                                                         double* __restrict__ out) {
+template <class Chem, class S>
+__global__ void __launch_bounds__(128) k_lin_nodes_apply(const DevParams p, const LinKT<S> K, const Geo g,
+                                                         const S* __restrict__ v, const S* __restrict__ jn,
+                                                         S* __restrict__ out) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_struct * 8) return;
     constexpr int NF = Chem::NF;
     const int n = (int)(b / p.n_struct);
     const int sidx = (int)(b - (int64_t)n * p.n_struct);
     const int cell = g.sidx[sidx];
-    double x[NF];
+    S x[NF];
     int64_t idx[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         idx[f] = p.off[f] + (int64_t)n * p.flen[f] + (p.is_struct[f] ? sidx : cell);
         x[f] = v[idx[f]];
     }
-    const double* J = jn + (int64_t)n * NF * NF * p.n_struct + sidx;
+    const S* J = jn + (int64_t)n * NF * NF * p.n_struct + sidx;
 #pragma unroll
     for (int r = 0; r < NF; ++r) {
-        double acc = 0.0;
+        S acc = S(0);
 #pragma unroll
         for (int c = 0; c < NF; ++c) acc += J[(int64_t)(r * NF + c) * p.n_struct] * x[c];
-        if (sc_dt > 0.0) acc *= sc_dt * p.rscale[r];
-        out[idx[r]] = acc;
+        out[idx[r]] = acc * K.rs[r];
     }
 }
 
 // (b) one thread per (node, voxel): the storage diagonal of pore and separator voxels
-template <class Chem>
-__global__ void __launch_bounds__(128) k_lin_nodes_diag(const DevParams p, const NodeDiag nd, const Geo g,
-                                                        const double* __restrict__ v, double sc_dt,
-                                                        double* __restrict__ out) {
+template <class Chem, class S>
+__global__ void __launch_bounds__(128) k_lin_nodes_diag(const DevParams p, const LinKT<S> K, const Geo g,
+                                                        const S* __restrict__ v, S* __restrict__ out) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 8) return;
     constexpr int NL = Chem::NL, PHIL = Chem::PHIL;
@@ -938,52 +991,13 @@ __global__ void __launch_bounds__(128) k_lin_nodes_diag(const DevParams p, const
     const int cell = (int)(b - (int64_t)n * p.n_cell);
     const int ph = g.phase[cell];
     if (ph == 1) return;
-    const double dc = ph == 2 ? nd.c_sep : nd.c_pore, dphi = nd.phi;
+    const S dc = ph == 2 ? K.c_sep : K.c_pore;
 #pragma unroll
     for (int f = 0; f <= PHIL; ++f) {
         if (f >= NL && f != PHIL) continue;     // solid fields do not live here
         const int64_t idx = p.off[f] + (int64_t)n * p.flen[f] + cell;
-        double acc = (f == PHIL ? dphi : dc) * v[idx];
-        if (sc_dt > 0.0) acc *= sc_dt * p.rscale[f];
-        out[idx] = acc;
+        out[idx] = (f == PHIL ? K.phi : dc) * v[idx] * K.rs[f];
     }
-}
-
-// Per-call constants of the linearised line part, with the area / volume weights and the row
-// scales (sc_dt * rscale, or 1 for the unscaled product) folded in, so that the two kernels below
-// spend their FP64 issue slots on the tangents only.  While relaxing, the species rows carry no
-// transport and no anode term.
-struct LinK {
-    double fD[6], fK[6], fKd[6], fKm[6];   // face: D0 and kappa_m (species row), K^d and K^m (Phi^L row)
-    double vD[6], vK[6], vKd[6], vKm[6];   // volume: the same with the volume weight
-    double fS, vS;                         // Phi^S: kappa_s at faces, 2 kappa_s in the volume
-    double aLi, aL;                        // anode: k_Ano (Li+ row), F k_Ano (Phi^L row)
-    double cl0, cl1, cr0, cr1;             // pen [[psi]] - {d_n psi} as weights of the four line values
-};
-
-static LinK make_link(const DevParams& p, int nl, int philf, int phisf, int relax, double sc_dt) {
-    LinK k;
-    const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h, h2 = 0.5 * SQ3 / p.h, pen = p.penalty / p.h;
-    auto sc = [&](int f) { return sc_dt > 0.0 ? sc_dt * p.rscale[f] : 1.0; };
-    const double sL = sc(philf), sS = sc(phisf);
-    for (int m = 0; m < 6; ++m) {
-        const bool on = m < nl;
-        const double sm = on ? sc(m) : 0.0;
-        const double D0 = on && !relax ? p.D0[m] : 0.0, km = on && !relax ? p.kappa_m[m] : 0.0;
-        const double Kd = on ? p.Kd[m] : 0.0, Km = on ? p.Km[m] : 0.0;
-        k.fD[m] = D0 * wf * sm; k.fK[m] = km * wf * sm; k.fKd[m] = Kd * wf * sL; k.fKm[m] = Km * wf * sL;
-        k.vD[m] = D0 * vol * sm; k.vK[m] = km * vol * sm; k.vKd[m] = Kd * vol * sL; k.vKm[m] = Km * vol * sL;
-    }
-    k.fS = p.kappa_s * wf * sS;
-    k.vS = 2.0 * p.kappa_s * vol * sS;
-    k.aLi = relax ? 0.0 : p.kAno * wf * sc(0);
-    k.aL = p.F * p.kAno * wf * sL;
-    // (ALPHA l1 + BETA l0 - ALPHA r0 - BETA r1) pen - h2 ((l1 - l0) + (r1 - r0))
-    k.cl1 = ALPHA * pen - h2;
-    k.cl0 = BETA * pen + h2;
-    k.cr0 = -ALPHA * pen + h2;
-    k.cr1 = -BETA * pen - h2;
-    return k;
 }
 
 // Face-once form of the line part: (1) one thread per +d face (voxel, line) computes the tangent of
@@ -991,15 +1005,15 @@ static LinK make_link(const DevParams& p, int nl, int philf, int phisf, int rela
 // row-scaled; (2) one thread per (voxel, line) adds the volume terms and gathers its two faces.
 // An interior face is evaluated once instead of once from each side.
 // flux: [4 lines][NL + 2][n_cell] for the current direction.
-template <class Chem>
-__global__ void __launch_bounds__(128) k_lin_face_flux(const DevParams p, const LinK K, const Geo g,
-                                                       const double* __restrict__ v, const double* __restrict__ gbd,
-                                                       const double* __restrict__ face, int d,
-                                                       double* __restrict__ flux) {
+template <class Chem, class S>
+__global__ void __launch_bounds__(128) k_lin_face_flux(const DevParams p, const LinKT<S> K, const Geo g,
+                                                       const S* __restrict__ v, const S* __restrict__ gbd,
+                                                       const S* __restrict__ face, int d, S* __restrict__ flux) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 4) return;
     typedef LinShape<Chem> SH;
     constexpr int NL = Chem::NL;
+    const S A_ = S(ALPHA), B_ = S(BETA);
     const int q = (int)(b / p.n_cell);
     const int cell = (int)(b - (int64_t)q * p.n_cell);
     int i, j, k;
@@ -1009,54 +1023,51 @@ __global__ void __launch_bounds__(128) k_lin_face_flux(const DevParams p, const 
     const int coord = d == 0 ? i : d == 1 ? j : k;
     const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
     const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
-    double* out = flux + (int64_t)q * (NL + 2) * p.n_cell + cell;
-    auto put = [&](int e, double val) { out[(int64_t)e * p.n_cell] = val; };
-    const double* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
+    S* out = flux + (int64_t)q * (NL + 2) * p.n_cell + cell;
+    auto put = [&](int e, S val) { out[(int64_t)e * p.n_cell] = val; };
+    const S* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
     auto F = [&](int kk) { return Fd[(int64_t)kk * p.n_cell]; };
     auto V = [&](int f, int n, int idx) { return v[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
     if (coord + 1 >= ext) {
         // domain face: only the anode face (x = nx) carries a flux with a tangent
-        double fLi = 0.0, fL = 0.0;
+        S fLi = S(0), fL = S(0);
         if (d == 0) {
-            double dcLi = ALPHA * V(0, n1, cell) + BETA * V(0, n0, cell);
-            double dphL = ALPHA * V(Chem::PHIL, n1, cell) + BETA * V(Chem::PHIL, n0, cell);
-            double drA = F(0) * dcLi + F(1) * dphL;
+            S dcLi = A_ * V(0, n1, cell) + B_ * V(0, n0, cell);
+            S dphL = A_ * V(Chem::PHIL, n1, cell) + B_ * V(Chem::PHIL, n0, cell);
+            S drA = F(0) * dcLi + F(1) * dphL;
             fLi = drA * K.aLi;
             fL = drA * K.aL;
         }
         put(0, fLi);
-        for (int e = 1; e < NL + 2; ++e) put(e, e == NL ? fL : 0.0);
+        for (int e = 1; e < NL + 2; ++e) put(e, e == NL ? fL : S(0));
         return;
     }
     const int qc = cell + stride;
     const int64_t ol = (int64_t)face_slot(d, +1, q) * p.n_cell + cell, orr = (int64_t)face_slot(d, -1, q) * p.n_cell + qc;
-    const double dgl = gbd[ol], dgr = gbd[orr];
-    const double Hg = F(0), dHg = F(1) * dgl + F(2) * dgr;
-    auto bracket = [&](double l0, double l1, double r0, double r1) {
-        return K.cl1 * l1 + K.cl0 * l0 + K.cr0 * r0 + K.cr1 * r1;
-    };
-    const double BL = F(3 + NL);
-    const double dBL = bracket(V(Chem::PHIL, n0, cell), V(Chem::PHIL, n1, cell), V(Chem::PHIL, n0, qc),
-                               V(Chem::PHIL, n1, qc));
-    double fL = 0.0;
+    const S dgl = gbd[ol], dgr = gbd[orr];
+    const S Hg = F(0), dHg = F(1) * dgl + F(2) * dgr;
+    auto bracket = [&](S l0, S l1, S r0, S r1) { return K.cl1 * l1 + K.cl0 * l0 + K.cr0 * r0 + K.cr1 * r1; };
+    const S BL = F(3 + NL);
+    const S dBL = bracket(V(Chem::PHIL, n0, cell), V(Chem::PHIL, n1, cell), V(Chem::PHIL, n0, qc), V(Chem::PHIL, n1, qc));
+    S fL = S(0);
 #pragma unroll
     for (int m = 0; m < NL; ++m) {
-        const double l0 = V(m, n0, cell), l1 = V(m, n1, cell), r0 = V(m, n0, qc), r1 = V(m, n1, qc);
-        const double dterm = dHg * F(3 + m) + Hg * bracket(l0, l1, r0, r1);
-        double f = dterm * K.fD[m];
-        if (p.zc[m] != 0.0) {
+        const S l0 = V(m, n0, cell), l1 = V(m, n1, cell), r0 = V(m, n0, qc), r1 = V(m, n1, qc);
+        const S dterm = dHg * F(3 + m) + Hg * bracket(l0, l1, r0, r1);
+        S f = dterm * K.fD[m];
+        if ((K.charged >> m) & 1) {
             fL += dterm * K.fKd[m];
             const int base = 4 + NL + 5 * SH::ci(m);
-            const double dcl = ALPHA * l1 + BETA * l0, dcr = ALPHA * r0 + BETA * r1;
-            const double dHm = F(base + 1) * dgl + F(base + 2) * dcl + F(base + 3) * dgr + F(base + 4) * dcr;
-            const double mterm = dHm * BL + F(base) * dBL;
+            const S dcl = A_ * l1 + B_ * l0, dcr = A_ * r0 + B_ * r1;
+            const S dHm = F(base + 1) * dgl + F(base + 2) * dcl + F(base + 3) * dgr + F(base + 4) * dcr;
+            const S mterm = dHm * BL + F(base) * dBL;
             f += mterm * K.fK[m];
             fL += mterm * K.fKm[m];
         }
         put(m, f);
     }
     put(NL, fL);
-    double fS = 0.0;
+    S fS = S(0);
     if (g.phase[cell] == 1 && g.phase[qc] == 1) {
         const int s = g.cmap[cell], sq = g.cmap[qc];
         fS = bracket(V(Chem::PHIS, n0, s), V(Chem::PHIS, n1, s), V(Chem::PHIS, n0, sq), V(Chem::PHIS, n1, sq)) * K.fS;
@@ -1064,15 +1075,15 @@ __global__ void __launch_bounds__(128) k_lin_face_flux(const DevParams p, const 
     put(NL + 1, fS);
 }
 
-template <class Chem>
-__global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, const LinK K, const Geo g,
-                                                         const double* __restrict__ z, const double* __restrict__ v,
-                                                         const double* __restrict__ gb, const double* __restrict__ gbd,
-                                                         const double* __restrict__ flux, int d,
-                                                         double* __restrict__ out) {
+template <class Chem, class S>
+__global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, const LinKT<S> K, const Geo g,
+                                                         const S* __restrict__ z, const S* __restrict__ v,
+                                                         const S* __restrict__ gb, const S* __restrict__ gbd,
+                                                         const S* __restrict__ flux, int d, S* __restrict__ out) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 4) return;
     constexpr int NL = Chem::NL;
+    const S A_ = S(ALPHA), B_ = S(BETA);
     const int q = (int)(b / p.n_cell);
     const int cell = (int)(b - (int64_t)q * p.n_cell);
     int i, j, k;
@@ -1082,37 +1093,37 @@ __global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, cons
     const int coord = d == 0 ? i : d == 1 ? j : k;
     const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
     const bool hasL = coord > 0;
-    const double* Fp = flux + (int64_t)q * (NL + 2) * p.n_cell + cell;                 // own +d face
-    const double* Fm = flux + (int64_t)q * (NL + 2) * p.n_cell + (hasL ? cell - stride : cell);
+    const S* Fp = flux + (int64_t)q * (NL + 2) * p.n_cell + cell;                 // own +d face
+    const S* Fm = flux + (int64_t)q * (NL + 2) * p.n_cell + (hasL ? cell - stride : cell);
     auto V = [&](int f, int n, int idx) { return v[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
     auto Z = [&](int f, int n, int idx) { return z[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
     // own face as left voxel adds +f (ALPHA to n1, BETA to n0); the -d face, where this voxel is the
     // right one, adds -f (ALPHA to n0, BETA to n1); fl is the volume flux along the line
-    auto gather = [&](int e, int f, int idx, double fl) {
-        const double fp = Fp[(int64_t)e * p.n_cell];
-        const double fm = hasL ? Fm[(int64_t)e * p.n_cell] : 0.0;
-        const double o1 = fl + ALPHA * fp - BETA * fm;
-        const double o0 = -fl + BETA * fp - ALPHA * fm;
+    auto gather = [&](int e, int f, int idx, S fl) {
+        const S fp = Fp[(int64_t)e * p.n_cell];
+        const S fm = hasL ? Fm[(int64_t)e * p.n_cell] : S(0);
+        const S o1 = fl + A_ * fp - B_ * fm;
+        const S o0 = -fl + B_ * fp - A_ * fm;
         out[p.off[f] + (int64_t)n0 * p.flen[f] + idx] += o0;
         out[p.off[f] + (int64_t)n1 * p.flen[f] + idx] += o1;
     };
-    const double gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
-    const double dgN0 = gbd[(int64_t)n0 * p.n_cell + cell], dgN1 = gbd[(int64_t)n1 * p.n_cell + cell];
-    const double dPhi = Z(Chem::PHIL, n1, cell) - Z(Chem::PHIL, n0, cell);
-    const double ddPhi = V(Chem::PHIL, n1, cell) - V(Chem::PHIL, n0, cell);
-    const double gsum = gN0 + gN1, dgsum = dgN0 + dgN1;
-    double flL = 0.0;
+    const S gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
+    const S dgN0 = gbd[(int64_t)n0 * p.n_cell + cell], dgN1 = gbd[(int64_t)n1 * p.n_cell + cell];
+    const S dPhi = Z(Chem::PHIL, n1, cell) - Z(Chem::PHIL, n0, cell);
+    const S ddPhi = V(Chem::PHIL, n1, cell) - V(Chem::PHIL, n0, cell);
+    const S gsum = gN0 + gN1, dgsum = dgN0 + dgN1;
+    S flL = S(0);
 #pragma unroll
     for (int m = 0; m < NL; ++m) {
-        const double C0 = Z(m, n0, cell), C1 = Z(m, n1, cell);
-        const double dC0 = V(m, n0, cell), dC1 = V(m, n1, cell);
-        const double A = dgsum * (C1 - C0) + gsum * (dC1 - dC0);     // tangent of g_sum dc
-        double fl = A * K.vD[m];
-        if (p.zc[m] != 0.0) {
+        const S C0 = Z(m, n0, cell), C1 = Z(m, n1, cell);
+        const S dC0 = V(m, n0, cell), dC1 = V(m, n1, cell);
+        const S A = dgsum * (C1 - C0) + gsum * (dC1 - dC0);     // tangent of g_sum dc
+        S fl = A * K.vD[m];
+        if ((K.charged >> m) & 1) {
             flL += A * K.vKd[m];
-            const double msum = gN0 * C0 + gN1 * C1;
-            const double dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
-            const double B = dmsum * dPhi + msum * ddPhi;             // tangent of (g c)_sum dPhi
+            const S msum = gN0 * C0 + gN1 * C1;
+            const S dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
+            const S B = dmsum * dPhi + msum * ddPhi;             // tangent of (g c)_sum dPhi
             fl += B * K.vK[m];
             flL += B * K.vKm[m];
         }
@@ -1131,10 +1142,10 @@ __global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, cons
 // face points of the three lines through n), the volume term of each of those lines and the two
 // faces at the ends of each line, where node n enters through its trace (weight ALPHA or BETA)
 // and the normal-derivative term (+-sqrt(3)/h).  One thread per (node, voxel); FMAs only.
-template <class Chem>
+template <class Chem, class LT>
 __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                 const double* __restrict__ gb, const double* __restrict__ gam,
-                                                 const double* __restrict__ jn, const double* __restrict__ face, double dt,
+                                                 const double* __restrict__ gb, const LT* __restrict__ gam,
+                                                 const LT* __restrict__ jn, const LT* __restrict__ face, double dt,
                                                  int relax, const NodeDiag nd, double* __restrict__ blk) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 8) return;
@@ -1149,7 +1160,7 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
     const int an[3] = {n & 1, (n >> 1) & 1, (n >> 2) & 1};
     const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h, gq = SQ3 / p.h, pen = p.penalty / p.h;
     auto Z = [&](int f, int nn) { return z[p.off[f] + (int64_t)nn * p.flen[f] + cell]; };
-    const double* J = st ? jn + (int64_t)n * NF * NF * p.n_struct + g.cmap[cell] : nullptr;
+    const LT* J = st ? jn + (int64_t)n * NF * NF * p.n_struct + g.cmap[cell] : nullptr;
     const double ddc = ph == 2 ? nd.c_sep : nd.c_pore, ddphi = nd.phi;
     double* B = blk + b * NF * NF;
 #pragma unroll 1
@@ -1161,7 +1172,7 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
         double col[NF];
         if (st) {
 #pragma unroll
-            for (int r = 0; r < NF; ++r) col[r] = J[(int64_t)(r * NF + c) * p.n_struct];
+            for (int r = 0; r < NF; ++r) col[r] = double(J[(int64_t)(r * NF + c) * p.n_struct]);
         } else {
 #pragma unroll
             for (int r = 0; r < NF; ++r) col[r] = r != c ? 0.0 : (r < NL ? ddc : (r == PHIL ? ddphi : 0.0));
@@ -1172,7 +1183,7 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
         const double del = (NS == 2 && st && (c == NL || c == NL + 1)) ? -1.0 : 0.0;   // of eps_L
         auto dg_at = [&](int slot, double w) {
             const int64_t o = (int64_t)slot * p.n_cell + cell;
-            return gb[o] * (gam[o] * del - p.visc * dcs) * w;
+            return gb[o] * (double(gam[o]) * del - p.visc * dcs) * w;
         };
         const double dgN = dg_at(n, 1.0);
 #pragma unroll 1
@@ -1222,8 +1233,8 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
                 const bool inside = left ? coord + 1 < ext : coord > 0;
                 if (!inside) {
                     if (left && d == 0) {   // anode face: r_Ano(c_Li, Phi^L) at the face point
-                        const double* Fo = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
-                        const double drA = Fo[0] * (dm == 0 ? tw : 0.0) + Fo[(int64_t)p.n_cell] * (dPL ? tw : 0.0);
+                        const LT* Fo = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
+                        const double drA = double(Fo[0]) * (dm == 0 ? tw : 0.0) + double(Fo[(int64_t)p.n_cell]) * (dPL ? tw : 0.0);
                         if (!relax) col[0] += drA * p.kAno * wrow;
                         col[PHIL] += drA * p.F * p.kAno * wrow;
                     }
@@ -1231,8 +1242,8 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
                 }
                 const int fc = left ? cell : cell - stride;        // voxel owning the face data
                 const int oc = left ? cell + stride : cell - stride;   // the other voxel
-                const double* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + fc;
-                auto F = [&](int kk) { return Fd[(int64_t)kk * p.n_cell]; };
+                const LT* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + fc;
+                auto F = [&](int kk) { return double(Fd[(int64_t)kk * p.n_cell]); };
                 const double dgo = dg_at(face_slot(d, side, q), tw);   // own g at this face point
                 const double dHg = (left ? F(1) : F(2)) * dgo;
                 const double Hg = F(0), BL = F(3 + NL);
@@ -1279,56 +1290,87 @@ int64_t dg1_lin_sizes(const DevParams& p, int64_t* jn, int64_t* gam, int64_t* fa
 int64_t dg1_lin_flux_len(const DevParams& p) { return (int64_t)4 * (p.nl + 2) * p.n_cell;
 }
 
-template <class Chem>
+template <class Chem, class LT>
 static cudaError_t linearize_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t,
-                                  double dt, int relax, const DG1Lin& lin) {
-    k_dg1_g<Chem, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, lin.gb, lin.gb);
-    k_lin_gam<Chem><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, lin.gam);
+                                  double dt, int relax, LT* jn, LT* gam, LT* face, double* gb) {
+    k_dg1_g<Chem, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
+    k_lin_gam<Chem, LT><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, gam);
     if (p.n_struct > 0)
-        k_lin_nodes_build<Chem><<<nblocks((int64_t)p.n_struct * 8, 64), 64, 0, L.st>>>(p, g, z, t, dt, relax, lin.jn);
+        k_lin_nodes_build<Chem, LT><<<nblocks((int64_t)p.n_struct * 8, 64), 64, 0, L.st>>>(p, g, z, t, dt, relax, jn);
     for (int d = 0; d < 3; ++d)
-        k_lin_faces_build<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, lin.gb, d, lin.face);
+        k_lin_faces_build<Chem, LT><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, gb, d, face);
     *L.counter += 6;
     return cudaGetLastError();
 }
 
+// Linearise at z: FP64 arithmetic; stored in FP64, or in FP32 (lin.f32) for the FP32 product of
+// the mixed-precision path (the FP64 transport factors stay in lin.gb for the preconditioner).
 cudaError_t dg1_linearize(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t, double dt,
                           int relax, const DG1Lin& lin) {
-    return p.nf == 10 ? linearize_impl<ChemTO>(L, p, g, z, t, dt, relax, lin)
-                      : linearize_impl<ChemR3>(L, p, g, z, t, dt, relax, lin);
+    cudaError_t e;
+    if (lin.f32) {
+        e = p.nf == 10 ? linearize_impl<ChemTO, float>(L, p, g, z, t, dt, relax, lin.jn32, lin.gam32, lin.face32, lin.gb)
+                       : linearize_impl<ChemR3, float>(L, p, g, z, t, dt, relax, lin.jn32, lin.gam32, lin.face32, lin.gb);
+        if (e == cudaSuccess) e = to_f32(L, lin.gb32, lin.gb, (int64_t)NG * p.n_cell);
+        return e;
+    }
+    return p.nf == 10 ? linearize_impl<ChemTO, double>(L, p, g, z, t, dt, relax, lin.jn, lin.gam, lin.face, lin.gb)
+                      : linearize_impl<ChemR3, double>(L, p, g, z, t, dt, relax, lin.jn, lin.gam, lin.face, lin.gb);
 }
 
-template <class Chem>
-static cudaError_t lin_apply_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
-                                  double t, double dt, int relax, double sc_dt, double* out, const DG1Lin& lin) {
-    k_lin_g<Chem><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, v, lin.gb, lin.gam, lin.gbd);
+template <class Chem, class S>
+static cudaError_t lin_apply_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v,
+                                  double dt, int relax, double sc_dt, S* out, const S* jn, const S* gam, const S* face,
+                                  const S* gb, S* gbd, S* flux) {
+    const LinKT<S> K = make_link<S>(p, Chem::NL, Chem::NF, Chem::PHIL, Chem::PHIS, relax, dt, sc_dt);
+    k_lin_g<Chem, S><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, K, g, v, gb, gam, gbd);
     if (p.n_struct > 0)
-        k_lin_nodes_apply<Chem><<<nblocks((int64_t)p.n_struct * 8, 128), 128, 0, L.st>>>(p, g, v, lin.jn, sc_dt, out);
-    k_lin_nodes_diag<Chem><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, make_node_diag(p, dt, relax), g, v,
-                                                                                   sc_dt, out);
-    const LinK K = make_link(p, Chem::NL, Chem::PHIL, Chem::PHIS, relax, sc_dt);
+        k_lin_nodes_apply<Chem, S><<<nblocks((int64_t)p.n_struct * 8, 128), 128, 0, L.st>>>(p, K, g, v, jn, out);
+    k_lin_nodes_diag<Chem, S><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, K, g, v, out);
     for (int d = 0; d < 3; ++d) {
-        k_lin_face_flux<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, K, g, v, lin.gbd, lin.face, d,
-                                                                                      lin.flux);
-        k_lin_line_gather<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, K, g, z, v, lin.gb, lin.gbd,
-                                                                                        lin.flux, d, out);
+        k_lin_face_flux<Chem, S><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, K, g, v, gbd, face, d, flux);
+        k_lin_line_gather<Chem, S><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, K, g, z, v, gb, gbd, flux, d,
+                                                                                           out);
     }
     *L.counter += 9;
     return cudaGetLastError();
 }
 
-cudaError_t dg1_lin_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
-                          double t, double dt, int relax, double sc_dt, double* out, const DG1Lin& lin) {
-    return p.nf == 10 ? lin_apply_impl<ChemTO>(L, p, g, z, v, t, dt, relax, sc_dt, out, lin)
-                      : lin_apply_impl<ChemR3>(L, p, g, z, v, t, dt, relax, sc_dt, out, lin);
+template <>
+cudaError_t dg1_lin_apply<double>(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
+                                  double t, double dt, int relax, double sc_dt, double* out, const DG1Lin& lin) {
+    if (lin.f32) return cudaErrorInvalidValue;
+    return p.nf == 10 ? lin_apply_impl<ChemTO, double>(L, p, g, z, v, dt, relax, sc_dt, out, lin.jn, lin.gam, lin.face,
+                                                       lin.gb, lin.gbd, lin.flux)
+                      : lin_apply_impl<ChemR3, double>(L, p, g, z, v, dt, relax, sc_dt, out, lin.jn, lin.gam, lin.face,
+                                                       lin.gb, lin.gbd, lin.flux);
+}
+
+template <>
+cudaError_t dg1_lin_apply<float>(const LaunchCtx& L, const DevParams& p, const Geo& g, const float* z, const float* v,
+                                 double t, double dt, int relax, double sc_dt, float* out, const DG1Lin& lin) {
+    if (!lin.f32) return cudaErrorInvalidValue;
+    return p.nf == 10 ? lin_apply_impl<ChemTO, float>(L, p, g, z, v, dt, relax, sc_dt, out, lin.jn32, lin.gam32,
+                                                      lin.face32, lin.gb32, lin.gbd32, lin.flux32)
+                      : lin_apply_impl<ChemR3, float>(L, p, g, z, v, dt, relax, sc_dt, out, lin.jn32, lin.gam32,
+                                                      lin.face32, lin.gb32, lin.gbd32, lin.flux32);
 }
 
 cudaError_t dg1_lin_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double dt, int relax,
                            const DG1Lin& lin, double* blk) {
     const int nb = nblocks((int64_t)p.n_cell * 8, 128);
     const NodeDiag nd = make_node_diag(p, dt, relax);
-    if (p.nf == 10) k_lin_blk<ChemTO><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);
-    else k_lin_blk<ChemR3><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);
+    if (lin.f32) {
+        if (p.nf == 10)
+            k_lin_blk<ChemTO, float><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam32, lin.jn32, lin.face32, dt, relax, nd, blk);
+        else
+            k_lin_blk<ChemR3, float><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam32, lin.jn32, lin.face32, dt, relax, nd, blk);
+    } else {
+        if (p.nf == 10)
+            k_lin_blk<ChemTO, double><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);
+        else
+            k_lin_blk<ChemR3, double><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);
+    }
     *L.counter += 1;
     return cudaGetLastError();
 }

@@ -63,12 +63,14 @@ cudaError_t dg1_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, co
 int64_t dg1_face_buffer_len(const DevParams& p);
 // Linearised FP64 DG1 JVP: cached derivative data at a fixed linearisation point.
 struct DG1Lin {
-    double* jn;     // [8][NF*NF][n_struct] node Jacobians of the structure voxels
-    double* gam;    // [32][n_cell] 3/(2 eps_L) per transport-factor slot
-    double* face;   // [12][NFD][n_cell] face data of the + faces
-    double* gb;     // [32][n_cell] transport factors at the linearisation point
-    double* gbd;    // [32][n_cell] their tangents (apply scratch)
-    double* flux;   // [4][NL+2][n_cell] face-flux tangents of one direction (apply scratch)
+    bool f32 = false;       // linearisation stored in FP32 for the FP32 product (mixed precision)
+    double* jn = nullptr;   // [8][NF*NF][n_struct] node Jacobians of the structure voxels
+    double* gam = nullptr;  // [32][n_cell] 3/(2 eps_L) per transport-factor slot
+    double* face = nullptr; // [12][NFD][n_cell] face data of the + faces
+    double* gb = nullptr;   // [32][n_cell] transport factors at the linearisation point (FP64 in both modes)
+    double* gbd = nullptr;  // [32][n_cell] their tangents (apply scratch)
+    double* flux = nullptr; // [4][NL+2][n_cell] face-flux tangents of one direction (apply scratch)
+    float *jn32 = nullptr, *gam32 = nullptr, *face32 = nullptr, *gb32 = nullptr, *gbd32 = nullptr, *flux32 = nullptr;
 };
 int64_t dg1_lin_flux_len(const DevParams& p);
 // per-node diagonal blocks of S J (dt-scaled rows) from a current linearisation at z
@@ -77,8 +79,9 @@ cudaError_t dg1_lin_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g,
 int64_t dg1_lin_sizes(const DevParams& p, int64_t* jn, int64_t* gam, int64_t* face);
 cudaError_t dg1_linearize(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t, double dt,
                           int relax, const DG1Lin& lin);
-cudaError_t dg1_lin_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* v,
-                          double t, double dt, int relax, double sc_dt, double* out, const DG1Lin& lin);
+template <class S>
+cudaError_t dg1_lin_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v,
+                          double t, double dt, int relax, double sc_dt, S* out, const DG1Lin& lin);
 
 // ------------------------------------------------------------------ linear algebra (la.cu)
 // Block-Jacobi: invert nblk blocks of nf x nf (row-major) in place; identity rows for absent

@@ -94,3 +94,18 @@ def test_dg1_cell_voltage_and_ledger():
     mo = lis.cell_means(model, grid, z)
     assert abs(led[0] - mo["sulfur"]) <= 1e-12 * abs(mo["sulfur"])
     assert abs(led[1] - mo["lithium"]) <= 1e-12 * abs(mo["lithium"])
+
+
+def test_dg1_mixed_precision_step_matches_fp64():
+    """The mixed-precision path (FP32 product from the FP32 copy of the linearisation, FP32 Krylov
+    basis and blocks, FP64 Newton) reaches the FP64 step's state to 1e-8."""
+    from paper_2511_05233_gb300 import dgls
+
+    model, grid, phase, z0, z = make_case("tradeoff", 1, (8, 5, 4), potential_noise=0.01)
+    c64 = gpu_context(model, phase)
+    c32 = gpu_context(model, phase, precision=dgls.MIXED)
+    a, b = to_dev(np.zeros_like(z)), to_dev(np.zeros_like(z))
+    _, i64 = c64.step(to_dev(z), a, 0.0, 1e-3)
+    _, i32 = c32.step(to_dev(z), b, 0.0, 1e-3)
+    assert i64.converged and i32.converged
+    assert_state_close(model, grid, to_host(b), to_host(a), 1e-8)
