@@ -61,9 +61,10 @@ def workspace_estimate(req):
     return dof * 8 * (31 + 20) + n * nn * 100 * 8 + (64 << 20)
 
 
-def run_one(req, stream=None):
+def run_one(req, stream=None, precision=None, keep_state=False):
     """Set up the cell, take the Tab. 6 equilibrium state and run the naive controller for
-    req.n_steps accepted steps; returns the curve and a checksum of the final state."""
+    req.n_steps accepted steps; returns the curve and a checksum of the final state (and the state
+    itself with keep_state).  precision: dgls.FP64 (default) or dgls.MIXED."""
     import torch
 
     from . import dgls, inputs
@@ -74,7 +75,8 @@ def run_one(req, stream=None):
         if np.any(ph[:, :, 0] == inputs.STRUCT):
             phase = ph
             break
-    prm = dgls.default_params(dgls.TRADEOFF, req.order, f_C=req.f_C, eps_struct=1 - req.porosity)
+    prm = dgls.default_params(dgls.TRADEOFF, req.order, f_C=req.f_C, eps_struct=1 - req.porosity,
+                              precision=dgls.FP64 if precision is None else precision)
     with torch.cuda.stream(stream) if stream is not None else _null():
         ctx = dgls.Context(phase, 1e-6, prm, stream=stream or torch.cuda.current_stream())
         z = ctx.new_state()
@@ -82,9 +84,12 @@ def run_one(req, stream=None):
         res = ctx.discharge(z, controller=dgls.NAIVE, dt0=1e-3, max_steps=req.n_steps)
         zh = z.cpu().numpy()
         ctx.close()
-    return {"t": res["t"].tolist(), "dt": res["dt"].tolist(), "U_cell": res["U_cell"].tolist(),
-            "status": res["status"], "sha256": hashlib.sha256(zh.tobytes()).hexdigest(),
-            "n_dof": int(zh.size)}
+    out = {"t": res["t"].tolist(), "dt": res["dt"].tolist(), "U_cell": res["U_cell"].tolist(),
+           "status": res["status"], "sha256": hashlib.sha256(zh.tobytes()).hexdigest(),
+           "n_dof": int(zh.size)}
+    if keep_state:
+        out["state"] = zh
+    return out
 
 
 class _null:
@@ -95,7 +100,7 @@ class _null:
         return False
 
 
-def serve(requests, slots=4, hbm_budget=150 << 30, time_scale=1.0):
+def serve(requests, slots=4, hbm_budget=150 << 30, time_scale=1.0, precision=None, keep_state=False):
     """Run the requests with continuous batching; returns them with start/end times filled."""
     import torch
 
@@ -110,7 +115,7 @@ def serve(requests, slots=4, hbm_budget=150 << 30, time_scale=1.0):
     def worker(req, sidx, need):
         req.start = time.perf_counter() - t0
         try:
-            req.result = run_one(req, streams[sidx])
+            req.result = run_one(req, streams[sidx], precision, keep_state)
         except Exception as e:  # a failed request is reported, not fatal to the server
             req.result = {"status": f"error: {e}"}
         req.end = time.perf_counter() - t0
@@ -152,7 +157,7 @@ def serve(requests, slots=4, hbm_budget=150 << 30, time_scale=1.0):
     return requests, time.perf_counter() - t0
 
 
-def sequential(requests, time_scale=1.0):
+def sequential(requests, time_scale=1.0, precision=None, keep_state=False):
     """The plain loop: one request at a time on the default stream, each starting at its arrival
     or when the previous one is done."""
     t0 = time.perf_counter()
@@ -161,9 +166,24 @@ def sequential(requests, time_scale=1.0):
         if r.arrival * time_scale > now:
             time.sleep(r.arrival * time_scale - now)
         r.start = time.perf_counter() - t0
-        r.result = run_one(r)
+        r.result = run_one(r, None, precision, keep_state)
         r.end = time.perf_counter() - t0
     return requests, time.perf_counter() - t0
+
+
+def max_rel_diff(reqs, refs):
+    """Largest relative difference over the requests of the U_cell curve and of the final state
+    (scaled by the largest value of that request's quantity) against reference runs."""
+    by_id = {r.rid: r for r in refs}
+    du = ds = 0.0
+    for r in reqs:
+        a, b = r.result, by_id[r.rid].result
+        if "state" not in a or "state" not in b or len(a["U_cell"]) != len(b["U_cell"]):
+            return None
+        ua, ub = np.asarray(a["U_cell"]), np.asarray(b["U_cell"])
+        du = max(du, float(np.abs(ua - ub).max() / np.abs(ub).max()))
+        ds = max(ds, float(np.abs(a["state"] - b["state"]).max() / np.abs(b["state"]).max()))
+    return {"U_cell": du, "state": ds}
 
 
 def latency_stats(reqs, wall):
@@ -179,18 +199,29 @@ def main():
     ap.add_argument("--rate", type=float, default=4.0, help="Poisson arrival rate, requests per second")
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="precision of the served runs; the sequential baseline is always FP64")
     a = ap.parse_args()
     import copy
 
+    from . import dgls
+
+    prec = dgls.MIXED if a.precision == "mixed" else dgls.FP64
     reqs = make_requests(a.requests, a.rate, a.seed, n_steps=a.steps)
-    served, wall = serve(copy.deepcopy(reqs), slots=a.slots)
-    seqd, wall_seq = sequential(copy.deepcopy(reqs))
-    same = all(x.result.get("U_cell") == y.result.get("U_cell") and x.result.get("sha256") == y.result.get("sha256")
-               for x, y in zip(sorted(served, key=lambda r: r.rid), sorted(seqd, key=lambda r: r.rid)))
-    print(json.dumps({"served": latency_stats(served, wall), "sequential": latency_stats(seqd, wall_seq),
-                      "identical_results_alone_and_in_mix": bool(same),
-                      "requests": len(reqs), "slots": a.slots,
-                      "statuses": sorted({r.result.get("status") for r in served})}))
+    served, wall = serve(copy.deepcopy(reqs), slots=a.slots, precision=prec, keep_state=True)
+    seqd, wall_seq = sequential(copy.deepcopy(reqs), keep_state=True)
+    out = {"served": latency_stats(served, wall), "sequential_fp64": latency_stats(seqd, wall_seq),
+           "precision_served": a.precision, "requests": len(reqs), "slots": a.slots,
+           "statuses": sorted({r.result.get("status") for r in served})}
+    if prec == dgls.FP64:
+        out["identical_results_alone_and_in_mix"] = all(
+            x.result.get("U_cell") == y.result.get("U_cell") and x.result.get("sha256") == y.result.get("sha256")
+            for x, y in zip(sorted(served, key=lambda r: r.rid), sorted(seqd, key=lambda r: r.rid)))
+    else:
+        out["max_rel_diff_vs_fp64"] = max_rel_diff(served, seqd)
+    out["throughput_gain"] = out["served"]["sims_per_hr"] / out["sequential_fp64"]["sims_per_hr"]
+    out["p99_gain"] = out["sequential_fp64"]["p99_s"] / out["served"]["p99_s"]
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

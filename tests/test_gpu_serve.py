@@ -27,3 +27,20 @@ def test_served_results_equal_sequential_results():
         assert r.result["sha256"] == ref["sha256"]
     overlap = any(a.start < b.end and b.start < a.end for a in served for b in served if a.rid < b.rid)
     assert overlap, "no two requests ran concurrently"
+
+
+def test_mixed_precision_serving_matches_fp64():
+    """Requests served concurrently in mixed precision: bitwise the same as the same mixed runs
+    alone, and within 1e-8 (U_cell curve and final state, relative) of the FP64 runs."""
+    from paper_2511_05233_gb300 import dgls, serve
+
+    reqs = serve.make_requests(4, rate_hz=50.0, seed=5, side_range=(10, 14), n_steps=3)
+    served, _ = serve.serve(copy.deepcopy(reqs), slots=3, precision=dgls.MIXED, keep_state=True)
+    alone, _ = serve.sequential(copy.deepcopy(reqs), time_scale=0.0, precision=dgls.MIXED, keep_state=True)
+    ref, _ = serve.sequential(copy.deepcopy(reqs), time_scale=0.0, keep_state=True)
+    by_id = {r.rid: r for r in alone}
+    for r in served:
+        assert r.result["status"] == "DG_OK", r.result
+        assert r.result["sha256"] == by_id[r.rid].result["sha256"]
+    err = serve.max_rel_diff(served, ref)
+    assert err is not None and err["U_cell"] <= 1e-8 and err["state"] <= 1e-8, err
