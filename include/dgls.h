@@ -109,6 +109,7 @@ typedef struct {
     int32_t max_halvings;      /* consecutive halvings before DG_ERR_ABORTED (30) */
     const double* replay_dt;   /* host array: if non-NULL take these step sizes (n_replay) */
     int32_t n_replay;
+    int32_t limiter;           /* DG1: 1 applies dg_limit to the state after every accepted step */
 } dg_discharge_opts;
 
 typedef struct {               /* caller-allocated host arrays of length n_max */
@@ -213,6 +214,16 @@ dg_status dg_discharge(dg_ctx* ctx, double* z_dev, const dg_discharge_opts* opts
  * dg_profile_read fills ms[5] (summed device milliseconds) and launches[5] (calls). */
 dg_status dg_profile(dg_ctx* ctx, int32_t enable);
 dg_status dg_profile_read(const dg_ctx* ctx, double ms[5], int64_t calls[5]);
+
+/* Vertex-based slope limiter of App. B (Kuzmin's rule, which the paper applies to its DG1 scheme
+ * because that scheme is not positivity-preserving, Sec. 2.6), in place on the liquid species of a
+ * DG1 state z_dev.  Per voxel and species, the deviation of the conserved density q = eps_L c from
+ * its voxel mean is scaled by the largest factor in [0, 1] that keeps the Q1 field's value at every
+ * voxel corner within the range of the means of the voxels sharing that corner (only voxels inside
+ * the domain).  Voxel means of q, hence all species amounts, are unchanged; non-negative means give
+ * non-negative nodal concentrations.  Solid fractions and potentials are left alone.  DG_ERR_ARG for
+ * DG0 contexts.  Asynchronous on the context's stream; uses the context's scratch. */
+dg_status dg_limit(dg_ctx* ctx, double* z_dev);
 
 /* Number of CUDA kernels this context has launched (monotone counter). */
 int64_t dg_launch_count(const dg_ctx* ctx);

@@ -626,6 +626,13 @@ extern "C" dg_status dg_block_jacobi(dg_ctx* ctx, const double* z, double t, dou
     return DG_OK;
 }
 
+extern "C" dg_status dg_limit(dg_ctx* ctx, double* z) {
+    if (!ctx || !z) return fail(ctx, DG_ERR_ARG, "dg_limit: bad argument");
+    if (ctx->P.order != 1) return fail(ctx, DG_ERR_ARG, "dg_limit: the slope limiter acts on DG1 states");
+    CK(dg1_limit(ctx->L, ctx->P, ctx->G, z, ctx->gbd));
+    return DG_OK;
+}
+
 extern "C" dg_status dg_row_scales(dg_ctx* ctx, double dt, double* s) {
     if (!ctx || !s || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_row_scales: bad argument");
     CK(row_scales(ctx->L, ctx->P, dt, s));
@@ -1003,6 +1010,7 @@ extern "C" dg_status dg_discharge(dg_ctx* ctx, double* z, const dg_discharge_opt
             std::swap(cur, nxt);
             t += dt;
             halv = 0;
+            if (o->limiter && ctx->P.order == 1) CK(dg1_limit(L, ctx->P, ctx->G, cur, ctx->gbd));
             double U;
             dg_status s = dg_cell_voltage(ctx, cur, &U);
             if (s != DG_OK) return s;

@@ -1375,6 +1375,104 @@ cudaError_t dg1_lin_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g,
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ slope limiter
+// Vertex-based slope limiter (App. B, after Kuzmin 2010) on the conserved densities q = eps_L c of
+// the liquid species: per voxel and species the deviation of q from its voxel mean is scaled by the
+// largest factor in [0, 1] that keeps the Q1 field at each of the 8 voxel corners within the range of
+// the means of the voxels sharing that corner.  Voxel means (hence every species) are unchanged.
+template <class Chem>
+__device__ __forceinline__ void node_eps_l(const DevParams& p, const Geo& g, const double* z, int cell, double* eL) {
+    const int ph = g.phase[cell];
+    const int s = g.cmap[cell];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        double es[2] = {0.0, 0.0};
+        if (Chem::NS == 2 && ph == 1) {
+            es[0] = ld(z, p, Chem::NL, n, s);
+            es[1] = ld(z, p, Chem::NL + 1, n, s);
+        }
+        eL[n] = liquid_fraction<Chem, double>(p, ph, es);
+    }
+}
+
+template <class Chem>
+__global__ void __launch_bounds__(128) k_lim_means(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                   double* __restrict__ mean) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    double eL[8];
+    node_eps_l<Chem>(p, g, z, cell, eL);
+#pragma unroll 1
+    for (int m = 0; m < Chem::NL; ++m) {
+        double acc = 0.0;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) acc += eL[n] * ld(z, p, m, n, cell);
+        mean[(int64_t)m * p.n_cell + cell] = acc / 8.0;
+    }
+}
+
+template <class Chem>
+__global__ void __launch_bounds__(128) k_lim_apply(const DevParams p, const Geo g, const double* __restrict__ mean,
+                                                   double* __restrict__ z) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    int i, j, k;
+    cell_ijk(p, cell, i, j, k);
+    double eL[8];
+    node_eps_l<Chem>(p, g, z, cell, eL);
+    const double W[2][2] = {{ALPHA, BETA}, {BETA, ALPHA}};   // W[corner side][node side]
+#pragma unroll 1
+    for (int m = 0; m < Chem::NL; ++m) {
+        const double* M = mean + (int64_t)m * p.n_cell;
+        const double qbar = M[cell];
+        double q[8];
+#pragma unroll
+        for (int n = 0; n < 8; ++n) q[n] = eL[n] * ld(z, p, m, n, cell);
+        double alpha = 1.0;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+            double uc = 0.0;
+#pragma unroll
+            for (int n = 0; n < 8; ++n) uc += W[cx][n & 1] * W[cy][(n >> 1) & 1] * W[cz][n >> 2] * q[n];
+            double vmax = -INFINITY, vmin = INFINITY;
+            for (int kk = k + cz - 1; kk <= k + cz; ++kk) {
+                if (kk < 0 || kk >= p.nz) continue;
+                for (int jj = j + cy - 1; jj <= j + cy; ++jj) {
+                    if (jj < 0 || jj >= p.ny) continue;
+                    for (int ii = i + cx - 1; ii <= i + cx; ++ii) {
+                        if (ii < 0 || ii >= p.nx) continue;
+                        const double v = M[ii + (int64_t)p.nx * (jj + (int64_t)p.ny * kk)];
+                        vmax = fmax(vmax, v);
+                        vmin = fmin(vmin, v);
+                    }
+                }
+            }
+            const double d = uc - qbar;
+            if (d > 0.0) alpha = fmin(alpha, fmin(1.0, (vmax - qbar) / d));
+            else if (d < 0.0) alpha = fmin(alpha, fmin(1.0, (vmin - qbar) / d));
+        }
+        if (alpha < 1.0) {
+#pragma unroll
+            for (int n = 0; n < 8; ++n)
+                z[p.off[m] + (int64_t)n * p.flen[m] + cell] = (qbar + alpha * (q[n] - qbar)) / eL[n];
+        }
+    }
+}
+
+cudaError_t dg1_limit(const LaunchCtx& L, const DevParams& p, const Geo& g, double* z, double* scratch) {
+    const int nb = nblocks(p.n_cell, 128);
+    if (p.nf == 10) {
+        k_lim_means<ChemTO><<<nb, 128, 0, L.st>>>(p, g, z, scratch);
+        k_lim_apply<ChemTO><<<nb, 128, 0, L.st>>>(p, g, scratch, z);
+    } else {
+        k_lim_means<ChemR3><<<nb, 128, 0, L.st>>>(p, g, z, scratch);
+        k_lim_apply<ChemR3><<<nb, 128, 0, L.st>>>(p, g, scratch, z);
+    }
+    *L.counter += 2;
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 
 int64_t dg1_face_buffer_len(const DevParams& p) { return (int64_t)NG * p.n_cell; }

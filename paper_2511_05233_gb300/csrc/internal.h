@@ -73,6 +73,8 @@ struct DG1Lin {
     float *jn32 = nullptr, *gam32 = nullptr, *face32 = nullptr, *gb32 = nullptr, *gbd32 = nullptr, *flux32 = nullptr;
 };
 int64_t dg1_lin_flux_len(const DevParams& p);
+// vertex-based slope limiter of the liquid species of a DG1 state (scratch: NL x n_cell doubles)
+cudaError_t dg1_limit(const LaunchCtx& L, const DevParams& p, const Geo& g, double* z, double* scratch);
 // per-node diagonal blocks of S J (dt-scaled rows) from a current linearisation at z
 cudaError_t dg1_lin_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double dt, int relax,
                            const DG1Lin& lin, double* blk);

@@ -47,7 +47,7 @@ class DischargeOpts(C.Structure):
     _fields_ = [("controller", C.c_int32), ("t0", C.c_double), ("dt0", C.c_double), ("dt_min", C.c_double),
                 ("dt_max", C.c_double), ("tol", C.c_double), ("cutoff_V", C.c_double), ("t_end", C.c_double),
                 ("max_steps", C.c_int32), ("max_halvings", C.c_int32), ("replay_dt", C.POINTER(C.c_double)),
-                ("n_replay", C.c_int32)]
+                ("n_replay", C.c_int32), ("limiter", C.c_int32)]
 
 
 class Curve(C.Structure):
@@ -95,6 +95,7 @@ def lib():
             "dg_profile": (C.c_int, [_P, C.c_int32]),
             "dg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "dg_launch_count": (C.c_int64, [_P]),
+            "dg_limit": (C.c_int, [_P, _P]),
             "dg_reorth_count": (C.c_int64, [_P]),
             "dg_workspace_bytes": (C.c_int64, [_P]),
         }
@@ -245,7 +246,7 @@ class Context:
         return list(out)
 
     def discharge(self, z, controller=NAIVE, dt0=1e-3, dt_min=1e-6, dt_max=10.0, tol=1e-5, cutoff_V=1.9,
-                  t_end=0.0, max_steps=100000, max_halvings=30, replay_dt=None, t0=0.0):
+                  t_end=0.0, max_steps=100000, max_halvings=30, replay_dt=None, t0=0.0, limiter=False):
         n_max = max_steps if replay_dt is None else len(replay_dt)
         arr = {k: np.zeros(n_max) for k in ("t", "dt", "U_cell", "c_m")}
         nit = np.zeros(n_max, dtype=np.int32)
@@ -255,7 +256,7 @@ class Context:
             rp = np.ascontiguousarray(replay_dt, dtype=np.float64)
         o = DischargeOpts(controller, t0, dt0, dt_min, dt_max, tol, cutoff_V, t_end, max_steps, max_halvings,
                           rp.ctypes.data_as(C.POINTER(C.c_double)) if rp is not None else None,
-                          len(rp) if rp is not None else 0)
+                          len(rp) if rp is not None else 0, 1 if limiter else 0)
         cv = Curve(n_max, 0, *[arr[k].ctypes.data_as(C.POINTER(C.c_double)) for k in ("t", "dt", "U_cell", "c_m")],
                    nit.ctypes.data_as(C.POINTER(C.c_int32)), git.ctypes.data_as(C.POINTER(C.c_int32)), 0, 0, 0)
         st = self._lib.dg_discharge(self._h, _ptr(z), C.byref(o), C.byref(cv))
@@ -280,6 +281,10 @@ class Context:
 
     def launch_count(self):
         return int(self._lib.dg_launch_count(self._h))
+
+    def limit(self, z):
+        """Vertex-based slope limiter of the liquid species of a DG1 state, in place (asynchronous)."""
+        self._check(self._lib.dg_limit(self._h, _ptr(z)))
 
     def reorth_count(self):
         return int(self._lib.dg_reorth_count(self._h))

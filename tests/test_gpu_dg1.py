@@ -109,3 +109,43 @@ def test_dg1_mixed_precision_step_matches_fp64():
     _, i32 = c32.step(to_dev(z), b, 0.0, 1e-3)
     assert i64.converged and i32.converged
     assert_state_close(model, grid, to_host(b), to_host(a), 1e-8)
+
+
+def test_dg1_limiter_parity():
+    """dg_limit (vertex-based slope limiter on eps_L c) against the oracle's limiter."""
+    from oracle import limiter
+
+    model, grid, phase, z0, _ = make_case("tradeoff", 1, (7, 5, 4))
+    z = z0 * (1.0 + 0.4 * inputs.uniform_noise(z0.size, 11))
+    ref = limiter.kuzmin_limit(model, grid, z)
+    assert not np.array_equal(ref, z)
+    ctx = gpu_context(model, phase)
+    zd = to_dev(z)
+    ctx.limit(zd)
+    assert_state_close(model, grid, to_host(zd), ref, 1e-12)
+
+
+def test_dg1_discharge_with_limiter_matches_oracle():
+    """Naive controller with the limiter after every accepted step, against the oracle's controller
+    driving oracle steps followed by the oracle's limiter."""
+    from oracle import control, limiter
+    from paper_2511_05233_gb300 import dgls
+
+    model, grid, phase, z0, _ = make_case("reduced3", 1, (6, 4, 3))
+
+    def step(zz, t, dt):
+        z1, info = newton.implicit_euler_step(model, grid, zz, t, dt)
+        return info.converged, (limiter.kuzmin_limit(model, grid, z1) if info.converged else z1)
+
+    def cutoff(zz):
+        U = lis.cell_voltage(model, grid, zz)
+        return U <= 1.9, U
+
+    zf, rec = control.naive(step, cutoff, z0, dt0=1e-3, max_steps=3)
+    ctx = gpu_context(model, phase)
+    zd = to_dev(z0)
+    res = ctx.discharge(zd, controller=dgls.NAIVE, dt0=1e-3, max_steps=3, limiter=True)
+    assert res["status"] == "DG_OK"
+    assert np.allclose(res["dt"], rec.dt, rtol=1e-14, atol=0)
+    assert np.allclose(res["U_cell"], rec.U, rtol=1e-8, atol=0)
+    assert_state_close(model, grid, to_host(zd), zf, 1e-8)
