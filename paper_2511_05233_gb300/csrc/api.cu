@@ -403,15 +403,14 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
             ctx->lin.jn = jn; ctx->lin.gam = gam; ctx->lin.face = face; ctx->lin.gb = lgb; ctx->lin.gbd = ctx->gbd;
             ctx->lin.flux = lflux;
         } else {
-            // FP32 copy of the linearisation for the FP32 product; the FP64 transport factors it is
-            // built from live in the residual's scratch, read only by the preconditioner build that
-            // follows each linearisation, before any further residual evaluation
+            // FP32 linearisation (from the FP32 copy of z) for the FP32 products and blocks
             float *jn, *gam, *face, *lgb, *lflux;
             AL(jn, njn); AL(gam, ngam); AL(face, nface); AL(lgb, ngam); AL(lflux, dg1_lin_flux_len(P));
             ctx->lin.f32 = true;
             ctx->lin.jn32 = jn; ctx->lin.gam32 = gam; ctx->lin.face32 = face; ctx->lin.gb32 = lgb;
             ctx->lin.gbd32 = ctx->gbd32; ctx->lin.flux32 = lflux;
-            ctx->lin.gb = ctx->gb;
+            ctx->lin.z32 = ctx->z32;
+            ctx->lin.ndof = N;
         }
         ctx->has_lin = true;
     }
@@ -510,13 +509,14 @@ static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt
     if (ctx->prm.precision == DG_PREC_MIXED) {
         e = to_f32(ctx->L, ctx->z32, z, ctx->ndof);
         if (e == cudaSuccess) {
-            if (ctx->has_lin)   // DG1: FP64 blocks from the FP32 linearisation, inverted to FP32 below
+            if (ctx->has_lin)   // DG1: blocks from the FP32 linearisation, inverted to FP32 below
                 e = dg1_lin_blocks(ctx->L, ctx->P, ctx->G, z, dt, relax, ctx->lin, ctx->blk);
             else
                 e = dg0_blocks<float>(ctx->L, ctx->P, ctx->G, ctx->z32, t, dt, relax, ctx->blk, ctx->gb32);
         }
-        if (e == cudaSuccess && ctx->prm.preconditioner != 0 && !ctx->has_lin)
-            e = dg0_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb);
+        if (e == cudaSuccess && ctx->prm.preconditioner != 0)   // FP64 transport factors for the multigrid
+            e = ctx->P.order == 0 ? dg0_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb)
+                                  : dg1_gfactor(ctx->L, ctx->P, ctx->G, z, ctx->gb);
     } else if (ctx->has_lin) {
         // FP64 DG1: the blocks come from the linearisation at z, which the caller has just built
         e = dg1_lin_blocks(ctx->L, ctx->P, ctx->G, z, dt, relax, ctx->lin, ctx->blk);
@@ -529,7 +529,7 @@ static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt
     if (e == cudaSuccess) e = block_invert(ctx->L, ctx->blk, ctx->nblk, ctx->P.nf, ctx->blk32, ctx->d_bad);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
     if (ctx->prm.preconditioner != 0) {
-        const double* gbz = ctx->has_lin ? ctx->lin.gb : ctx->gb;
+        const double* gbz = (ctx->has_lin && !ctx->lin.f32) ? ctx->lin.gb : ctx->gb;
         e = mg_setup(ctx->L, ctx->P, ctx->G, z, gbz, t, dt, relax, ctx->mg);
         if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("multigrid setup: ") + cudaGetErrorString(e));
     }

@@ -695,24 +695,24 @@ struct LinShape {
     static __device__ __forceinline__ int ci(int m) { return m < 1 ? m : m - 1; }
 };
 
-template <class Chem, class LT>
-__global__ void __launch_bounds__(128) k_lin_gam(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                 LT* __restrict__ gam) {
+template <class Chem, class S>
+__global__ void __launch_bounds__(128) k_lin_gam(const DevParams p, const Geo g, const S* __restrict__ z,
+                                                 S* __restrict__ gam) {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= p.n_cell) return;
     constexpr int NS = Chem::NS;
     const int ph = g.phase[cell];
     const int s = g.cmap[cell];
-    double es[8][2];
+    S es[8][2];
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-        es[n][0] = es[n][1] = 0.0;
+        es[n][0] = es[n][1] = S(0);
         if (NS == 2 && ph == 1) {
             es[n][0] = ld(z, p, Chem::NL, n, s);
             es[n][1] = ld(z, p, Chem::NL + 1, n, s);
         }
-        double eL = liquid_fraction<Chem, double>(p, ph, es[n]);
-        gam[(int64_t)n * p.n_cell + cell] = LT((ph == 1 && NS == 2 && eL > 0.0) ? 1.5 / eL : 0.0);
+        S eL = liquid_fraction<Chem, S>(p, ph, es[n]);
+        gam[(int64_t)n * p.n_cell + cell] = (ph == 1 && NS == 2 && eL > S(0)) ? S(1.5) / eL : S(0);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d)
@@ -722,22 +722,22 @@ __global__ void __launch_bounds__(128) k_lin_gam(const DevParams p, const Geo g,
             for (int q = 0; q < 4; ++q) {
                 int n0, n1;
                 line_nodes(d, q, n0, n1);
-                const double wn = side > 0 ? ALPHA : BETA, wf = side > 0 ? BETA : ALPHA;
-                double et[2] = {es[n1][0] * wn + es[n0][0] * wf, es[n1][1] * wn + es[n0][1] * wf};
-                double eL = liquid_fraction<Chem, double>(p, ph, et);
-                gam[(int64_t)face_slot(d, side, q) * p.n_cell + cell] = LT((ph == 1 && NS == 2 && eL > 0.0) ? 1.5 / eL : 0.0);
+                const S wn = side > 0 ? S(ALPHA) : S(BETA), wf = side > 0 ? S(BETA) : S(ALPHA);
+                S et[2] = {es[n1][0] * wn + es[n0][0] * wf, es[n1][1] * wn + es[n0][1] * wf};
+                S eL = liquid_fraction<Chem, S>(p, ph, et);
+                gam[(int64_t)face_slot(d, side, q) * p.n_cell + cell] = (ph == 1 && NS == 2 && eL > S(0)) ? S(1.5) / eL : S(0);
             }
 }
 
 // node Jacobians of the structure voxels: one thread per (node, structure voxel), NF seeded
 // evaluations of the node terms.  Elsewhere (pore, separator) the node terms are the storage terms
 // alone and their Jacobian is the diagonal that make_node_diag gives, so nothing is stored there.
-template <class Chem, class LT>
-__global__ void __launch_bounds__(64) k_lin_nodes_build(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                        double t, double dt, int relax, LT* __restrict__ jn) {
+template <class Chem, class S>
+__global__ void __launch_bounds__(64) k_lin_nodes_build(const DevParams p, const Geo g, const S* __restrict__ z,
+                                                        double t, double dt, int relax, S* __restrict__ jn) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_struct * 8) return;
-    typedef Dual<double> T;
+    typedef Dual<S> T;
     constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
     const int n = (int)(b / p.n_struct);
     const int sidx = (int)(b - (int64_t)n * p.n_struct);
@@ -746,7 +746,7 @@ __global__ void __launch_bounds__(64) k_lin_nodes_build(const DevParams p, const
 #pragma unroll
     for (int f = 0; f < NF; ++f) old[f] = 0.0;
     const double tH = smooth_step(t);
-    LT* J = jn + (int64_t)n * NF * NF * p.n_struct + sidx;    // [row*NF + col][structure voxel]
+    S* J = jn + (int64_t)n * NF * NF * p.n_struct + sidx;    // [row*NF + col][structure voxel]
 #pragma unroll 1
     for (int col = 0; col < NF; ++col) {
         T c[NL], es[2], phiL, phiS;
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(64) k_lin_nodes_build(const DevParams p, const
         T R[NF];
         node_terms<Chem, T>(p, 1, c, es, phiL, phiS, old, tH, dt, relax, R);
 #pragma unroll
-        for (int row = 0; row < NF; ++row) J[(int64_t)(row * NF + col) * p.n_struct] = LT(R[row].d);
+        for (int row = 0; row < NF; ++row) J[(int64_t)(row * NF + col) * p.n_struct] = R[row].d;
     }
 }
 
@@ -781,9 +781,9 @@ static NodeDiag make_node_diag(const DevParams& p, double dt, int relax) {
 }
 
 // face data of the +d face of every voxel (and the anode derivatives on the x = nx face)
-template <class Chem, class LT>
-__global__ void __launch_bounds__(128) k_lin_faces_build(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                         const double* __restrict__ gb, int d, LT* __restrict__ face) {
+template <class Chem, class S>
+__global__ void __launch_bounds__(128) k_lin_faces_build(const DevParams p, const Geo g, const S* __restrict__ z,
+                                                         const S* __restrict__ gb, int d, S* __restrict__ face) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 4) return;
     typedef LinShape<Chem> SH;
@@ -794,58 +794,58 @@ __global__ void __launch_bounds__(128) k_lin_faces_build(const DevParams p, cons
     cell_ijk(p, cell, i, j, k);
     int n0, n1;
     line_nodes(d, q, n0, n1);
-    LT* F = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
-    auto put = [&](int kk, double v) { F[(int64_t)kk * p.n_cell] = LT(v); };
+    S* F = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
+    auto put = [&](int kk, S v) { F[(int64_t)kk * p.n_cell] = v; };
     const int coord = d == 0 ? i : d == 1 ? j : k;
     const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
     const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
-    const double pen = p.penalty / p.h, gq = SQ3 / p.h;
+    const S pen = S(p.penalty / p.h), gq = S(SQ3 / p.h);
     if (coord + 1 >= ext) {
         if (d == 0) {   // anode face of the last layer: r_Ano derivatives at the face point
-            double cLi = ALPHA * ld(z, p, 0, n1, cell) + BETA * ld(z, p, 0, n0, cell);
-            double phL = ALPHA * ld(z, p, Chem::PHIL, n1, cell) + BETA * ld(z, p, Chem::PHIL, n0, cell);
-            Dual<double> r1 = anode_rate<Dual<double>>(p, mkd(cLi, 1.0), mkd(phL, 0.0));
-            Dual<double> r2 = anode_rate<Dual<double>>(p, mkd(cLi, 0.0), mkd(phL, 1.0));
+            S cLi = S(ALPHA) * ld(z, p, 0, n1, cell) + S(BETA) * ld(z, p, 0, n0, cell);
+            S phL = S(ALPHA) * ld(z, p, Chem::PHIL, n1, cell) + S(BETA) * ld(z, p, Chem::PHIL, n0, cell);
+            Dual<S> r1 = anode_rate<Dual<S>>(p, mkd(cLi, S(1)), mkd(phL, S(0)));
+            Dual<S> r2 = anode_rate<Dual<S>>(p, mkd(cLi, S(0)), mkd(phL, S(1)));
             put(0, r1.d);
             put(1, r2.d);
         }
         return;
     }
     const int qc = cell + stride;
-    const double gl = gb[(int64_t)face_slot(d, +1, q) * p.n_cell + cell];
-    const double gr = gb[(int64_t)face_slot(d, -1, q) * p.n_cell + qc];
-    double Hg = 0.0, Ha = 0.0, Hb = 0.0;
-    if (gl * gr > 0.0) {
-        double r = 1.0 / (gl + gr);
-        Hg = 2.0 * gl * gr * r;
-        Ha = 2.0 * gr * gr * r * r;
-        Hb = 2.0 * gl * gl * r * r;
+    const S gl = gb[(int64_t)face_slot(d, +1, q) * p.n_cell + cell];
+    const S gr = gb[(int64_t)face_slot(d, -1, q) * p.n_cell + qc];
+    S Hg = S(0), Ha = S(0), Hb = S(0);
+    if (gl * gr > S(0)) {
+        S r = S(1) / (gl + gr);
+        Hg = S(2) * gl * gr * r;
+        Ha = S(2) * gr * gr * r * r;
+        Hb = S(2) * gl * gl * r * r;
     }
     put(0, Hg);
     put(1, Ha);
     put(2, Hb);
     {
-        double P0 = ld(z, p, Chem::PHIL, n0, cell), P1 = ld(z, p, Chem::PHIL, n1, cell);
-        double Q0 = ld(z, p, Chem::PHIL, n0, qc), Q1 = ld(z, p, Chem::PHIL, n1, qc);
-        double jL = (ALPHA * P1 + BETA * P0) - (ALPHA * Q0 + BETA * Q1);
-        double mL = 0.5 * gq * ((P1 - P0) + (Q1 - Q0));
+        S P0 = ld(z, p, Chem::PHIL, n0, cell), P1 = ld(z, p, Chem::PHIL, n1, cell);
+        S Q0 = ld(z, p, Chem::PHIL, n0, qc), Q1 = ld(z, p, Chem::PHIL, n1, qc);
+        S jL = (S(ALPHA) * P1 + S(BETA) * P0) - (S(ALPHA) * Q0 + S(BETA) * Q1);
+        S mL = S(0.5) * gq * ((P1 - P0) + (Q1 - Q0));
         put(3 + NL, jL * pen - mL);
     }
 #pragma unroll
     for (int m = 0; m < NL; ++m) {
-        double C0 = ld(z, p, m, n0, cell), C1 = ld(z, p, m, n1, cell);
-        double Q0 = ld(z, p, m, n0, qc), Q1 = ld(z, p, m, n1, qc);
-        double cl = ALPHA * C1 + BETA * C0, cr = ALPHA * Q0 + BETA * Q1;
-        put(3 + m, (cl - cr) * pen - 0.5 * gq * ((C1 - C0) + (Q1 - Q0)));
+        S C0 = ld(z, p, m, n0, cell), C1 = ld(z, p, m, n1, cell);
+        S Q0 = ld(z, p, m, n0, qc), Q1 = ld(z, p, m, n1, qc);
+        S cl = S(ALPHA) * C1 + S(BETA) * C0, cr = S(ALPHA) * Q0 + S(BETA) * Q1;
+        put(3 + m, (cl - cr) * pen - S(0.5) * gq * ((C1 - C0) + (Q1 - Q0)));
         if (p.zc[m] != 0.0) {
             const int base = 4 + NL + 5 * SH::ci(m);
-            double x = gl * cl, y = gr * cr;
-            double Hm = 0.0, Hx = 0.0, Hy = 0.0;
-            if (x * y > 0.0) {
-                double r = 1.0 / (x + y);
-                Hm = 2.0 * x * y * r;
-                Hx = 2.0 * y * y * r * r;
-                Hy = 2.0 * x * x * r * r;
+            S x = gl * cl, y = gr * cr;
+            S Hm = S(0), Hx = S(0), Hy = S(0);
+            if (x * y > S(0)) {
+                S r = S(1) / (x + y);
+                Hm = S(2) * x * y * r;
+                Hx = S(2) * y * y * r * r;
+                Hy = S(2) * x * x * r * r;
             }
             put(base + 0, Hm);
             put(base + 1, Hx * cl);     // coefficient of d g_l
@@ -1142,10 +1142,10 @@ __global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, cons
 // face points of the three lines through n), the volume term of each of those lines and the two
 // faces at the ends of each line, where node n enters through its trace (weight ALPHA or BETA)
 // and the normal-derivative term (+-sqrt(3)/h).  One thread per (node, voxel); FMAs only.
-template <class Chem, class LT>
-__global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                 const double* __restrict__ gb, const LT* __restrict__ gam,
-                                                 const LT* __restrict__ jn, const LT* __restrict__ face, double dt,
+template <class Chem, class S>
+__global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g, const S* __restrict__ z,
+                                                 const S* __restrict__ gb, const S* __restrict__ gam,
+                                                 const S* __restrict__ jn, const S* __restrict__ face, double dt,
                                                  int relax, const NodeDiag nd, double* __restrict__ blk) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)p.n_cell * 8) return;
@@ -1158,34 +1158,34 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
     const int ph = g.phase[cell];
     const bool st = ph == 1;
     const int an[3] = {n & 1, (n >> 1) & 1, (n >> 2) & 1};
-    const double vol = 3.0 * p.h / 8.0, wf = 0.25 * p.h * p.h, gq = SQ3 / p.h, pen = p.penalty / p.h;
+    const S vol = S(3.0 * p.h / 8.0), wf = S(0.25 * p.h * p.h), gq = S(SQ3 / p.h), pen = S(p.penalty / p.h);
     auto Z = [&](int f, int nn) { return z[p.off[f] + (int64_t)nn * p.flen[f] + cell]; };
-    const LT* J = st ? jn + (int64_t)n * NF * NF * p.n_struct + g.cmap[cell] : nullptr;
-    const double ddc = ph == 2 ? nd.c_sep : nd.c_pore, ddphi = nd.phi;
+    const S* J = st ? jn + (int64_t)n * NF * NF * p.n_struct + g.cmap[cell] : nullptr;
+    const S ddc = S(ph == 2 ? nd.c_sep : nd.c_pore), ddphi = S(nd.phi);
     double* B = blk + b * NF * NF;
 #pragma unroll 1
     for (int c = 0; c < NF; ++c) {
         if (p.is_struct[c] && !st) {
-            for (int r = 0; r < NF; ++r) B[r * NF + c] = r == c ? 1.0 : 0.0;
+            for (int r = 0; r < NF; ++r) B[r * NF + c] = r == c ? S(1.0) : S(0.0);
             continue;
         }
-        double col[NF];
+        S col[NF];
         if (st) {
 #pragma unroll
-            for (int r = 0; r < NF; ++r) col[r] = double(J[(int64_t)(r * NF + c) * p.n_struct]);
+            for (int r = 0; r < NF; ++r) col[r] = S(J[(int64_t)(r * NF + c) * p.n_struct]);
         } else {
 #pragma unroll
-            for (int r = 0; r < NF; ++r) col[r] = r != c ? 0.0 : (r < NL ? ddc : (r == PHIL ? ddphi : 0.0));
+            for (int r = 0; r < NF; ++r) col[r] = r != c ? S(0.0) : (r < NL ? ddc : (r == PHIL ? ddphi : S(0.0)));
         }
         const int dm = c < NL ? c : -1;                      // perturbed species
         const bool dPL = c == PHIL, dPS = c == PHIS;
-        const double dcs = c < NL ? p.wS[c] : 0.0;          // tangent of c_S at node n
-        const double del = (NS == 2 && st && (c == NL || c == NL + 1)) ? -1.0 : 0.0;   // of eps_L
-        auto dg_at = [&](int slot, double w) {
+        const S dcs = c < NL ? S(p.wS[c]) : S(0.0);          // tangent of c_S at node n
+        const S del = (NS == 2 && st && (c == NL || c == NL + 1)) ? -S(1.0) : S(0.0);   // of eps_L
+        auto dg_at = [&](int slot, S w) {
             const int64_t o = (int64_t)slot * p.n_cell + cell;
-            return gb[o] * (double(gam[o]) * del - p.visc * dcs) * w;
+            return gb[o] * (gam[o] * del - S(p.visc) * dcs) * w;
         };
-        const double dgN = dg_at(n, 1.0);
+        const S dgN = dg_at(n, S(1.0));
 #pragma unroll 1
         for (int d = 0; d < 3; ++d) {
             const int u = d == 0 ? an[1] : an[0];
@@ -1194,84 +1194,84 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
             int n0, n1;
             line_nodes(d, q, n0, n1);
             const bool a1 = n == n1;
-            const double sgn = a1 ? 1.0 : -1.0;
+            const S sgn = a1 ? S(1.0) : -S(1.0);
             const int coord = d == 0 ? i : d == 1 ? j : k;
             const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
             const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
             // ---- volume term of the line
             {
-                const double gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
-                const double dgN0 = a1 ? 0.0 : dgN, dgN1 = a1 ? dgN : 0.0;
-                const double P0 = Z(PHIL, n0), P1 = Z(PHIL, n1);
-                const double dPhi = P1 - P0, ddPhi = dPL ? sgn : 0.0;
-                const double gsum = gN0 + gN1, dgsum = dgN0 + dgN1;
-                double fLsum = 0.0;
+                const S gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
+                const S dgN0 = a1 ? S(0.0) : dgN, dgN1 = a1 ? dgN : S(0.0);
+                const S P0 = Z(PHIL, n0), P1 = Z(PHIL, n1);
+                const S dPhi = P1 - P0, ddPhi = dPL ? sgn : S(0.0);
+                const S gsum = gN0 + gN1, dgsum = dgN0 + dgN1;
+                S fLsum = S(0.0);
 #pragma unroll
                 for (int m = 0; m < NL; ++m) {
-                    const double C0 = Z(m, n0), C1 = Z(m, n1);
-                    const double dC0 = (m == dm && !a1) ? 1.0 : 0.0, dC1 = (m == dm && a1) ? 1.0 : 0.0;
-                    const double dc = C1 - C0, ddc = dC1 - dC0;
-                    double fl = relax ? 0.0 : (dgsum * dc + gsum * ddc) * p.D0[m];
-                    if (p.zc[m] != 0.0) {
-                        const double msum = gN0 * C0 + gN1 * C1;
-                        const double dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
-                        if (!relax) fl += (dmsum * dPhi + msum * ddPhi) * p.kappa_m[m];
-                        fLsum += (dgsum * dc + gsum * ddc) * p.Kd[m] + (dmsum * dPhi + msum * ddPhi) * p.Km[m];
+                    const S C0 = Z(m, n0), C1 = Z(m, n1);
+                    const S dC0 = (m == dm && !a1) ? S(1.0) : S(0.0), dC1 = (m == dm && a1) ? S(1.0) : S(0.0);
+                    const S dc = C1 - C0, ddc = dC1 - dC0;
+                    S fl = relax ? S(0.0) : (dgsum * dc + gsum * ddc) * S(p.D0[m]);
+                    if (p.zc[m] != S(0.0)) {
+                        const S msum = gN0 * C0 + gN1 * C1;
+                        const S dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
+                        if (!relax) fl += (dmsum * dPhi + msum * ddPhi) * S(p.kappa_m[m]);
+                        fLsum += (dgsum * dc + gsum * ddc) * S(p.Kd[m]) + (dmsum * dPhi + msum * ddPhi) * S(p.Km[m]);
                     }
                     col[m] += sgn * fl * vol;
                 }
                 col[PHIL] += sgn * fLsum * vol;
-                if (st && dPS) col[PHIS] += 2.0 * p.kappa_s * vol;
+                if (st && dPS) col[PHIS] += S(2.0) * S(p.kappa_s) * vol;
             }
             // ---- the two faces of the line: own voxel left (+d face) or right (-d face)
 #pragma unroll 1
             for (int side = 1; side >= -1; side -= 2) {
                 const bool left = side > 0;
-                const double tw = left ? (a1 ? ALPHA : BETA) : (a1 ? BETA : ALPHA);   // own trace weight
-                const double dBown = left ? tw * pen - 0.5 * gq * sgn : -tw * pen - 0.5 * gq * sgn;
-                const double wrow = left ? wf * tw : -wf * tw;
+                const S tw = left ? (a1 ? S(ALPHA) : S(BETA)) : (a1 ? S(BETA) : S(ALPHA));   // own trace weight
+                const S dBown = left ? tw * pen - S(0.5) * gq * sgn : -tw * pen - S(0.5) * gq * sgn;
+                const S wrow = left ? wf * tw : -wf * tw;
                 const bool inside = left ? coord + 1 < ext : coord > 0;
                 if (!inside) {
                     if (left && d == 0) {   // anode face: r_Ano(c_Li, Phi^L) at the face point
-                        const LT* Fo = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
-                        const double drA = double(Fo[0]) * (dm == 0 ? tw : 0.0) + double(Fo[(int64_t)p.n_cell]) * (dPL ? tw : 0.0);
-                        if (!relax) col[0] += drA * p.kAno * wrow;
-                        col[PHIL] += drA * p.F * p.kAno * wrow;
+                        const S* Fo = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
+                        const S drA = Fo[0] * (dm == 0 ? tw : S(0.0)) + Fo[(int64_t)p.n_cell] * (dPL ? tw : S(0.0));
+                        if (!relax) col[0] += drA * S(p.kAno) * wrow;
+                        col[PHIL] += drA * S(p.F) * S(p.kAno) * wrow;
                     }
                     continue;
                 }
                 const int fc = left ? cell : cell - stride;        // voxel owning the face data
                 const int oc = left ? cell + stride : cell - stride;   // the other voxel
-                const LT* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + fc;
-                auto F = [&](int kk) { return double(Fd[(int64_t)kk * p.n_cell]); };
-                const double dgo = dg_at(face_slot(d, side, q), tw);   // own g at this face point
-                const double dHg = (left ? F(1) : F(2)) * dgo;
-                const double Hg = F(0), BL = F(3 + NL);
-                const double dBL = dPL ? dBown : 0.0;
-                double fL = 0.0;
+                const S* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + fc;
+                auto F = [&](int kk) { return Fd[(int64_t)kk * p.n_cell]; };
+                const S dgo = dg_at(face_slot(d, side, q), tw);   // own g at this face point
+                const S dHg = (left ? F(1) : F(2)) * dgo;
+                const S Hg = F(0), BL = F(3 + NL);
+                const S dBL = dPL ? dBown : S(0.0);
+                S fL = S(0.0);
 #pragma unroll
                 for (int m = 0; m < NL; ++m) {
-                    const double dB = m == dm ? dBown : 0.0;
-                    const double dco = m == dm ? tw : 0.0;
-                    const double dterm = dHg * F(3 + m) + Hg * dB;
-                    double f = relax ? 0.0 : dterm * p.D0[m];
-                    if (p.zc[m] != 0.0) {
+                    const S dB = m == dm ? dBown : S(0.0);
+                    const S dco = m == dm ? tw : S(0.0);
+                    const S dterm = dHg * F(3 + m) + Hg * dB;
+                    S f = relax ? S(0.0) : dterm * S(p.D0[m]);
+                    if (p.zc[m] != S(0.0)) {
                         const int base = 4 + NL + 5 * SH::ci(m);
-                        const double dHm = left ? F(base + 1) * dgo + F(base + 2) * dco : F(base + 3) * dgo + F(base + 4) * dco;
-                        const double mterm = dHm * BL + F(base) * dBL;
-                        if (!relax) f += mterm * p.kappa_m[m];
-                        fL += dterm * p.Kd[m] + mterm * p.Km[m];
+                        const S dHm = left ? F(base + 1) * dgo + F(base + 2) * dco : F(base + 3) * dgo + F(base + 4) * dco;
+                        const S mterm = dHm * BL + F(base) * dBL;
+                        if (!relax) f += mterm * S(p.kappa_m[m]);
+                        fL += dterm * S(p.Kd[m]) + mterm * S(p.Km[m]);
                     }
                     col[m] += f * wrow;
                 }
                 col[PHIL] += fL * wrow;
-                if (st && dPS && g.phase[oc] == 1) col[PHIS] += dBown * p.kappa_s * wrow;
+                if (st && dPS && g.phase[oc] == 1) col[PHIS] += dBown * S(p.kappa_s) * wrow;
             }
         }
 #pragma unroll
         for (int r = 0; r < NF; ++r) {
-            double o = col[r] * dt * p.rscale[r];
-            if (p.is_struct[r] && !st) o = r == c ? 1.0 : 0.0;
+            double o = double(col[r]) * dt * p.rscale[r];
+            if (p.is_struct[r] && !st) o = r == c ? S(1.0) : S(0.0);
             B[r * NF + c] = o;
         }
     }
@@ -1290,29 +1290,30 @@ int64_t dg1_lin_sizes(const DevParams& p, int64_t* jn, int64_t* gam, int64_t* fa
 int64_t dg1_lin_flux_len(const DevParams& p) { return (int64_t)4 * (p.nl + 2) * p.n_cell;
 }
 
-template <class Chem, class LT>
-static cudaError_t linearize_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t,
-                                  double dt, int relax, LT* jn, LT* gam, LT* face, double* gb) {
-    k_dg1_g<Chem, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
-    k_lin_gam<Chem, LT><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, gam);
+template <class Chem, class S>
+static cudaError_t linearize_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, double t,
+                                  double dt, int relax, S* jn, S* gam, S* face, S* gb) {
+    k_dg1_g<Chem, S, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
+    k_lin_gam<Chem, S><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, gam);
     if (p.n_struct > 0)
-        k_lin_nodes_build<Chem, LT><<<nblocks((int64_t)p.n_struct * 8, 64), 64, 0, L.st>>>(p, g, z, t, dt, relax, jn);
+        k_lin_nodes_build<Chem, S><<<nblocks((int64_t)p.n_struct * 8, 64), 64, 0, L.st>>>(p, g, z, t, dt, relax, jn);
     for (int d = 0; d < 3; ++d)
-        k_lin_faces_build<Chem, LT><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, gb, d, face);
+        k_lin_faces_build<Chem, S><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, gb, d, face);
     *L.counter += 6;
     return cudaGetLastError();
 }
 
-// Linearise at z: FP64 arithmetic; stored in FP64, or in FP32 (lin.f32) for the FP32 product of
-// the mixed-precision path (the FP64 transport factors stay in lin.gb for the preconditioner).
+// Linearise at z: in FP64, or (lin.f32, the mixed-precision path, whose products and blocks are FP32)
+// in FP32 from an FP32 copy of z.
 cudaError_t dg1_linearize(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double t, double dt,
                           int relax, const DG1Lin& lin) {
-    cudaError_t e;
     if (lin.f32) {
-        e = p.nf == 10 ? linearize_impl<ChemTO, float>(L, p, g, z, t, dt, relax, lin.jn32, lin.gam32, lin.face32, lin.gb)
-                       : linearize_impl<ChemR3, float>(L, p, g, z, t, dt, relax, lin.jn32, lin.gam32, lin.face32, lin.gb);
-        if (e == cudaSuccess) e = to_f32(L, lin.gb32, lin.gb, (int64_t)NG * p.n_cell);
-        return e;
+        cudaError_t e = to_f32(L, lin.z32, z, lin.ndof);
+        if (e != cudaSuccess) return e;
+        return p.nf == 10 ? linearize_impl<ChemTO, float>(L, p, g, lin.z32, t, dt, relax, lin.jn32, lin.gam32, lin.face32,
+                                                          lin.gb32)
+                          : linearize_impl<ChemR3, float>(L, p, g, lin.z32, t, dt, relax, lin.jn32, lin.gam32, lin.face32,
+                                                          lin.gb32);
     }
     return p.nf == 10 ? linearize_impl<ChemTO, double>(L, p, g, z, t, dt, relax, lin.jn, lin.gam, lin.face, lin.gb)
                       : linearize_impl<ChemR3, double>(L, p, g, z, t, dt, relax, lin.jn, lin.gam, lin.face, lin.gb);
@@ -1360,11 +1361,13 @@ cudaError_t dg1_lin_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g,
                            const DG1Lin& lin, double* blk) {
     const int nb = nblocks((int64_t)p.n_cell * 8, 128);
     const NodeDiag nd = make_node_diag(p, dt, relax);
-    if (lin.f32) {
+    if (lin.f32) {   // FP32 arithmetic on the FP32 linearisation (the blocks only precondition an FP32 loop)
         if (p.nf == 10)
-            k_lin_blk<ChemTO, float><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam32, lin.jn32, lin.face32, dt, relax, nd, blk);
+            k_lin_blk<ChemTO, float><<<nb, 128, 0, L.st>>>(p, g, lin.z32, lin.gb32, lin.gam32, lin.jn32, lin.face32, dt,
+                                                           relax, nd, blk);
         else
-            k_lin_blk<ChemR3, float><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam32, lin.jn32, lin.face32, dt, relax, nd, blk);
+            k_lin_blk<ChemR3, float><<<nb, 128, 0, L.st>>>(p, g, lin.z32, lin.gb32, lin.gam32, lin.jn32, lin.face32, dt,
+                                                           relax, nd, blk);
     } else {
         if (p.nf == 10)
             k_lin_blk<ChemTO, double><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);

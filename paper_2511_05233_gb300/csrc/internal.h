@@ -67,10 +67,12 @@ struct DG1Lin {
     double* jn = nullptr;   // [8][NF*NF][n_struct] node Jacobians of the structure voxels
     double* gam = nullptr;  // [32][n_cell] 3/(2 eps_L) per transport-factor slot
     double* face = nullptr; // [12][NFD][n_cell] face data of the + faces
-    double* gb = nullptr;   // [32][n_cell] transport factors at the linearisation point (FP64 in both modes)
+    double* gb = nullptr;   // [32][n_cell] transport factors at the linearisation point (FP64 mode)
     double* gbd = nullptr;  // [32][n_cell] their tangents (apply scratch)
     double* flux = nullptr; // [4][NL+2][n_cell] face-flux tangents of one direction (apply scratch)
     float *jn32 = nullptr, *gam32 = nullptr, *face32 = nullptr, *gb32 = nullptr, *gbd32 = nullptr, *flux32 = nullptr;
+    float* z32 = nullptr;   // FP32 copy of the linearisation point (mixed precision)
+    int64_t ndof = 0;
 };
 int64_t dg1_lin_flux_len(const DevParams& p);
 // vertex-based slope limiter of the liquid species of a DG1 state (scratch: NL x n_cell doubles)
