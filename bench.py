@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--reorth", type=int, default=2, choices=[0, 1, 2],
                     help="GMRES Gram-Schmidt: 2 one pass (default), 0 second pass when needed, 1 always")
     ap.add_argument("--mg-cycles", type=int, default=1)
+    ap.add_argument("--eta-min", type=float, default=None, help="floor of the Eisenstat-Walker forcing term")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
@@ -180,6 +181,7 @@ def config_dict(a):
                         f"one implicit Euler step dt={WORKLOAD['dt']} s at {WORKLOAD['f_C']}C, Newton-GMRES(30) rtol 1e-10",
             "grid": a.n, "order": a.order, "chemistry": a.chem, "precision": a.precision, "preconditioner": a.precond,
             "gram_schmidt": ["cgs+dgks", "cgs2", "cgs"][a.reorth], "mg_cycles": a.mg_cycles,
+            **({"eta_min": a.eta_min} if a.eta_min is not None else {}),
             "l2": "inputs larger than L2 (every state vector > 129 MB)"}
 
 
@@ -207,7 +209,8 @@ def main():
     prm = dgls.default_params(chem, a.order, f_C=WORKLOAD["f_C"], eps_struct=1 - WORKLOAD["porosity"],
                               precision=dgls.MIXED if a.precision == "mixed" else dgls.FP64,
                               preconditioner={"bj": 0, "cpr": 1, "add": 2}[a.precond],
-                              precond_every=a.precond_every, reorth=a.reorth, mg_cycles=a.mg_cycles)
+                              precond_every=a.precond_every, reorth=a.reorth, mg_cycles=a.mg_cycles,
+                              **({"eta_min": a.eta_min} if a.eta_min is not None else {}))
     stream = torch.cuda.current_stream()
     ctx = dgls.Context(phase, WORKLOAD["h"], prm, stream)
     N = ctx.n_dof
@@ -317,7 +320,8 @@ def main():
         z64 = z.clone()
         prm32 = dgls.default_params(chem, a.order, f_C=WORKLOAD["f_C"], eps_struct=1 - WORKLOAD["porosity"],
                                     precision=dgls.MIXED, preconditioner={"bj": 0, "cpr": 1, "add": 2}[a.precond],
-                                    precond_every=a.precond_every, reorth=a.reorth, mg_cycles=a.mg_cycles)
+                                    precond_every=a.precond_every, reorth=a.reorth, mg_cycles=a.mg_cycles,
+                              **({"eta_min": a.eta_min} if a.eta_min is not None else {}))
         ctx32 = dgls.Context(phase, WORKLOAD["h"], prm32, stream)
         z32 = ctx32.new_state()
         for _ in range(max(1, min(a.warmup, 2))):
