@@ -1142,30 +1142,25 @@ __global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, cons
 // face points of the three lines through n), the volume term of each of those lines and the two
 // faces at the ends of each line, where node n enters through its trace (weight ALPHA or BETA)
 // and the normal-derivative term (+-sqrt(3)/h).  One thread per (node, voxel); FMAs only.
-template <class Chem, class S, bool ST>   // ST: structure voxels (compact list); else the others
+template <class Chem, class S>
 __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g, const S* __restrict__ z,
                                                  const S* __restrict__ gb, const S* __restrict__ gam,
                                                  const S* __restrict__ jn, const S* __restrict__ face, double dt,
                                                  int relax, const NodeDiag nd, double* __restrict__ blk) {
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nthr = (int64_t)(ST ? p.n_struct : p.n_cell) * 8;
-    if (tid >= nthr) return;
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 8) return;
     typedef LinShape<Chem> SH;
     constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
-    const int nvox = ST ? p.n_struct : p.n_cell;
-    const int n = (int)(tid / nvox);
-    const int vi = (int)(tid - (int64_t)n * nvox);
-    const int cell = ST ? g.sidx[vi] : vi;
-    const int ph = g.phase[cell];
-    if (!ST && ph == 1) return;
-    const int64_t b = (int64_t)n * p.n_cell + cell;     // block index (node, voxel)
+    const int n = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)n * p.n_cell);
     int i, j, k;
     cell_ijk(p, cell, i, j, k);
-    constexpr bool st = ST;
+    const int ph = g.phase[cell];
+    const bool st = ph == 1;
     const int an[3] = {n & 1, (n >> 1) & 1, (n >> 2) & 1};
     const S vol = S(3.0 * p.h / 8.0), wf = S(0.25 * p.h * p.h), gq = S(SQ3 / p.h), pen = S(p.penalty / p.h);
     auto Z = [&](int f, int nn) { return z[p.off[f] + (int64_t)nn * p.flen[f] + cell]; };
-    const S* J = st ? jn + (int64_t)n * NF * NF * p.n_struct + (ST ? vi : 0) : nullptr;
+    const S* J = st ? jn + (int64_t)n * NF * NF * p.n_struct + g.cmap[cell] : nullptr;
     const S ddc = S(ph == 2 ? nd.c_sep : nd.c_pore), ddphi = S(nd.phi);
     double* B = blk + b * NF * NF;
 #pragma unroll 1
@@ -1362,27 +1357,24 @@ cudaError_t dg1_lin_apply<float>(const LaunchCtx& L, const DevParams& p, const G
                                                       lin.face32, lin.gb32, lin.gbd32, lin.flux32);
 }
 
-template <class Chem, class S>
-static void lin_blocks_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* gb, const S* gam,
-                            const S* jn, const S* face, double dt, int relax, const NodeDiag& nd, double* blk) {
-    if (p.n_struct > 0)
-        k_lin_blk<Chem, S, true><<<nblocks((int64_t)p.n_struct * 8, 128), 128, 0, L.st>>>(p, g, z, gb, gam, jn, face, dt,
-                                                                                           relax, nd, blk);
-    k_lin_blk<Chem, S, false><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, g, z, gb, gam, jn, face, dt,
-                                                                                      relax, nd, blk);
-    *L.counter += 2;
-}
-
 cudaError_t dg1_lin_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double dt, int relax,
                            const DG1Lin& lin, double* blk) {
+    const int nb = nblocks((int64_t)p.n_cell * 8, 128);
     const NodeDiag nd = make_node_diag(p, dt, relax);
     if (lin.f32) {   // FP32 arithmetic on the FP32 linearisation (the blocks only precondition an FP32 loop)
-        if (p.nf == 10) lin_blocks_impl<ChemTO, float>(L, p, g, lin.z32, lin.gb32, lin.gam32, lin.jn32, lin.face32, dt, relax, nd, blk);
-        else lin_blocks_impl<ChemR3, float>(L, p, g, lin.z32, lin.gb32, lin.gam32, lin.jn32, lin.face32, dt, relax, nd, blk);
+        if (p.nf == 10)
+            k_lin_blk<ChemTO, float><<<nb, 128, 0, L.st>>>(p, g, lin.z32, lin.gb32, lin.gam32, lin.jn32, lin.face32, dt,
+                                                           relax, nd, blk);
+        else
+            k_lin_blk<ChemR3, float><<<nb, 128, 0, L.st>>>(p, g, lin.z32, lin.gb32, lin.gam32, lin.jn32, lin.face32, dt,
+                                                           relax, nd, blk);
     } else {
-        if (p.nf == 10) lin_blocks_impl<ChemTO, double>(L, p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);
-        else lin_blocks_impl<ChemR3, double>(L, p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);
+        if (p.nf == 10)
+            k_lin_blk<ChemTO, double><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);
+        else
+            k_lin_blk<ChemR3, double><<<nb, 128, 0, L.st>>>(p, g, z, lin.gb, lin.gam, lin.jn, lin.face, dt, relax, nd, blk);
     }
+    *L.counter += 1;
     return cudaGetLastError();
 }
 
