@@ -65,28 +65,28 @@ cudaError_t block_invert(const LaunchCtx& L, double* blk, int64_t nblk, int nf, 
 }
 
 // out = B^{-1} v per block; DG0: one block per voxel, DG1: one block per (node, voxel).
-// u = B^{-1} v per node block.  Structure voxels (all NF fields) and the others (liquid fields only:
-// their blocks are the identity on the solid and Phi^S entries) run in separate kernels, so that no
-// warp mixes the NF x NF product with the smaller one.
 template <class S, class BT, int NF>
-__global__ void __launch_bounds__(128) k_block_apply_struct(const DevParams p, const Geo g, const BT* __restrict__ blk,
-                                                            const S* __restrict__ v, S* __restrict__ out) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_block_apply(const DevParams p, const Geo g, const BT* __restrict__ blk,
+                                                     const S* __restrict__ v, S* __restrict__ out) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int nn = p.order == 1 ? 8 : 1;
-    if (t >= (int64_t)p.n_struct * nn) return;
-    const int node = (int)(t / p.n_struct);
-    const int sidx = (int)(t - (int64_t)node * p.n_struct);
-    const int cell = g.sidx[sidx];
+    if (b >= (int64_t)p.n_cell * nn) return;
+    int node = (int)(b / p.n_cell);
+    int cell = (int)(b - (int64_t)node * p.n_cell);
+    int ph = g.phase[cell];
+    int sidx = g.cmap[cell];
     int64_t idx[NF];
     S x[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        idx[f] = p.off[f] + (int64_t)node * p.flen[f] + (p.is_struct[f] ? sidx : cell);
-        x[f] = v[idx[f]];
+        if (!p.is_struct[f]) idx[f] = p.off[f] + (int64_t)node * p.flen[f] + cell;
+        else idx[f] = (ph == 1) ? p.off[f] + (int64_t)node * p.flen[f] + sidx : -1;
+        x[f] = idx[f] >= 0 ? v[idx[f]] : S(0);
     }
-    const BT* B = blk + ((int64_t)node * p.n_cell + cell) * NF * NF;
+    const BT* B = blk + b * NF * NF;
 #pragma unroll
     for (int r = 0; r < NF; ++r) {
+        if (idx[r] < 0) continue;
         S acc = S(0);
 #pragma unroll
         for (int c = 0; c < NF; ++c) acc += S(B[r * NF + c]) * x[c];
@@ -94,56 +94,14 @@ __global__ void __launch_bounds__(128) k_block_apply_struct(const DevParams p, c
     }
 }
 
-// fields that live on structure voxels only, at compile time: eps_S8, eps_Li2S, Phi^S of the Tradeoff
-// layout (NF = 10), Phi^S of the three-species layout (NF = 5)
-template <int NF>
-__host__ __device__ constexpr bool struct_field(int f) {
-    return NF == 10 ? (f == 6 || f == 7 || f == 9) : (f == 4);
-}
-
-template <class S, class BT, int NF>
-__global__ void __launch_bounds__(128) k_block_apply_liquid(const DevParams p, const Geo g, const BT* __restrict__ blk,
-                                                            const S* __restrict__ v, S* __restrict__ out) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int nn = p.order == 1 ? 8 : 1;
-    if (b >= (int64_t)p.n_cell * nn) return;
-    const int node = (int)(b / p.n_cell);
-    const int cell = (int)(b - (int64_t)node * p.n_cell);
-    if (g.phase[cell] == 1) return;
-    int64_t idx[NF];
-    S x[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        idx[f] = p.off[f] + (int64_t)node * p.flen[f] + cell;
-        x[f] = struct_field<NF>(f) ? S(0) : v[idx[f]];
-    }
-    const BT* B = blk + b * NF * NF;
-#pragma unroll
-    for (int r = 0; r < NF; ++r) {
-        if (struct_field<NF>(r)) continue;
-        S acc = S(0);
-#pragma unroll
-        for (int c = 0; c < NF; ++c)
-            if (!struct_field<NF>(c)) acc += S(B[r * NF + c]) * x[c];
-        out[idx[r]] = acc;
-    }
-}
-
 template <class S>
 cudaError_t block_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const void* blk, const S* v, S* out) {
-    const int nn = p.order == 1 ? 8 : 1;
-    const int nbl = nblocks((int64_t)p.n_cell * nn, 128), nbs = nblocks((int64_t)p.n_struct * nn, 128);
+    int64_t n = (int64_t)p.n_cell * (p.order == 1 ? 8 : 1);
+    int nb = nblocks(n, 128);
     typedef typename std::conditional<std::is_same<S, float>::value, float, double>::type BT;
-    for (int f = 0; f < p.nf; ++f)
-        if ((p.nf == 10 ? struct_field<10>(f) : struct_field<5>(f)) != (p.is_struct[f] != 0)) return cudaErrorInvalidValue;
-    if (p.nf == 10) {
-        if (p.n_struct > 0) k_block_apply_struct<S, BT, 10><<<nbs, 128, 0, L.st>>>(p, g, (const BT*)blk, v, out);
-        k_block_apply_liquid<S, BT, 10><<<nbl, 128, 0, L.st>>>(p, g, (const BT*)blk, v, out);
-    } else {
-        if (p.n_struct > 0) k_block_apply_struct<S, BT, 5><<<nbs, 128, 0, L.st>>>(p, g, (const BT*)blk, v, out);
-        k_block_apply_liquid<S, BT, 5><<<nbl, 128, 0, L.st>>>(p, g, (const BT*)blk, v, out);
-    }
-    *L.counter += 2;
+    if (p.nf == 10) k_block_apply<S, BT, 10><<<nb, 128, 0, L.st>>>(p, g, (const BT*)blk, v, out);
+    else k_block_apply<S, BT, 5><<<nb, 128, 0, L.st>>>(p, g, (const BT*)blk, v, out);
+    *L.counter += 1;
     return cudaGetLastError();
 }
 template cudaError_t block_apply<double>(const LaunchCtx&, const DevParams&, const Geo&, const void*, const double*, double*);
