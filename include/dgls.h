@@ -74,7 +74,9 @@ typedef struct {
     double newton_atol;        /* RMS floor of the scaled residual (1e-13, rounding level) */
     int32_t newton_max_it;     /* 25 */
     double eta_max;            /* Eisenstat-Walker forcing-term cap (1e-2) */
-    double eta_min;            /* forcing-term floor */
+    double eta_min;            /* forcing-term floor (1e-3): keeps the middle Newton iterations from
+                                  over-solving; the last iteration's tolerance still follows from
+                                  newton_rtol, and convergence is tested on the true residual */
     int64_t hbm_budget_bytes;  /* workspace cap checked in dg_setup (0: no cap) */
     int32_t preconditioner;    /* 0: cell-block Jacobi; 1: two-stage (CPR): multigrid on the potential
                                   block, then block Jacobi on the remainder; 2: the additive form of the

@@ -183,7 +183,7 @@ extern "C" dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t 
     p->reorth = 2;
     p->newton_max_it = 25;
     p->eta_max = 1e-2;
-    p->eta_min = 1e-12;
+    p->eta_min = 1e-3;
     p->hbm_budget_bytes = 0;
     return DG_OK;
 }
