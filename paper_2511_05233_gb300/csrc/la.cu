@@ -13,77 +13,53 @@ namespace dgls {
 static inline int nblocks(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
 // ------------------------------------------------------------------ block Jacobi
-// Gauss-Jordan inversion with partial pivoting of nf x nf blocks, 16 lanes per block (two blocks
-// per warp): the augmented matrix [B | I] sits in shared memory, lane r owns row r.  Per column the
-// half-warp finds the pivot (largest magnitude, smallest row on ties), swaps, scales and eliminates;
-// every element sees the same sequence of updates as in a one-thread loop.  A singular block is
-// counted in *bad and replaced by the identity.  All synchronisation is within the half-warp, whose
-// lanes run the same loop to the end (a singular block keeps looping with its updates switched off).
-constexpr int INV_BLOCKS_PER_CTA = 8;   // 128 threads
-
-__global__ void __launch_bounds__(128) k_block_invert(double* __restrict__ blk, int64_t nblk, int nf,
-                                                      float* __restrict__ blk32, int* __restrict__ bad) {
-    __shared__ double A[INV_BLOCKS_PER_CTA][DG_MAXF][2 * DG_MAXF];
-    const int half = threadIdx.x >> 4, lane = threadIdx.x & 15;
-    const unsigned hmask = 0xFFFFu << (16 * ((threadIdx.x >> 4) & 1));
-    const int64_t b = (int64_t)blockIdx.x * INV_BLOCKS_PER_CTA + half;
-    if (b >= nblk) return;                       // the whole half-warp leaves together
-    double(*M)[2 * DG_MAXF] = A[half];
+// Gauss-Jordan inversion with partial pivoting of one nf x nf block per thread.
+__global__ void k_block_invert(double* __restrict__ blk, int64_t nblk, int nf, float* __restrict__ blk32,
+                               int* __restrict__ bad) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblk) return;
+    double a[DG_MAXF][DG_MAXF], inv[DG_MAXF][DG_MAXF];
     double* B = blk + b * nf * nf;
-    for (int e = lane; e < nf * nf; e += 16) {
-        const int r = e / nf, c = e - r * nf;
-        M[r][c] = B[e];
-    }
-    for (int e = lane; e < nf * nf; e += 16) {
-        const int r = e / nf, c = e - r * nf;
-        M[r][nf + c] = (r == c) ? 1.0 : 0.0;
-    }
-    __syncwarp(hmask);
+    for (int r = 0; r < nf; ++r)
+        for (int c = 0; c < nf; ++c) {
+            a[r][c] = B[r * nf + c];
+            inv[r][c] = (r == c) ? 1.0 : 0.0;
+        }
     bool singular = false;
     for (int col = 0; col < nf; ++col) {
-        // pivot: max |M[r][col]| over r >= col, smallest r on ties
-        double v = (lane >= col && lane < nf) ? fabs(M[lane][col]) : -1.0;
-        int idx = lane;
-#pragma unroll
-        for (int off = 8; off > 0; off >>= 1) {
-            const double ov = __shfl_xor_sync(hmask, v, off, 16);
-            const int oi = __shfl_xor_sync(hmask, idx, off, 16);
-            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-        }
-        if (!(v > 0.0) || !isfinite(v)) singular = true;
-        const int piv = idx;
-        if (!singular && piv != col)
-            for (int c = lane; c < 2 * nf; c += 16) {
-                const double t = M[col][c];
-                M[col][c] = M[piv][c];
-                M[piv][c] = t;
+        int piv = col;
+        double best = fabs(a[col][col]);
+        for (int r = col + 1; r < nf; ++r)
+            if (fabs(a[r][col]) > best) { best = fabs(a[r][col]); piv = r; }
+        if (!(best > 0.0) || !isfinite(best)) { singular = true; break; }
+        if (piv != col)
+            for (int c = 0; c < nf; ++c) {
+                double t = a[col][c]; a[col][c] = a[piv][c]; a[piv][c] = t;
+                t = inv[col][c]; inv[col][c] = inv[piv][c]; inv[piv][c] = t;
             }
-        __syncwarp(hmask);
-        const double d = singular ? 1.0 : 1.0 / M[col][col];
-        __syncwarp(hmask);
-        if (!singular)
-            for (int c = lane; c < 2 * nf; c += 16) M[col][c] *= d;
-        __syncwarp(hmask);
-        if (!singular && lane < nf && lane != col) {
-            const double f = M[lane][col];
-            if (f != 0.0)
-                for (int c = 0; c < 2 * nf; ++c) M[lane][c] -= f * M[col][c];
+        double d = 1.0 / a[col][col];
+        for (int c = 0; c < nf; ++c) { a[col][c] *= d; inv[col][c] *= d; }
+        for (int r = 0; r < nf; ++r) {
+            if (r == col) continue;
+            double f = a[r][col];
+            if (f == 0.0) continue;
+            for (int c = 0; c < nf; ++c) { a[r][c] -= f * a[col][c]; inv[r][c] -= f * inv[col][c]; }
         }
-        __syncwarp(hmask);
     }
-    if (singular && lane == 0) atomicAdd(bad, 1);
-    for (int e = lane; e < nf * nf; e += 16) {
-        const int r = e / nf, c = e - r * nf;
-        const double x = singular ? ((r == c) ? 1.0 : 0.0) : M[r][nf + c];
-        B[e] = x;
-        if (blk32) blk32[(int64_t)e * nblk + b] = (float)x;   // FP32 copy entry-major: coalesced apply
+    if (singular) {
+        atomicAdd(bad, 1);
+        for (int r = 0; r < nf; ++r)
+            for (int c = 0; c < nf; ++c) inv[r][c] = (r == c) ? 1.0 : 0.0;
     }
+    for (int r = 0; r < nf; ++r)
+        for (int c = 0; c < nf; ++c) {
+            B[r * nf + c] = inv[r][c];
+            if (blk32) blk32[b * nf * nf + r * nf + c] = (float)inv[r][c];
+        }
 }
 
 cudaError_t block_invert(const LaunchCtx& L, double* blk, int64_t nblk, int nf, float* blk32, int* bad) {
-    if (nf > DG_MAXF || nf > 16) return cudaErrorInvalidValue;
-    k_block_invert<<<(int)((nblk + INV_BLOCKS_PER_CTA - 1) / INV_BLOCKS_PER_CTA), 128, 0, L.st>>>(blk, nblk, nf, blk32,
-                                                                                                    bad);
+    k_block_invert<<<nblocks(nblk, 64), 64, 0, L.st>>>(blk, nblk, nf, blk32, bad);
     *L.counter += 1;
     return cudaGetLastError();
 }
@@ -107,17 +83,13 @@ __global__ void __launch_bounds__(128) k_block_apply(const DevParams p, const Ge
         else idx[f] = (ph == 1) ? p.off[f] + (int64_t)node * p.flen[f] + sidx : -1;
         x[f] = idx[f] >= 0 ? v[idx[f]] : S(0);
     }
-    // FP64 blocks: NF x NF consecutive per block; FP32 blocks: entry-major, [r * NF + c][block]
-    const bool soa = std::is_same<BT, float>::value;
-    const int64_t nblk = (int64_t)p.n_cell * nn;
-    const BT* B = soa ? blk + b : blk + b * NF * NF;
-    const int64_t es = soa ? nblk : 1;
+    const BT* B = blk + b * NF * NF;
 #pragma unroll
     for (int r = 0; r < NF; ++r) {
         if (idx[r] < 0) continue;
         S acc = S(0);
 #pragma unroll
-        for (int c = 0; c < NF; ++c) acc += S(B[(int64_t)(r * NF + c) * es]) * x[c];
+        for (int c = 0; c < NF; ++c) acc += S(B[r * NF + c]) * x[c];
         out[idx[r]] = acc;
     }
 }
