@@ -388,7 +388,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         AL(ctx->z32, N);
         AL(ctx->gb32, scratch);
         AL(ctx->gbd32, scratch);
-        AL(ctx->blk32, ctx->nblk * P.nf * P.nf);
+        AL(ctx->blk32, ctx->nblk * P.nf * P.nf);   // entry-major ([r * nf + c][block]), see block_invert
     } else {
         double *V, *w, *u, *x, *y1, *t2;
         AL(V, (int64_t)(m + 1) * N); AL(w, N); AL(u, N); AL(x, N); AL(y1, N); AL(t2, N);

@@ -54,7 +54,7 @@ __global__ void k_block_invert(double* __restrict__ blk, int64_t nblk, int nf, f
     for (int r = 0; r < nf; ++r)
         for (int c = 0; c < nf; ++c) {
             B[r * nf + c] = inv[r][c];
-            if (blk32) blk32[b * nf * nf + r * nf + c] = (float)inv[r][c];
+            if (blk32) blk32[(int64_t)(r * nf + c) * nblk + b] = (float)inv[r][c];   // entry-major: coalesced apply
         }
 }
 
@@ -83,13 +83,17 @@ __global__ void __launch_bounds__(128) k_block_apply(const DevParams p, const Ge
         else idx[f] = (ph == 1) ? p.off[f] + (int64_t)node * p.flen[f] + sidx : -1;
         x[f] = idx[f] >= 0 ? v[idx[f]] : S(0);
     }
-    const BT* B = blk + b * NF * NF;
+    // FP64 blocks: NF x NF consecutive per block; FP32 blocks: entry-major, [r * NF + c][block]
+    const bool soa = std::is_same<BT, float>::value;
+    const int64_t nblk = (int64_t)p.n_cell * nn;
+    const BT* B = soa ? blk + b : blk + b * NF * NF;
+    const int64_t es = soa ? nblk : 1;
 #pragma unroll
     for (int r = 0; r < NF; ++r) {
         if (idx[r] < 0) continue;
         S acc = S(0);
 #pragma unroll
-        for (int c = 0; c < NF; ++c) acc += S(B[r * NF + c]) * x[c];
+        for (int c = 0; c < NF; ++c) acc += S(B[(int64_t)(r * NF + c) * es]) * x[c];
         out[idx[r]] = acc;
     }
 }
