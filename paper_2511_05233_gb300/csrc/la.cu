@@ -13,48 +13,53 @@ namespace dgls {
 static inline int nblocks(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
 // ------------------------------------------------------------------ block Jacobi
-// Gauss-Jordan inversion with partial pivoting of one nf x nf block per thread.
+// Gauss-Jordan inversion with partial pivoting of one nf x nf block per thread, in place: at step k
+// the pivot row is swapped in, column k is replaced by the inverse's column (pivot 1 / a_kk, the
+// others -a_ik / a_kk) while the rows are eliminated, and the row swaps are undone at the end by the
+// same column swaps in reverse order.  Half the work and local memory of the augmented [A | I] form.
 __global__ void k_block_invert(double* __restrict__ blk, int64_t nblk, int nf, float* __restrict__ blk32,
                                int* __restrict__ bad) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblk) return;
-    double a[DG_MAXF][DG_MAXF], inv[DG_MAXF][DG_MAXF];
+    double a[DG_MAXF][DG_MAXF];
+    int rec[DG_MAXF];
     double* B = blk + b * nf * nf;
     for (int r = 0; r < nf; ++r)
-        for (int c = 0; c < nf; ++c) {
-            a[r][c] = B[r * nf + c];
-            inv[r][c] = (r == c) ? 1.0 : 0.0;
-        }
+        for (int c = 0; c < nf; ++c) a[r][c] = B[r * nf + c];
     bool singular = false;
-    for (int col = 0; col < nf; ++col) {
-        int piv = col;
-        double best = fabs(a[col][col]);
-        for (int r = col + 1; r < nf; ++r)
-            if (fabs(a[r][col]) > best) { best = fabs(a[r][col]); piv = r; }
+    for (int k = 0; k < nf; ++k) {
+        int piv = k;
+        double best = fabs(a[k][k]);
+        for (int r = k + 1; r < nf; ++r)
+            if (fabs(a[r][k]) > best) { best = fabs(a[r][k]); piv = r; }
         if (!(best > 0.0) || !isfinite(best)) { singular = true; break; }
-        if (piv != col)
-            for (int c = 0; c < nf; ++c) {
-                double t = a[col][c]; a[col][c] = a[piv][c]; a[piv][c] = t;
-                t = inv[col][c]; inv[col][c] = inv[piv][c]; inv[piv][c] = t;
-            }
-        double d = 1.0 / a[col][col];
-        for (int c = 0; c < nf; ++c) { a[col][c] *= d; inv[col][c] *= d; }
+        rec[k] = piv;
+        if (piv != k)
+            for (int c = 0; c < nf; ++c) { double t = a[k][c]; a[k][c] = a[piv][c]; a[piv][c] = t; }
+        const double d = 1.0 / a[k][k];
+        a[k][k] = 1.0;
+        for (int c = 0; c < nf; ++c) a[k][c] *= d;
         for (int r = 0; r < nf; ++r) {
-            if (r == col) continue;
-            double f = a[r][col];
+            if (r == k) continue;
+            const double f = a[r][k];
             if (f == 0.0) continue;
-            for (int c = 0; c < nf; ++c) { a[r][c] -= f * a[col][c]; inv[r][c] -= f * inv[col][c]; }
+            a[r][k] = 0.0;
+            for (int c = 0; c < nf; ++c) a[r][c] -= f * a[k][c];
         }
     }
     if (singular) {
         atomicAdd(bad, 1);
         for (int r = 0; r < nf; ++r)
-            for (int c = 0; c < nf; ++c) inv[r][c] = (r == c) ? 1.0 : 0.0;
+            for (int c = 0; c < nf; ++c) a[r][c] = (r == c) ? 1.0 : 0.0;
+    } else {
+        for (int k = nf - 1; k >= 0; --k)
+            if (rec[k] != k)
+                for (int r = 0; r < nf; ++r) { double t = a[r][k]; a[r][k] = a[r][rec[k]]; a[r][rec[k]] = t; }
     }
     for (int r = 0; r < nf; ++r)
         for (int c = 0; c < nf; ++c) {
-            B[r * nf + c] = inv[r][c];
-            if (blk32) blk32[(int64_t)(r * nf + c) * nblk + b] = (float)inv[r][c];   // entry-major: coalesced apply
+            B[r * nf + c] = a[r][c];
+            if (blk32) blk32[(int64_t)(r * nf + c) * nblk + b] = (float)a[r][c];   // entry-major: coalesced apply
         }
 }
 

@@ -149,3 +149,21 @@ def test_dg1_discharge_with_limiter_matches_oracle():
     assert np.allclose(res["dt"], rec.dt, rtol=1e-14, atol=0)
     assert np.allclose(res["U_cell"], rec.U, rtol=1e-8, atol=0)
     assert_state_close(model, grid, to_host(zd), zf, 1e-8)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_dg1_relaxation_parity(precision):
+    """Parabolic relaxation (Sec. 2.8) of a DG1 state, one step of dt = 0.1 s: the relaxation
+    form of the linearised products and blocks (FP64, and FP32 inside the mixed Newton iteration).
+    (A second step starts almost relaxed and its Newton target sits at the rounding level of the
+    scaled residual for this small grid.)"""
+    from oracle import init
+    from paper_2511_05233_gb300 import dgls
+
+    model, grid, phase, z0, _ = make_case("tradeoff", 1, (6, 4, 3))
+    kw = {"precision": dgls.MIXED} if precision == "mixed" else {}
+    ctx = gpu_context(model, phase, **kw)
+    ref = init.relax(model, grid, z0, dt=0.1, t_init=0.1)
+    zd = to_dev(z0)
+    ctx.relax(zd, 0.1, 1)
+    assert_state_close(model, grid, to_host(zd), ref, 1e-8)
