@@ -473,7 +473,7 @@ extern "C" dg_status dg_layout(const dg_ctx* ctx, int64_t* n_dof, int32_t* n_fie
 static dg_status residual_(dg_ctx* ctx, const double* z, const double* zn, double t, double dt, int relax, double* r) {
     ProfScope ps(ctx, 0);
     cudaError_t e = ctx->P.order == 0 ? dg0_residual(ctx->L, ctx->P, ctx->G, z, zn, t, dt, relax, r, ctx->gb)
-                                      : dg1_residual(ctx->L, ctx->P, ctx->G, z, zn, t, dt, relax, r, ctx->gb);
+                                      : dg1_residual(ctx->L, ctx->P, ctx->G, z, zn, t, dt, relax, r, ctx->gb, ctx->gbd);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("residual: ") + cudaGetErrorString(e));
     ctx->res_evals++;
     return DG_OK;

@@ -1478,23 +1478,161 @@ cudaError_t dg1_limit(const LaunchCtx& L, const DevParams& p, const Geo& g, doub
 
 // ------------------------------------------------------------------ launchers
 
+// ------------------------------------------------------------------ residual, each face once
+// (1) one thread per +d face (voxel, nodal line): the weighted fluxes of every transport equation
+// through that face (and the anode exchange on the x = nx face); (2) one thread per (voxel, line):
+// the volume terms of the line, plus its two faces, plus the collector current on the x = 0 face.
+// flux: [4 lines][NL + 2][n_cell] for the current direction.
+template <class Chem>
+__global__ void __launch_bounds__(128) k_res_face(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                  const double* __restrict__ gb, int d, int relax,
+                                                  double* __restrict__ flux) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 4) return;
+    constexpr int NL = Chem::NL;
+    const int q = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)q * p.n_cell);
+    int i, j, k;
+    cell_ijk(p, cell, i, j, k);
+    int n0, n1;
+    line_nodes(d, q, n0, n1);
+    const double wf = 0.25 * p.h * p.h, gq = SQ3 / p.h, pen = p.penalty / p.h;
+    const double al = ALPHA, be = BETA;
+    const int coord = d == 0 ? i : d == 1 ? j : k;
+    const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
+    const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+    double* out = flux + (int64_t)q * (NL + 2) * p.n_cell + cell;
+    auto put = [&](int e, double val) { out[(int64_t)e * p.n_cell] = val; };
+    auto Z = [&](int f, int n, int idx) { return z[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
+    if (coord + 1 >= ext) {
+        double fLi = 0.0, fL = 0.0;
+        if (d == 0) {   // anode exchange at the face points of the x = nx face
+            const double cLi = Z(0, n1, cell) * al + Z(0, n0, cell) * be;
+            const double phL = Z(Chem::PHIL, n1, cell) * al + Z(Chem::PHIL, n0, cell) * be;
+            const double rA = anode_rate<double>(p, cLi, phL);
+            if (!relax) fLi = rA * (wf * p.kAno);
+            fL = rA * (wf * (p.F * p.kAno));
+        }
+        put(0, fLi);
+        for (int e = 1; e < NL + 2; ++e) put(e, e == NL ? fL : 0.0);
+        return;
+    }
+    const int qc = cell + stride;
+    const double gl = gb[(int64_t)face_slot(d, +1, q) * p.n_cell + cell];
+    const double gr = gb[(int64_t)face_slot(d, -1, q) * p.n_cell + qc];
+    const double Hg = harm(gl, gr);
+    const double PL0 = Z(Chem::PHIL, n0, cell), PL1 = Z(Chem::PHIL, n1, cell);
+    const double PQ0 = Z(Chem::PHIL, n0, qc), PQ1 = Z(Chem::PHIL, n1, qc);
+    const double jL = (PL1 * al + PL0 * be) - (PQ0 * al + PQ1 * be);
+    const double mL = ((PL1 - PL0) + (PQ1 - PQ0)) * (gq * 0.5);
+    double fL = 0.0;
+#pragma unroll 1
+    for (int m = 0; m < NL; ++m) {
+        const double C0 = Z(m, n0, cell), C1 = Z(m, n1, cell), Q0 = Z(m, n0, qc), Q1 = Z(m, n1, qc);
+        const double tP = C1 * al + C0 * be, tN = Q0 * al + Q1 * be;
+        const double mc = ((C1 - C0) + (Q1 - Q0)) * (gq * 0.5);
+        const double dterm = ((tP - tN) * pen - mc) * Hg;
+        double f = relax ? 0.0 : dterm * p.D0[m];
+        if (p.zc[m] != 0.0) {
+            const double Hm = harm(gl * tP, gr * tN);
+            const double mterm = (jL * pen - mL) * Hm;
+            if (!relax) f += mterm * p.kappa_m[m];
+            fL += dterm * p.Kd[m] + mterm * p.Km[m];
+        }
+        put(m, f * wf);
+    }
+    put(NL, fL * wf);
+    double fS = 0.0;
+    if (g.phase[cell] == 1 && g.phase[qc] == 1) {
+        const int s = g.cmap[cell], sq = g.cmap[qc];
+        const double S0 = Z(Chem::PHIS, n0, s), S1 = Z(Chem::PHIS, n1, s);
+        const double Q0 = Z(Chem::PHIS, n0, sq), Q1 = Z(Chem::PHIS, n1, sq);
+        const double jS = (S1 * al + S0 * be) - (Q0 * al + Q1 * be);
+        const double mS = ((S1 - S0) + (Q1 - Q0)) * (gq * 0.5);
+        fS = (jS * pen - mS) * p.kappa_s * wf;
+    }
+    put(NL + 1, fS);
+}
+
+template <class Chem>
+__global__ void __launch_bounds__(128) k_res_gather(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                    const double* __restrict__ gb, const double* __restrict__ flux, int d,
+                                                    double t, int relax, double* __restrict__ r) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 4) return;
+    constexpr int NL = Chem::NL;
+    const int q = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)q * p.n_cell);
+    int i, j, k;
+    cell_ijk(p, cell, i, j, k);
+    int n0, n1;
+    line_nodes(d, q, n0, n1);
+    const double vol = 3.0 * p.h / 8.0;
+    const int coord = d == 0 ? i : d == 1 ? j : k;
+    const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+    const bool hasL = coord > 0;
+    const double* Fp = flux + (int64_t)q * (NL + 2) * p.n_cell + cell;
+    const double* Fm = flux + (int64_t)q * (NL + 2) * p.n_cell + (hasL ? cell - stride : cell);
+    auto Z = [&](int f, int n, int idx) { return z[p.off[f] + (int64_t)n * p.flen[f] + idx]; };
+    auto gather = [&](int e, int f, int idx, double a0, double a1) {
+        const double fp = Fp[(int64_t)e * p.n_cell];
+        const double fm = hasL ? Fm[(int64_t)e * p.n_cell] : 0.0;
+        a1 += fp * ALPHA - fm * BETA;
+        a0 += fp * BETA - fm * ALPHA;
+        r[p.off[f] + (int64_t)n0 * p.flen[f] + idx] += a0;
+        r[p.off[f] + (int64_t)n1 * p.flen[f] + idx] += a1;
+    };
+    const double gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
+    const double gsum = gN0 + gN1;
+    const double dPhi = Z(Chem::PHIL, n1, cell) - Z(Chem::PHIL, n0, cell);
+    double accL = 0.0;
+#pragma unroll 1
+    for (int m = 0; m < NL; ++m) {
+        const double C0 = Z(m, n0, cell), C1 = Z(m, n1, cell);
+        const double dc = C1 - C0;
+        double fl = relax ? 0.0 : gsum * dc * p.D0[m];
+        if (p.zc[m] != 0.0) {
+            const double msum = gN0 * C0 + gN1 * C1;
+            if (!relax) fl += msum * dPhi * p.kappa_m[m];
+            accL += (gsum * dc * p.Kd[m] + msum * dPhi * p.Km[m]) * vol;
+        }
+        fl = fl * vol;
+        gather(m, m, cell, -fl, fl);
+    }
+    gather(NL, Chem::PHIL, cell, -accL, accL);
+    if (g.phase[cell] == 1) {
+        const int sidx = g.cmap[cell];
+        const double fs = (Z(Chem::PHIS, n1, sidx) - Z(Chem::PHIS, n0, sidx)) * (2.0 * p.kappa_s * vol);
+        double a0 = -fs, a1 = fs;
+        if (d == 0 && i == 0) {   // collector current on the x = 0 face (ramped while relaxing)
+            const double fj = 0.25 * p.h * p.h * p.j_cc * (relax ? smooth_step(t) : 1.0);
+            a0 += fj * ALPHA;
+            a1 += fj * BETA;
+        }
+        gather(NL + 1, Chem::PHIS, sidx, a0, a1);
+    }
+}
+
 int64_t dg1_face_buffer_len(const DevParams& p) { return (int64_t)NG * p.n_cell; }
 
 template <class Chem>
 static cudaError_t residual_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* zn,
-                                 double t, double dt, int relax, double* r, double* gb) {
+                                 double t, double dt, int relax, double* r, double* gb, double* flux) {
     k_dg1_g<Chem, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
     k_dg1_nodes<Chem, double, 0><<<nblocks((int64_t)p.n_cell * 8, 128), 128, 0, L.st>>>(p, g, z, z, zn, t, dt, relax, 0.0, r);
-    for (int d = 0; d < 3; ++d)
-        k_dg1_lines<Chem, double, 0><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb, d, t, dt, relax, 0.0, r);
-    *L.counter += 5;
+    for (int d = 0; d < 3; ++d) {
+        k_res_face<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, gb, d, relax, flux);
+        k_res_gather<Chem><<<nblocks((int64_t)p.n_cell * 4, 128), 128, 0, L.st>>>(p, g, z, gb, flux, d, t, relax, r);
+    }
+    *L.counter += 8;
     return cudaGetLastError();
 }
 
+// flux: scratch of at least 4 (NL + 2) n_cell doubles
 cudaError_t dg1_residual(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* zn,
-                         double t, double dt, int relax, double* r, double* gb) {
-    return p.nf == 10 ? residual_impl<ChemTO>(L, p, g, z, zn, t, dt, relax, r, gb)
-                      : residual_impl<ChemR3>(L, p, g, z, zn, t, dt, relax, r, gb);
+                         double t, double dt, int relax, double* r, double* gb, double* flux) {
+    return p.nf == 10 ? residual_impl<ChemTO>(L, p, g, z, zn, t, dt, relax, r, gb, flux)
+                      : residual_impl<ChemR3>(L, p, g, z, zn, t, dt, relax, r, gb, flux);
 }
 
 template <class Chem, class S>

@@ -52,7 +52,7 @@ cudaError_t dg0_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, co
 
 // ------------------------------------------------------------------ DG1 (dg1.cu)
 cudaError_t dg1_residual(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z,
-                         const double* zn, double t, double dt, int relax, double* r, double* fbuf);
+                         const double* zn, double t, double dt, int relax, double* r, double* fbuf, double* flux);
 template <class S>
 cudaError_t dg1_jvp(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v,
                     double t, double dt, int relax, double out_scale_dt, S* out, S* fbuf, S* fbuf_d);
