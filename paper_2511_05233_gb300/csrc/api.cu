@@ -520,9 +520,8 @@ static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt
     } else if (ctx->has_lin) {
         // FP64 DG1: the blocks come from the linearisation at z, which the caller has just built
         e = dg1_lin_blocks(ctx->L, ctx->P, ctx->G, z, dt, relax, ctx->lin, ctx->blk);
-    } else {
-        e = ctx->P.order == 0 ? dg0_blocks<double>(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb)
-                              : dg1_blocks<double>(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb);
+    } else {   // DG0 (every DG1 context carries a linearisation)
+        e = dg0_blocks<double>(ctx->L, ctx->P, ctx->G, z, t, dt, relax, ctx->blk, ctx->gb);
     }
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("blocks: ") + cudaGetErrorString(e));
     e = cudaMemsetAsync(ctx->d_bad, 0, sizeof(int), ctx->L.st);

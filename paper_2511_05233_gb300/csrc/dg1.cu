@@ -197,180 +197,13 @@ __global__ void __launch_bounds__(128) k_dg1_nodes(const DevParams p, const Geo 
 }
 
 // ------------------------------------------------------------------ (B2) lines: volume + faces
-// Values of one nodal line of a voxel: the fields that carry fluxes (liquid species, Phi^L, Phi^S).
-template <class Chem, class T>
-struct Line {
-    T c[2][Chem::NL];
-    T phiL[2], phiS[2];
-};
-
-template <class Chem, class T, class S>
-__device__ __forceinline__ void load_line(const DevParams& p, const S* z, const S* v, bool tan, int cell, int sidx,
-                                          bool st, int n0, int n1, int seed_node, int seed_f, Line<Chem, T>& L) {
-    const int nodes[2] = {n0, n1};
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const int n = nodes[a];
-#pragma unroll
-        for (int m = 0; m < Chem::NL; ++m) {
-            double d = tan ? (double)ld(v, p, m, n, cell) : ((n == seed_node && m == seed_f) ? 1.0 : 0.0);
-            L.c[a][m] = Make<T>::var(ld(z, p, m, n, cell), d);
-        }
-        {
-            double d = tan ? (double)ld(v, p, Chem::PHIL, n, cell) : ((n == seed_node && Chem::PHIL == seed_f) ? 1.0 : 0.0);
-            L.phiL[a] = Make<T>::var(ld(z, p, Chem::PHIL, n, cell), d);
-        }
-        if (st) {
-            double d = tan ? (double)ld(v, p, Chem::PHIS, n, sidx) : ((n == seed_node && Chem::PHIS == seed_f) ? 1.0 : 0.0);
-            L.phiS[a] = Make<T>::var(ld(z, p, Chem::PHIS, n, sidx), d);
-        } else {
-            L.phiS[a] = Make<T>::c(0.0);
-        }
-    }
-}
-
-// Contributions of one line to its two nodes: acc[0][e] -> node n0, acc[1][e] -> node n1 for the
-// transport equations e = 0..NL-1 (species), NL (Phi^L), NL+1 (Phi^S).
-//   gN[2]: g at the two nodes; gP[2]: own face g at the -/+ face points; gQ[2]: neighbour face g
-//   on the other side of the -/+ face; Qm/Qp: neighbour lines (valid flags hasQ).
-template <class Chem, class T>
-__device__ __forceinline__ void line_terms(const DevParams& p, const Line<Chem, T>& P, const T* gN, const T* gP,
-                                           bool stP, const Line<Chem, T>* Q, const T* gQ, const bool* hasQ,
-                                           const bool* stQ, int relax, T acc[2][Chem::NL + 2]) {
-    typedef typename Base<T>::type Sc;
-    constexpr int NL = Chem::NL;
-    const Sc h = Sc(p.h);
-    const Sc vol = Sc(3.0 * p.h / 8.0);
-    const Sc wf = Sc(0.25 * p.h * p.h);
-    const Sc gq = Sc(SQ3 / p.h);
-    const Sc pen = Sc(p.penalty / p.h);
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int e = 0; e < NL + 2; ++e) acc[a][e] = Make<T>::c(0.0);
-
-    // ---- volume term of the line
-    {
-        T gsum = gN[0] + gN[1];
-        T dPhi = P.phiL[1] - P.phiL[0];
-        T accL = Make<T>::c(0.0);
-#pragma unroll
-        for (int m = 0; m < NL; ++m) {
-            T dc = P.c[1][m] - P.c[0][m];
-            T fl = Make<T>::c(0.0);
-            if (!relax) fl = gsum * dc * Sc(p.D0[m]);
-            if (p.zc[m] != 0.0) {
-                T msum = gN[0] * P.c[0][m] + gN[1] * P.c[1][m];
-                if (!relax) fl += msum * dPhi * Sc(p.kappa_m[m]);
-                accL += gsum * dc * Sc(p.Kd[m]) + msum * dPhi * Sc(p.Km[m]);
-            }
-            fl = fl * vol;
-            acc[1][m] += fl;
-            acc[0][m] -= fl;
-        }
-        accL = accL * vol;
-        acc[1][NL] += accL;
-        acc[0][NL] -= accL;
-        if (stP) {
-            T fs = (P.phiS[1] - P.phiS[0]) * Sc(2.0 * p.kappa_s) * vol;
-            acc[1][NL + 1] += fs;
-            acc[0][NL + 1] -= fs;
-        }
-    }
-    // ---- faces: side 0 is the xi = -1 face (neighbour on the left), side 1 the xi = +1 face
-#pragma unroll
-    for (int sd = 0; sd < 2; ++sd) {
-        if (!hasQ[sd]) continue;
-        const Line<Chem, T>& N = Q[sd];
-        // own trace at this face and the neighbour's trace at its opposite face
-        const Sc wn = Sc(ALPHA), wfar = Sc(BETA);
-        const int near = sd, far = 1 - sd;          // own near node index on this side
-        // left cell / right cell roles: for sd = 1 P is left (minus), for sd = 0 P is right (plus)
-        T gl = sd == 1 ? gP[1] : gQ[0];
-        T gr = sd == 1 ? gQ[1] : gP[0];
-        // traces: P at its face, N at its opposite face (near node of N is index 1 - sd)
-        T Hg = harm(gl, gr);
-        // potentials
-        T tPL = P.phiL[near] * wn + P.phiL[far] * wfar;
-        T tNL = N.phiL[far] * wn + N.phiL[near] * wfar;
-        T grPL = (P.phiL[1] - P.phiL[0]) * gq;
-        T grNL = (N.phiL[1] - N.phiL[0]) * gq;
-        // jump oriented left minus right, mean normal gradient
-        T jL = sd == 1 ? tPL - tNL : tNL - tPL;
-        T mL = (grPL + grNL) * Sc(0.5);
-        T fl[NL + 2];
-#pragma unroll
-        for (int e = 0; e < NL + 2; ++e) fl[e] = Make<T>::c(0.0);
-        T accL = Make<T>::c(0.0);
-#pragma unroll
-        for (int m = 0; m < NL; ++m) {
-            T tPc = P.c[near][m] * wn + P.c[far][m] * wfar;
-            T tNc = N.c[far][m] * wn + N.c[near][m] * wfar;
-            T jc = sd == 1 ? tPc - tNc : tNc - tPc;
-            T mc = (P.c[1][m] - P.c[0][m] + N.c[1][m] - N.c[0][m]) * (gq * Sc(0.5));
-            // flux of the (left -> right) face written as -{K}_H {d_n psi} + pen {K}_H [[psi]]
-            T dterm = (jc * pen - mc) * Hg;
-            T f = Make<T>::c(0.0);
-            if (!relax) f = dterm * Sc(p.D0[m]);
-            if (p.zc[m] != 0.0) {
-                T cl = sd == 1 ? tPc : tNc;
-                T cr = sd == 1 ? tNc : tPc;
-                T Hm = harm(gl * cl, gr * cr);
-                T mterm = (jL * pen - mL) * Hm;
-                if (!relax) f += mterm * Sc(p.kappa_m[m]);
-                accL += dterm * Sc(p.Kd[m]) + mterm * Sc(p.Km[m]);
-            }
-            fl[m] = f;
-        }
-        fl[NL] = accL;
-        if (stP && stQ[sd]) {
-            T tPS = P.phiS[near] * wn + P.phiS[far] * wfar;
-            T tNS = N.phiS[far] * wn + N.phiS[near] * wfar;
-            T jS = sd == 1 ? tPS - tNS : tNS - tPS;
-            T mS = (P.phiS[1] - P.phiS[0] + N.phiS[1] - N.phiS[0]) * (gq * Sc(0.5));
-            fl[NL + 1] = (jS * pen - mS) * Sc(p.kappa_s);
-        }
-        // left cell receives +f * v-, right cell -f * v+; P is left when sd = 1
-        const Sc sgn = sd == 1 ? Sc(1.0) : Sc(-1.0);
-#pragma unroll
-        for (int e = 0; e < NL + 2; ++e) {
-            T f = fl[e] * (wf * sgn);
-            acc[near][e] += f * wn;
-            acc[far][e] += f * wfar;
-        }
-    }
-}
-
-// Neumann terms on domain faces of a line: anode (x = nx face of the last layer) and current
-// collector (x = 0 face of structure voxels), Eqs. 25-27 at the face Gauss point of the line.
-template <class Chem, class T>
-__device__ __forceinline__ void line_boundary(const DevParams& p, const Line<Chem, T>& P, int d, int i, bool stP,
-                                              double jscale, int relax, T acc[2][Chem::NL + 2]) {
-    typedef typename Base<T>::type Sc;
-    constexpr int NL = Chem::NL;
-    if (d != 0) return;
-    const Sc wf = Sc(0.25 * p.h * p.h);
-    if (i == p.nx - 1) {
-        T cLi = P.c[1][0] * Sc(ALPHA) + P.c[0][0] * Sc(BETA);
-        T phL = P.phiL[1] * Sc(ALPHA) + P.phiL[0] * Sc(BETA);
-        T rA = anode_rate<T>(p, cLi, phL);
-        T fLi = rA * (wf * Sc(p.kAno));
-        T fL = rA * (wf * Sc(p.F * p.kAno));
-        if (!relax) { acc[1][0] += fLi * Sc(ALPHA); acc[0][0] += fLi * Sc(BETA); }
-        acc[1][NL] += fL * Sc(ALPHA);
-        acc[0][NL] += fL * Sc(BETA);
-    }
-    if (i == 0 && stP) {
-        double fj = 0.25 * p.h * p.h * p.j_cc * jscale;
-        acc[0][NL + 1] += Make<T>::c(fj * ALPHA);
-        acc[1][NL + 1] += Make<T>::c(fj * BETA);
-    }
-}
-
-// One thread per (line, voxel) of direction d.  The fields are streamed one at a time (register
-// pressure: the whole line with both neighbours would hold ~100 dual numbers), each field's two
-// nodal outputs are read-modify-written as soon as they are complete.
-template <class Chem, class S, int MODE>    // MODE 0 residual, 1 JVP tangent
+// Dual-number form, launched where no linearisation is current (the public dg_jvp of a
+// mixed-precision context): one thread per (line, voxel) of direction d, evaluating both faces of
+// its line.
+// The fields are streamed one at a time (register pressure: the whole line with both neighbours
+// would hold ~100 dual numbers), each field's two nodal outputs are read-modify-written as soon as
+// they are complete.
+template <class Chem, class S, int MODE>    // MODE 1: JVP tangent (the residual uses k_res_face/gather)
 __global__ void __launch_bounds__(128) k_dg1_lines(const DevParams p, const Geo g, const S* __restrict__ z,
                                                    const S* __restrict__ v, const S* __restrict__ gb,
                                                    const S* __restrict__ gbd, int d, double t, double dt, int relax,
@@ -554,124 +387,6 @@ __global__ void __launch_bounds__(128) k_dg1_lines(const DevParams p, const Geo 
     }
 }
 
-// ------------------------------------------------------------------ per-node diagonal blocks of S J
-// One thread per (node, voxel): for each own unknown (column) seed it, evaluate the node terms and
-// the three lines through the node with the seed (own g values recomputed so that they carry the
-// tangent), and keep the rows of this node.
-template <class Chem, class S>
-__global__ void __launch_bounds__(64) k_dg1_blk(const DevParams p, const Geo g, const S* __restrict__ z,
-                                                const S* __restrict__ gb, double t, double dt, int relax,
-                                                double* __restrict__ blk) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= (int64_t)p.n_cell * 8) return;
-    typedef Dual<S> T;
-    typedef S Sc;
-    constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
-    const int n = (int)(b / p.n_cell);
-    const int cell = (int)(b - (int64_t)n * p.n_cell);
-    int i, j, k;
-    cell_ijk(p, cell, i, j, k);
-    const int ph = g.phase[cell];
-    const int sidx = g.cmap[cell];
-    const bool st = ph == 1;
-    double* B = blk + b * NF * NF;
-    double old[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) old[f] = 0.0;
-    const double tH = smooth_step(t);
-    const int an[3] = {n & 1, (n >> 1) & 1, (n >> 2) & 1};
-#pragma unroll 1
-    for (int col = 0; col < NF; ++col) {
-        if (p.is_struct[col] && !st) {
-            for (int row = 0; row < NF; ++row) B[row * NF + col] = row == col ? 1.0 : 0.0;
-            continue;
-        }
-        double colv[NF];
-        // node terms with the seed
-        {
-            T c[NL], es[2], phiL, phiS;
-#pragma unroll
-            for (int m = 0; m < NL; ++m) c[m] = Make<T>::var(ld(z, p, m, n, cell), col == m ? 1.0 : 0.0);
-            es[0] = es[1] = Make<T>::c(0.0);
-            phiS = Make<T>::c(0.0);
-            phiL = Make<T>::var(ld(z, p, PHIL, n, cell), col == PHIL ? 1.0 : 0.0);
-            if (st) {
-#pragma unroll
-                for (int q = 0; q < NS; ++q) es[q] = Make<T>::var(ld(z, p, NL + q, n, sidx), col == NL + q ? 1.0 : 0.0);
-                phiS = Make<T>::var(ld(z, p, PHIS, n, sidx), col == PHIS ? 1.0 : 0.0);
-            }
-            T R[NF];
-            node_terms<Chem, T>(p, ph, c, es, phiL, phiS, old, tH, dt, relax, R);
-#pragma unroll
-            for (int f = 0; f < NF; ++f) colv[f] = (double)R[f].d;
-        }
-        // the three lines through node n
-#pragma unroll 1
-        for (int d = 0; d < 3; ++d) {
-            int u = d == 0 ? an[1] : an[0];
-            int w = d == 2 ? an[1] : an[2];
-            int q = u + 2 * w;
-            int n0, n1;
-            line_nodes(d, q, n0, n1);
-            Line<Chem, T> P;
-            load_line<Chem, T, S>(p, z, z, false, cell, sidx, st, n0, n1, n, col, P);
-            // own g at the nodes and at the two face points of the line, with the seed
-            T es2[2][2];
-            for (int a = 0; a < 2; ++a) {
-                int nn = a == 0 ? n0 : n1;
-                for (int s2 = 0; s2 < 2; ++s2)
-                    es2[a][s2] = (NS == 2 && st) ? Make<T>::var(ld(z, p, NL + s2, nn, sidx), (nn == n && col == NL + s2) ? 1.0 : 0.0)
-                                                 : Make<T>::c(0.0);
-            }
-            T gN[2], gP[2];
-            for (int a = 0; a < 2; ++a) {
-                T eL = liquid_fraction<Chem, T>(p, ph, es2[a]);
-                gN[a] = transport_factor<Chem, T>(p, eL, P.c[a]);
-            }
-            for (int s2 = 0; s2 < 2; ++s2) {
-                const Sc wn = Sc(s2 == 1 ? ALPHA : BETA), wfar = Sc(s2 == 1 ? BETA : ALPHA);
-                T ct[NL], et[2];
-                for (int m = 0; m < NL; ++m) ct[m] = P.c[1][m] * wn + P.c[0][m] * wfar;
-                et[0] = es2[1][0] * wn + es2[0][0] * wfar;
-                et[1] = es2[1][1] * wn + es2[0][1] * wfar;
-                T eL = liquid_fraction<Chem, T>(p, ph, et);
-                gP[s2] = transport_factor<Chem, T>(p, eL, ct);
-            }
-            Line<Chem, T> Q[2];
-            T gQ[2];
-            bool hasQ[2], stQ[2];
-            const int coord = d == 0 ? i : d == 1 ? j : k;
-            const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
-            const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
-            for (int sd = 0; sd < 2; ++sd) {
-                int qc = coord + (sd == 0 ? -1 : 1);
-                hasQ[sd] = qc >= 0 && qc < ext;
-                stQ[sd] = false;
-                gQ[sd] = Make<T>::c(0.0);
-                if (hasQ[sd]) {
-                    int qcell = cell + (sd == 0 ? -stride : stride);
-                    stQ[sd] = g.phase[qcell] == 1;
-                    load_line<Chem, T, S>(p, z, z, false, qcell, g.cmap[qcell], stQ[sd], n0, n1, -1, -1, Q[sd]);
-                    gQ[sd] = Make<T>::c(gb[(int64_t)face_slot(d, sd == 0 ? +1 : -1, q) * p.n_cell + qcell]);
-                }
-            }
-            T acc[2][NL + 2];
-            line_terms<Chem, T>(p, P, gN, gP, st, Q, gQ, hasQ, stQ, relax, acc);
-            line_boundary<Chem, T>(p, P, d, i, st, relax ? tH : 1.0, relax, acc);
-            const int a = (n == n1) ? 1 : 0;
-            for (int e = 0; e < NL + 2; ++e) {
-                int f = e < NL ? e : (e == NL ? PHIL : PHIS);
-                colv[f] += (double)acc[a][e].d;
-            }
-        }
-#pragma unroll
-        for (int row = 0; row < NF; ++row) {
-            double o = colv[row] * dt * p.rscale[row];
-            if (p.is_struct[row] && !st) o = row == col ? 1.0 : 0.0;
-            B[row * NF + col] = o;
-        }
-    }
-}
 
 // ------------------------------------------------------------------ linearised FP64 JVP
 // The FP64 JVP above recomputes, for every Krylov vector, the values and all transcendentals and
@@ -1657,23 +1372,6 @@ template cudaError_t dg1_jvp<double>(const LaunchCtx&, const DevParams&, const G
 template cudaError_t dg1_jvp<float>(const LaunchCtx&, const DevParams&, const Geo&, const float*, const float*, double,
                                     double, int, double, float*, float*, float*);
 
-template <class S>
-cudaError_t dg1_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, double t, double dt,
-                       int relax, double* blk, S* gb) {
-    if (p.nf == 10) {
-        k_dg1_g<ChemTO, S, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
-        k_dg1_blk<ChemTO, S><<<nblocks((int64_t)p.n_cell * 8, 64), 64, 0, L.st>>>(p, g, z, gb, t, dt, relax, blk);
-    } else {
-        k_dg1_g<ChemR3, S, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);
-        k_dg1_blk<ChemR3, S><<<nblocks((int64_t)p.n_cell * 8, 64), 64, 0, L.st>>>(p, g, z, gb, t, dt, relax, blk);
-    }
-    *L.counter += 2;
-    return cudaGetLastError();
-}
-template cudaError_t dg1_blocks<double>(const LaunchCtx&, const DevParams&, const Geo&, const double*, double, double,
-                                        int, double*, double*);
-template cudaError_t dg1_blocks<float>(const LaunchCtx&, const DevParams&, const Geo&, const float*, double, double,
-                                       int, double*, float*);
 
 cudaError_t dg1_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double* gb) {
     if (p.nf == 10) k_dg1_g<ChemTO, double, false><<<nblocks(p.n_cell, 128), 128, 0, L.st>>>(p, g, z, z, gb, gb);

@@ -56,9 +56,6 @@ cudaError_t dg1_residual(const LaunchCtx& L, const DevParams& p, const Geo& g, c
 template <class S>
 cudaError_t dg1_jvp(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v,
                     double t, double dt, int relax, double out_scale_dt, S* out, S* fbuf, S* fbuf_d);
-template <class S>
-cudaError_t dg1_blocks(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z,
-                       double t, double dt, int relax, double* blk, S* fbuf);
 cudaError_t dg1_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, double* fbuf);
 int64_t dg1_face_buffer_len(const DevParams& p);
 // Linearised FP64 DG1 JVP: cached derivative data at a fixed linearisation point.
