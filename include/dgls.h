@@ -71,7 +71,8 @@ typedef struct {
     int32_t gmres_restart;     /* Krylov subspace size m (30) */
     int32_t gmres_max_it;      /* total GMRES iterations per linear solve */
     double newton_rtol;        /* converged when ||S R|| <= max(rtol ||S R(z^n)||, atol sqrt(n_dof)) */
-    double newton_atol;        /* RMS floor of the scaled residual (1e-13, rounding level) */
+    double newton_atol;        /* RMS floor of the scaled residual (1e-12): just above its rounding
+                                  level, which a nearly converged step (a late relaxation step) reaches */
     int32_t newton_max_it;     /* 25 */
     double eta_max;            /* Eisenstat-Walker forcing-term cap (1e-2) */
     double eta_min;            /* forcing-term floor (1e-3): keeps the middle Newton iterations from

@@ -9,7 +9,7 @@ subtractive cancellation, for any residual written with complex-analytic operati
 Newton (the role of PETSc ``newtonls`` in Sec. 2.7): exact linear solves with SuperLU,
 backtracking line search on the scaled residual norm ||S R||_2 (Armijo 1e-4, step
 halving, at most 10 cuts), convergence when ||S R||_2 <= max(rtol ||S R(z^n)||_2, atol sqrt(N))
-(atol = 1e-13: an RMS scaled residual at the rounding level, for steps that start almost converged),
+(atol = 1e-12: an RMS scaled residual just above its rounding level, for steps that start almost converged),
 failure on the iteration limit, a failed line search or non-finite values.
 Row scales S: Delta t / (M c_ref) for species and solid rows, Delta t / (M F c_ref)
 for the two charge rows, M the cell (DG0) or node (DG1) volume.
@@ -114,7 +114,7 @@ class NewtonInfo:
     reason: str = ""
 
 
-def newton(model, grid, zn, t, dt, z0=None, rtol=1e-10, max_it=25, relax=False, max_cuts=10, atol=1e-13):
+def newton(model, grid, zn, t, dt, z0=None, rtol=1e-10, max_it=25, relax=False, max_cuts=10, atol=1e-12):
     """Solve R(z; z^n, t, dt) = 0 for z = z^{n+1} starting from z0 (default z^n)."""
     S = row_scales(model, grid, dt)
     z = (zn if z0 is None else z0).astype(float).copy()

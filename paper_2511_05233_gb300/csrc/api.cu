@@ -176,7 +176,7 @@ extern "C" dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t 
     p->gmres_restart = 30;
     p->gmres_max_it = 600;
     p->newton_rtol = 1e-10;
-    p->newton_atol = 1e-13;
+    p->newton_atol = 1e-12;
     p->preconditioner = 2;
     p->mg_cycles = 1;
     p->precond_every = 0;

@@ -167,3 +167,22 @@ def test_dg1_relaxation_parity(precision):
     zd = to_dev(z0)
     ctx.relax(zd, 0.1, 1)
     assert_state_close(model, grid, to_host(zd), ref, 1e-8)
+
+
+@pytest.mark.parametrize("order,n,n_big", [(1, (6, 4, 3), (12, 10, 8)), (0, (12, 8, 6), (24, 16, 12))])
+def test_full_relaxation_converges_and_matches_oracle(order, n, n_big):
+    """The initialisation of Sec. 2.8 as the discharge uses it: the first relaxation steps match the
+    oracle's, and the full 40 steps of 0.1 s (to 4 s) all converge on a larger grid."""
+    from oracle import init
+
+    model, grid, phase, z0, _ = make_case("tradeoff", order, n)
+    ctx = gpu_context(model, phase)
+    ref = init.relax(model, grid, z0, dt=0.1, t_init=0.3)
+    zd = to_dev(z0)
+    ctx.relax(zd, 0.1, 3)
+    assert_state_close(model, grid, to_host(zd), ref, 1e-8)
+    mb, gb, pb, zb0, _ = make_case("tradeoff", order, n_big)
+    cb = gpu_context(mb, pb)
+    z40 = to_dev(zb0)
+    cb.relax(z40, 0.1, 40)                       # raises unless all 40 steps converge
+    assert np.all(np.isfinite(to_host(z40)))
