@@ -1,0 +1,90 @@
+"""A complete galvanostatic discharge on one synthetic structure: Tab. 6 equilibrium state, the
+parabolic relaxation of Sec. 2.8 (40 steps of 0.1 s), then the naive controller (Fig. 4) at the
+given C-rate down to the 1.9 V cut-off.  Prints one JSON line with the discharge curve (time, cell
+voltage U_cell (Eq. A1), specific capacity c_m (App. B)), the step statistics and the wall time;
+with --compare, the same discharge in the other precision and the largest relative difference of
+the two curves at the common accepted times.
+
+    python -m paper_2511_05233_gb300.discharge_run --n 32 --order 1 --f-C 0.5 --precision fp64
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, h=1e-6):
+    import torch
+
+    from . import dgls, inputs
+
+    phase = None
+    for s in range(seed, seed + 50):
+        ph = inputs.make_structure(n, porosity, corr_len, s)
+        if np.any(ph[:, :, 0] == inputs.STRUCT):
+            phase = ph
+            break
+    prm = dgls.default_params(dgls.TRADEOFF, order, f_C=f_C, eps_struct=1.0 - porosity,
+                              precision=dgls.MIXED if precision == "mixed" else dgls.FP64)
+    ctx = dgls.Context(phase, h, prm)
+    z = ctx.new_state()
+    ctx.equilibrium_state(z)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.relax(z, 0.1, 40)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    res = ctx.discharge(z, controller=dgls.NAIVE, dt0=1e-3, dt_min=1e-6, dt_max=10.0, cutoff_V=1.9,
+                        max_steps=max_steps, limiter=limiter)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    out = {"n": n, "order": order, "porosity": porosity, "corr_len": corr_len, "f_C": f_C, "precision": precision,
+           "n_dof": ctx.n_dof, "status": res["status"], "steps": int(len(res["t"])), "attempts": res["attempts"],
+           "failures": res["failures"], "reached_cutoff": bool(len(res["U_cell"]) and res["U_cell"][-1] <= 1.9),
+           "t_end_s": float(res["t"][-1]) if len(res["t"]) else 0.0,
+           "capacity_ah_per_kg": float(res["c_m"][-1]) if len(res["c_m"]) else 0.0,
+           "newton_total": int(np.sum(res["newton_its"])), "gmres_total": int(np.sum(res["gmres_its"])),
+           "wall_relax_s": t1 - t0, "wall_discharge_s": t2 - t1,
+           "curve": {"t": res["t"].tolist(), "U_cell": res["U_cell"].tolist(), "c_m": res["c_m"].tolist()}}
+    ctx.close()
+    return out
+
+
+def curve_diff(a, b):
+    """Largest relative difference of U_cell at the accepted times the two runs share."""
+    ta, tb = np.asarray(a["curve"]["t"]), np.asarray(b["curve"]["t"])
+    m = min(len(ta), len(tb))
+    same = bool(m and np.array_equal(ta[:m], tb[:m]))
+    ua, ub = np.asarray(a["curve"]["U_cell"][:m]), np.asarray(b["curve"]["U_cell"][:m])
+    return {"same_times_for_first_steps": same, "common_steps": int(m),
+            "max_rel_diff_U_cell": float(np.abs(ua - ub).max() / np.abs(ua).max()) if m else None}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--order", type=int, default=1)
+    ap.add_argument("--porosity", type=float, default=0.5)
+    ap.add_argument("--corr-len", type=float, default=4.0)
+    ap.add_argument("--f-C", type=float, default=0.5)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--max-steps", type=int, default=5000)
+    ap.add_argument("--limiter", action="store_true")
+    ap.add_argument("--compare", action="store_true", help="also run the other precision and compare")
+    a = ap.parse_args()
+    r = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, a.precision, a.seed, a.max_steps, a.limiter)
+    out = {"run": r}
+    if a.compare:
+        other = "mixed" if a.precision == "fp64" else "fp64"
+        r2 = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, other, a.seed, a.max_steps, a.limiter)
+        out["other"] = r2
+        out["comparison"] = curve_diff(r, r2)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
