@@ -10,7 +10,10 @@ Newton (the role of PETSc ``newtonls`` in Sec. 2.7): exact linear solves with Su
 backtracking line search on the scaled residual norm ||S R||_2 (Armijo 1e-4, step
 halving, at most 10 cuts), convergence when ||S R||_2 <= max(rtol ||S R(z^n)||_2, atol sqrt(N))
 (atol = 1e-12: an RMS scaled residual just above its rounding level, for steps that start almost converged),
-failure on the iteration limit, a failed line search or non-finite values.
+or when the line search can no longer reduce ||S R||_2 and ||S R||_2 <= stall_rtol ||S R(z^n)||_2
+(stall_rtol = 1e-8, PETSc's default relative tolerance: at large dt the rounding level of the scaled
+residual lies above rtol ||S R(z^n)||_2); failure on the iteration limit, a failed line search above
+that level or non-finite values.
 Row scales S: Delta t / (M c_ref) for species and solid rows, Delta t / (M F c_ref)
 for the two charge rows, M the cell (DG0) or node (DG1) volume.
 """
@@ -114,7 +117,8 @@ class NewtonInfo:
     reason: str = ""
 
 
-def newton(model, grid, zn, t, dt, z0=None, rtol=1e-10, max_it=25, relax=False, max_cuts=10, atol=1e-12):
+def newton(model, grid, zn, t, dt, z0=None, rtol=1e-10, max_it=25, relax=False, max_cuts=10, atol=1e-12,
+           stall_rtol=1e-8):
     """Solve R(z; z^n, t, dt) = 0 for z = z^{n+1} starting from z0 (default z^n)."""
     S = row_scales(model, grid, dt)
     z = (zn if z0 is None else z0).astype(float).copy()
@@ -143,6 +147,10 @@ def newton(model, grid, zn, t, dt, z0=None, rtol=1e-10, max_it=25, relax=False, 
                 break
             lam *= 0.5
         else:
+            # no decrease possible: stagnation at the rounding level of the scaled residual counts
+            # as converged within stall_rtol (PETSc's default relative tolerance), else a failure
+            if np.isfinite(nrm) and nrm <= stall_rtol * n0:
+                return z, NewtonInfo(True, it, n0, nrm)
             return z, NewtonInfo(False, it, n0, nrm, "line_search")
         z, Rz, nrm = zt, Rt, nt
         it += 1

@@ -181,6 +181,7 @@ extern "C" dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t 
     p->mg_cycles = 1;
     p->precond_every = 0;
     p->reorth = 2;
+    p->newton_stall_rtol = 1e-8;
     p->newton_max_it = 25;
     p->eta_max = 1e-2;
     p->eta_min = 1e-3;
@@ -220,6 +221,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     if (!(prm->eps_struct > 0 && prm->eps_struct <= 1) || prm->gmres_restart < 1 || prm->gmres_restart > MAXK - 1)
         return DG_ERR_ARG;
     if (prm->reorth < 0 || prm->reorth > 2) return DG_ERR_ARG;
+    if (!(prm->newton_stall_rtol >= 0.0)) return DG_ERR_ARG;
     const int64_t ncell64 = (int64_t)s->nx * s->ny * s->nz;
     if (ncell64 > 2000000000LL) return DG_ERR_ARG;
     dg_ctx* ctx = new dg_ctx();
@@ -844,7 +846,13 @@ static dg_status newton_(dg_ctx* ctx, const double* zn, double t1, double dt, in
             if (std::isfinite(nt) && nt <= (1.0 - 1e-4 * lam) * nrm) { ok = true; break; }
             lam *= 0.5;
         }
-        if (!ok) { result = fail(ctx, DG_ERR_NOCONV, "Newton: line search failed"); break; }
+        if (!ok) {
+            // stagnation at the rounding level of the scaled residual: converged if within the
+            // stall tolerance, otherwise a genuine failure
+            if (std::isfinite(nrm) && nrm <= ctx->prm.newton_stall_rtol * n0) break;
+            result = fail(ctx, DG_ERR_NOCONV, "Newton: line search failed");
+            break;
+        }
         std::swap(ctx->zc, ctx->zt);
         std::swap(ctx->R, ctx->Rt);
         // Eisenstat-Walker choice 2 (gamma 0.9, alpha 2) with the usual safeguard

@@ -137,3 +137,22 @@ def test_dg0_mixed_precision_step_matches_fp64():
     _, i32 = c32.step(to_dev(z), b, 0.0, 1e-3)
     assert i64.converged and i32.converged
     assert_state_close(model, grid, to_host(b), to_host(a), 1e-8)
+
+
+def test_dg0_large_step_after_relaxation():
+    """A step of dt = 2 s (where the controller spends most of a discharge) from a relaxed state,
+    Newton-GMRES on the GPU against exact Newton in the oracle."""
+    from oracle import init
+
+    model, grid, phase, z0, _ = make_case("tradeoff", 0, (9, 6, 5))
+    zr = init.relax(model, grid, z0, dt=0.1, t_init=0.4)
+    ref, info = newton.implicit_euler_step(model, grid, zr, 0.4, 2.0)
+    assert info.converged
+    ctx = gpu_context(model, phase)
+    zd = to_dev(z0)
+    ctx.relax(zd, 0.1, 4)
+    assert_state_close(model, grid, to_host(zd), zr, 1e-8)
+    out = to_dev(np.zeros_like(z0))
+    st, ginfo = ctx.step(zd, out, 0.4, 2.0)
+    assert ginfo.converged
+    assert_state_close(model, grid, to_host(out), ref, 1e-8)

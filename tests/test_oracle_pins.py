@@ -395,3 +395,43 @@ def test_structure_generator():
     from scipy import ndimage
     lab, n = ndimage.label(ph2 == inputs.STRUCT, structure=ndimage.generate_binary_structure(3, 1))
     assert set(np.unique(lab[:, :, 0])) - {0} == set(range(1, n + 1))
+
+
+@pytest.mark.parametrize("level,expect", [(1e-9, True), (1e-6, False)])
+def test_newton_stall_rule(monkeypatch, level, expect):
+    """A Newton solve that stagnates at a residual floor is converged if the floor is below 1e-8 of
+    the initial scaled residual and a failure if it is above.  The floor is planted in the oracle: a
+    noise vector of the given size that changes with the state (seeded by its bytes), like rounding,
+    and is real, so the complex-step Jacobian does not see it."""
+    model, grid, phase, z0, z = _stall_case()
+    dt = 1e-3
+    R0 = lis.residual(model, grid, z, z, dt, dt)
+    S = newton.row_scales(model, grid, dt)
+    n0 = np.linalg.norm(S * R0)
+    base = lis.residual
+
+    def noisy(m, g, zz, *a, **k):
+        r = base(m, g, zz, *a, **k)
+        if np.iscomplexobj(zz):
+            return r
+        e = np.random.default_rng(abs(hash(np.asarray(zz).tobytes())) % (2 ** 32)).normal(size=r.size)
+        return r + e * (level * n0 / np.linalg.norm(S * e))
+
+    monkeypatch.setattr(lis, "residual", noisy)
+    _, info = newton.newton(model, grid, z, dt, dt)
+    assert info.converged is expect
+    if not expect:
+        assert info.reason in ("line_search", "max_it")
+
+
+def _stall_case():
+    phase = inputs.make_structure((6, 4, 3), 0.6, 2.0, 1)
+    for s in range(1, 60):
+        phase = inputs.make_structure((6, 4, 3), 0.6, 2.0, s)
+        if np.any(phase[:, :, 0] == inputs.STRUCT):
+            break
+    grid = lis.Grid(phase, 1e-6)
+    model = lis.Model(ch.reduced3(), order=0, eps_struct=0.4)
+    z0 = init.uniform_state(model, grid, init.equilibrium_fields(model))
+    z = init.perturb(model, grid, z0, inputs.uniform_noise(z0.size, 2))
+    return model, grid, phase, z0, z
