@@ -93,6 +93,14 @@ typedef struct {
                                   orthogonalisation, the solver of Sec. 2.7; default); 0 = a second
                                   pass when the first cancelled, ||w'|| < ||w|| / sqrt(2)
                                   (Daniel-Gragg-Kaufman-Stewart); 1 = always two passes (CGS2) */
+    int32_t species_mg;        /* DG1 with preconditioner 1 or 2: coarse correction of the liquid species
+                                  rows (an aggregation multigrid per pair of species on P^T S J P: the
+                                  storage and own-species reaction diagonal plus the interior-penalty
+                                  diffusion conductances of Eq. 46), applied together with the potential
+                                  correction in the multiplicative form (one more Jacobian-vector product
+                                  per application).  0 = off; 1 = on; 2 = on when
+                                  max_m D_m^0 dt / h^2 >= 10, the steps where diffusion reaches past
+                                  the neighbouring voxels (default) */
 } dg_params;
 
 typedef struct {

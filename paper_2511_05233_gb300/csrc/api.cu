@@ -55,6 +55,9 @@ struct dg_ctx {
     void* y1 = nullptr;            // CPR: potential correction
     void* t2 = nullptr;            // CPR: remaining residual
     std::vector<MGLevel> mg;
+    std::vector<MGLevel> mgsp[3];  // species coarse level: one hierarchy per pair of liquid species
+    int sp_pairs = 0;
+    bool sp_on = false;            // species correction built for the current preconditioner
     float* z32 = nullptr;
     // discharge work states
     double *za = nullptr, *zb = nullptr, *zC = nullptr, *zF = nullptr;
@@ -181,6 +184,7 @@ extern "C" dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t 
     p->mg_cycles = 1;
     p->precond_every = 0;
     p->reorth = 2;
+    p->species_mg = 2;
     p->newton_stall_rtol = 1e-8;
     p->newton_max_it = 25;
     p->eta_max = 1e-2;
@@ -221,6 +225,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     if (!(prm->eps_struct > 0 && prm->eps_struct <= 1) || prm->gmres_restart < 1 || prm->gmres_restart > MAXK - 1)
         return DG_ERR_ARG;
     if (prm->reorth < 0 || prm->reorth > 2) return DG_ERR_ARG;
+    if (prm->species_mg < 0 || prm->species_mg > 2) return DG_ERR_ARG;
     if (!(prm->newton_stall_rtol >= 0.0)) return DG_ERR_ARG;
     const int64_t ncell64 = (int64_t)s->nx * s->ny * s->nz;
     if (ncell64 > 2000000000LL) return DG_ERR_ARG;
@@ -358,6 +363,10 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         dg1_lin_sizes(P, &njn, &ngam, &nface);
         need += (njn + 2 * ngam + nface + dg1_lin_flux_len(P)) * (mixed ? 4 : 8);
     }
+    if (prm->preconditioner != 0) {   // multigrid hierarchies: 153 bytes a voxel on level 0, 8/7 over all levels
+        const int hier = 1 + (prm->order == 1 && prm->species_mg != 0 ? (P.nl + 1) / 2 : 0);
+        need += hier * ncell * 175;
+    }
     if (prm->hbm_budget_bytes > 0 && need > prm->hbm_budget_bytes) {
         dg_status st = fail(ctx, DG_ERR_OOM, "workspace of " + std::to_string(need) + " bytes exceeds hbm_budget_bytes");
         delete ctx;
@@ -420,6 +429,15 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         free_all(ctx);
         delete ctx;
         return DG_ERR_OOM;
+    }
+    if (prm->preconditioner != 0 && prm->order == 1 && prm->species_mg != 0) {
+        ctx->sp_pairs = (P.nl + 1) / 2;
+        for (int k = 0; k < ctx->sp_pairs; ++k)
+            if (mg_levels_alloc(ctx->mgsp[k], nx, ny, nz, ctx->allocs, &ctx->ws_bytes) != cudaSuccess) {
+                free_all(ctx);
+                delete ctx;
+                return DG_ERR_OOM;
+            }
     }
 #undef AL
     if (cudaMallocHost(&ctx->hres, 256 * sizeof(double)) != cudaSuccess) {
@@ -534,11 +552,24 @@ static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt
         e = mg_setup(ctx->L, ctx->P, ctx->G, z, gbz, t, dt, relax, ctx->mg);
         if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("multigrid setup: ") + cudaGetErrorString(e));
     }
+    // species coarse level: off while relaxing (the species rows are storage alone there)
+    ctx->sp_on = false;
+    if (ctx->sp_pairs > 0 && !relax) {
+        double dmax = 0.0;
+        for (int m = 0; m < ctx->P.nl; ++m) dmax = std::max(dmax, ctx->P.D0[m]);
+        ctx->sp_on = ctx->prm.species_mg == 1 || dmax * dt / (ctx->P.h * ctx->P.h) >= 10.0;
+    }
+    if (ctx->sp_on) {
+        const double* gbz = (ctx->has_lin && !ctx->lin.f32) ? ctx->lin.gb : ctx->gb;
+        const void* jn = ctx->lin.f32 ? (const void*)ctx->lin.jn32 : (const void*)ctx->lin.jn;
+        e = mg_species_setup(ctx->L, ctx->P, ctx->G, z, gbz, jn, ctx->lin.f32, dt, ctx->mgsp, ctx->sp_pairs);
+        if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("species multigrid setup: ") + cudaGetErrorString(e));
+    }
     return DG_OK;
 }
 
 // u = M^{-1} v: block Jacobi, or the two-stage CPR preconditioner
-//   y1 = P MG(R v);  u = B^{-1} (v - S J y1) + y1
+//   y1 = P MG(R v) (+ the species coarse correction);  u = B^{-1} (v - S J y1) + y1
 template <class S>
 static dg_status precond_apply_(dg_ctx* ctx, const S* v, S* u, const S* zS, double t, double dt, int relax, S* gbS,
                                 S* gbdS, const void* blkS) {
@@ -551,7 +582,11 @@ static dg_status precond_apply_(dg_ctx* ctx, const S* v, S* u, const S* zS, doub
     S* y1 = (S*)ctx->y1;
     S* t2 = (S*)ctx->t2;
     CK(cpr_stage1<S>(ctx->L, ctx->P, ctx->G, ctx->mg, ctx->prm.mg_cycles, v, y1));
-    if (ctx->prm.preconditioner == 2) {
+    // with the species coarse level the two corrections are always applied in the multiplicative
+    // form: added to the node blocks, the decoupled species correction over-corrects the smooth
+    // modes of the reaction-coupled polysulfides wherever storage and diffusion are comparable
+    if (ctx->sp_on) CK(mg_species_apply<S>(ctx->L, ctx->P, ctx->mgsp, ctx->sp_pairs, v, y1));
+    if (ctx->prm.preconditioner == 2 && !ctx->sp_on) {
         // additive form: u = B^{-1} v + P MG(R v) (no Jacobian-vector product)
         CK(block_apply<S>(ctx->L, ctx->P, ctx->G, blkS, v, u));
         CK(saxpby<S>(ctx->L, u, 1.0, y1, 1.0, N));

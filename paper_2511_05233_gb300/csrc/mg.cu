@@ -308,28 +308,34 @@ __global__ void k_mg_prolong(MGLevel F, MGLevel C) {
     if (F.st[f]) F.x[(int64_t)F.n + f] += C.x[(int64_t)C.n + c];
 }
 
-// coarsest level (n <= 64 voxels, 2n <= 128 unknowns): dense inverse by Gauss-Jordan in one
-// thread block at set-up (the operator is a symmetric M-matrix, so no pivoting is needed), one
-// dense matrix-vector product per V-cycle.
-__global__ void __launch_bounds__(128) k_mg_dense_build(MGLevel L) {
-    __shared__ double piv[256];
-    const int m = 2 * L.n;                 // unknowns: L fields 0..n-1, S fields n..2n-1
-    const int r = threadIdx.x;
-    double* A = L.dense;                   // [m][2m]: [A | I] row-major
-    if (r < m) {
-        for (int c = 0; c < 2 * m; ++c) A[r * 2 * m + c] = 0.0;
+// coarsest level (n <= 64 voxels, m = 2n <= 128 unknowns): dense inverse at set-up by in-place
+// Gauss-Jordan elimination in shared memory (m x m doubles, at most 128 KB) in one thread block of
+// 1024 threads; the operator is a symmetric M-matrix, so no pivoting is needed.  One dense
+// matrix-vector product per V-cycle.
+constexpr int DENSE_THREADS = 1024;
+constexpr int DENSE_MAX = 128;
+
+__global__ void __launch_bounds__(DENSE_THREADS) k_mg_dense_build(MGLevel L) {
+    extern __shared__ double A[];            // [m][m] row-major: L fields 0..n-1, S fields n..2n-1
+    __shared__ double rowk[DENSE_MAX], colk[DENSE_MAX];
+    const int m = 2 * L.n;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < m * m; e += DENSE_THREADS) A[e] = 0.0;
+    __syncthreads();
+    if (tid < m) {
+        const int r = tid;
         const int cell = r < L.n ? r : r - L.n;
         const bool isL = r < L.n;
-        // column of A applied to unit vectors: use apply_A on basis vectors is O(m^2); build directly
         int i, j, k;
         ijk(cell, L.nx, L.ny, i, j, k);
         const int64_t n = L.n;
         const double* G = isL ? L.gL : L.gS;
+        double* row = A + (int64_t)r * m;
         double diag = 0.0;
         auto nbr = [&](int q, double g) {
             if (g == 0.0) return;
             diag += g;
-            A[r * 2 * m + (isL ? q : n + q)] -= g;
+            row[isL ? q : n + q] -= g;
         };
         if (i + 1 < L.nx) nbr(cell + 1, G[cell]);
         if (j + 1 < L.ny) nbr(cell + L.nx, G[n + cell]);
@@ -339,43 +345,43 @@ __global__ void __launch_bounds__(128) k_mg_dense_build(MGLevel L) {
         if (k > 0) nbr(cell - L.nx * L.ny, G[2 * n + cell - L.nx * L.ny]);
         const double a = L.a[cell];
         if (isL) {
-            A[r * 2 * m + r] += diag + a + L.dL[cell];
-            A[r * 2 * m + n + cell] -= a;
+            row[r] += diag + a + L.dL[cell];
+            row[n + cell] -= a;
         } else if (L.st[cell]) {
-            A[r * 2 * m + r] += diag + a + L.dS[cell];
-            A[r * 2 * m + cell] -= a;
+            row[r] += diag + a + L.dS[cell];
+            row[cell] -= a;
         } else {
-            for (int c = 0; c < m; ++c) A[r * 2 * m + c] = 0.0;
-            A[r * 2 * m + r] = 1.0;
+            for (int c = 0; c < m; ++c) row[c] = 0.0;
+            row[r] = 1.0;
         }
-        A[r * 2 * m + m + r] = 1.0;
     }
     __syncthreads();
+    // pivot k: row k <- row k / p (entry k <- 1/p); row i != k <- row i - A[i][k] row k (entry k <- -A[i][k]/p)
     for (int kk = 0; kk < m; ++kk) {
-        if (r < 2 * m) piv[r] = A[kk * 2 * m + r];
-        if (r + 128 < 2 * m) piv[r + 128] = A[kk * 2 * m + r + 128];
-        __syncthreads();
-        if (r < m && r != kk) {
-            double f = A[r * 2 * m + kk] / piv[kk];
-            if (f != 0.0)
-                for (int c = 0; c < 2 * m; ++c) A[r * 2 * m + c] -= f * piv[c];
+        if (tid < m) {
+            const double pinv = 1.0 / A[(int64_t)kk * m + kk];
+            rowk[tid] = tid == kk ? pinv : A[(int64_t)kk * m + tid] * pinv;
+            colk[tid] = A[(int64_t)tid * m + kk];
         }
         __syncthreads();
-        if (r == kk) {
-            double d = 1.0 / piv[kk];
-            for (int c = 0; c < 2 * m; ++c) A[r * 2 * m + c] *= d;
+        for (int e = tid; e < m * m; e += DENSE_THREADS) {
+            const int i = e / m, c = e - i * m;
+            if (i == kk) A[e] = rowk[c];
+            else if (c == kk) A[e] = -colk[i] * rowk[kk];
+            else A[e] -= colk[i] * rowk[c];
         }
         __syncthreads();
     }
+    for (int e = tid; e < m * m; e += DENSE_THREADS) L.dense[e] = A[e];
 }
 
 __global__ void __launch_bounds__(128) k_mg_dense_solve(MGLevel L) {
     const int m = 2 * L.n;
     const int r = threadIdx.x;
     if (r >= m) return;
-    const double* A = L.dense;
+    const double* A = L.dense + (int64_t)r * m;
     double acc = 0.0;
-    for (int c = 0; c < m; ++c) acc += A[r * 2 * m + m + c] * L.b[c];
+    for (int c = 0; c < m; ++c) acc += A[c] * L.b[c];
     L.x[r] = acc;
 }
 
@@ -414,6 +420,99 @@ __global__ void k_cpr_prolong(const DevParams p, const Geo g, MGLevel L, S* __re
     if (s >= 0) y[p.off[fS] + (int64_t)n * p.flen[fS] + s] = (S)L.x[(int64_t)L.n + cell];
 }
 
+// ------------------------------------------------------------------ species coarse level (DG1)
+// At large dt the rows of a liquid species are dominated by diffusion, whose smooth error the node
+// blocks cannot remove.  With the voxel-constant prolongation P, P^T (S J) P of species m keeps,
+// of Eqs. 45-47, the node terms and the interior penalty only (the volume integral and the
+// consistency term of Eq. 46 act on gradients, which vanish on voxel constants):
+//   (A x)_P = sum_faces G (x_P - x_Q) + d_P x_P
+//   G   = dt rscale_m (h^2/4) (penalty/h) D_m^0 sum_{4 face points} H(g_P, g_Q)
+//   d_P = dt rscale_m sum_{8 nodes} dR_m/dc_m   (storage and own-species reaction derivative),
+// plus, for Li+, the derivative of the anode exchange (Eq. 27) on the x = nx face.  Migration and
+// the couplings to the other species and to the potentials are left to the node blocks.  Two
+// species share one hierarchy as its two fields, uncoupled (a = 0, every voxel carries both; a
+// missing second species is an identity row).
+template <class Chem, class SJ>
+__global__ void k_sp_dg1(const DevParams p, const Geo g, const double* __restrict__ z, const double* __restrict__ gb,
+                         const SJ* __restrict__ jn, double dt, double mdt, int m0, int m1, MGLevel L) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    constexpr int NF = Chem::NF;
+    int i, j, k;
+    ijk(cell, p.nx, p.ny, i, j, k);
+    const int ph = g.phase[cell];
+    const double s = dt * p.rscale[m0];                 // all liquid species rows share one scale
+    const double wf = 0.25 * p.h * p.h;
+    const double gpen = s * wf * p.penalty / p.h;
+    const double D0 = p.D0[m0], D1 = m1 >= 0 ? p.D0[m1] : 0.0;
+    for (int d = 0; d < 3; ++d) {
+        int qi = i + (d == 0), qj = j + (d == 1), qk = k + (d == 2);
+        double hs = 0.0;
+        if (qi < p.nx && qj < p.ny && qk < p.nz) {
+            int q = qi + p.nx * (qj + p.ny * qk);
+            for (int pt = 0; pt < 4; ++pt) {
+                // own + face point (slot 8 + (2d+1)*4 + pt), neighbour - face point (slot 8 + 2d*4 + pt)
+                double gP = gb[(int64_t)(8 + (2 * d + 1) * 4 + pt) * p.n_cell + cell];
+                double gQ = gb[(int64_t)(8 + (2 * d) * 4 + pt) * p.n_cell + q];
+                hs += harm(gP, gQ);
+            }
+        }
+        L.gL[(int64_t)d * L.n + cell] = gpen * D0 * hs;
+        L.gS[(int64_t)d * L.n + cell] = gpen * D1 * hs;
+    }
+    double d0 = 0.0, d1 = 0.0;
+    if (ph == 1) {
+        const int sidx = g.cmap[cell];
+        for (int n = 0; n < 8; ++n) {
+            const SJ* J = jn + (int64_t)n * NF * NF * p.n_struct + sidx;
+            d0 += (double)J[(int64_t)(m0 * NF + m0) * p.n_struct];
+            if (m1 >= 0) d1 += (double)J[(int64_t)(m1 * NF + m1) * p.n_struct];
+        }
+    } else {   // storage alone: eps_L M / dt per node (eps_L = 1 in pores, the separator porosity there)
+        d0 = 8.0 * mdt * (ph == 2 ? p.eps_sep : 1.0);
+        d1 = m1 >= 0 ? d0 : 0.0;
+    }
+    if (m0 == 0 && i == p.nx - 1) {
+        for (int pt = 0; pt < 4; ++pt) {
+            int n0 = 2 * (pt & 1) + 4 * (pt >> 1), n1 = n0 + 1;
+            double cLi = ALPHA * z[p.off[0] + (int64_t)n1 * p.flen[0] + cell] + BETA * z[p.off[0] + (int64_t)n0 * p.flen[0] + cell];
+            double phL = ALPHA * z[p.off[Chem::PHIL] + (int64_t)n1 * p.flen[Chem::PHIL] + cell] +
+                         BETA * z[p.off[Chem::PHIL] + (int64_t)n0 * p.flen[Chem::PHIL] + cell];
+            Dual<double> r = anode_rate<Dual<double>>(p, mkd(cLi, 1.0), mkd(phL, 0.0));
+            d0 += wf * p.kAno * r.d;
+        }
+    }
+    L.a[cell] = 0.0;
+    L.dL[cell] = s * d0;
+    L.dS[cell] = s * d1;
+    L.st[cell] = m1 >= 0 ? 1 : 0;
+}
+
+// b = P^T v of the pair's two species (sum over the 8 nodes of the voxel)
+template <class S>
+__global__ void k_sp_restrict(const DevParams p, const S* __restrict__ v, int m0, int m1, MGLevel L) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    double b0 = 0.0, b1 = 0.0;
+    for (int n = 0; n < 8; ++n) {
+        b0 += (double)v[p.off[m0] + (int64_t)n * p.flen[m0] + cell];
+        if (m1 >= 0) b1 += (double)v[p.off[m1] + (int64_t)n * p.flen[m1] + cell];
+    }
+    L.b[cell] = b0;
+    L.b[(int64_t)L.n + cell] = b1;
+}
+
+// y += P x on the pair's two species
+template <class S>
+__global__ void k_sp_prolong_add(const DevParams p, MGLevel L, int m0, int m1, S* __restrict__ y) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)p.n_cell * 8) return;
+    const int n = (int)(b / p.n_cell);
+    const int cell = (int)(b - (int64_t)n * p.n_cell);
+    y[p.off[m0] + (int64_t)n * p.flen[m0] + cell] += (S)L.x[cell];
+    if (m1 >= 0) y[p.off[m1] + (int64_t)n * p.flen[m1] + cell] += (S)L.x[(int64_t)L.n + cell];
+}
+
 // ------------------------------------------------------------------ host drivers
 cudaError_t mg_levels_alloc(std::vector<MGLevel>& lv, int nx, int ny, int nz, std::vector<void*>& allocs,
                             int64_t* bytes) {
@@ -445,7 +544,7 @@ cudaError_t mg_levels_alloc(std::vector<MGLevel>& lv, int nx, int ny, int nz, st
         if ((e = al(&L.xt, 2 * (int64_t)L.n)) != cudaSuccess) return e;
         if ((e = al(&L.b, 2 * (int64_t)L.n)) != cudaSuccess) return e;
         const bool last = L.n <= 64 || (x == 1 && y == 1 && zz == 1);
-        if (last && (e = al(&L.dense, (int64_t)(2 * L.n) * (4 * L.n))) != cudaSuccess) return e;
+        if (last && (e = al(&L.dense, (int64_t)(2 * L.n) * (2 * L.n))) != cudaSuccess) return e;
         lv.push_back(L);
         if (last) break;
         x = (x + 1) / 2;
@@ -453,6 +552,28 @@ cudaError_t mg_levels_alloc(std::vector<MGLevel>& lv, int nx, int ny, int nz, st
         zz = (zz + 1) / 2;
     }
     return cudaSuccess;
+}
+
+// coarse levels, 2 x 2 block diagonals and the dense coarsest inverse of a hierarchy whose level 0
+// has just been written
+static cudaError_t mg_hierarchy(const LaunchCtx& Lc, std::vector<MGLevel>& lv) {
+    for (size_t l = 0; l + 1 < lv.size(); ++l) {
+        k_mg_coarsen<<<nb(lv[l + 1].n, 256), 256, 0, Lc.st>>>(lv[l], lv[l + 1]);
+        *Lc.counter += 1;
+    }
+    for (auto& L : lv) {
+        k_mg_diag<<<nb(L.n, 256), 256, 0, Lc.st>>>(L);
+        *Lc.counter += 1;
+    }
+    const int m = 2 * lv.back().n;
+    const size_t smem = (size_t)m * m * sizeof(double);
+    // opt in to more than 48 KB of dynamic shared memory (once per process; thread-safe static init)
+    static const cudaError_t attr = cudaFuncSetAttribute(k_mg_dense_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         DENSE_MAX * DENSE_MAX * (int)sizeof(double));
+    if (attr != cudaSuccess) return attr;
+    k_mg_dense_build<<<1, DENSE_THREADS, smem, Lc.st>>>(lv.back());
+    *Lc.counter += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t mg_setup(const LaunchCtx& Lc, const DevParams& p, const Geo& g, const double* z, const double* gb,
@@ -466,17 +587,7 @@ cudaError_t mg_setup(const LaunchCtx& Lc, const DevParams& p, const Geo& g, cons
         else k_pp_dg1<ChemR3><<<nb(p.n_cell, 128), 128, 0, Lc.st>>>(p, g, z, gb, t, dt, relax, lv[0]);
     }
     *Lc.counter += 1;
-    for (size_t l = 0; l + 1 < lv.size(); ++l) {
-        k_mg_coarsen<<<nb(lv[l + 1].n, 256), 256, 0, Lc.st>>>(lv[l], lv[l + 1]);
-        *Lc.counter += 1;
-    }
-    for (auto& L : lv) {
-        k_mg_diag<<<nb(L.n, 256), 256, 0, Lc.st>>>(L);
-        *Lc.counter += 1;
-    }
-    k_mg_dense_build<<<1, 128, 0, Lc.st>>>(lv.back());
-    *Lc.counter += 1;
-    return cudaGetLastError();
+    return mg_hierarchy(Lc, lv);
 }
 
 static void vcycle(const LaunchCtx& Lc, std::vector<MGLevel>& lv, size_t l) {
@@ -517,5 +628,46 @@ template cudaError_t cpr_stage1<double>(const LaunchCtx&, const DevParams&, cons
                                         const double*, double*);
 template cudaError_t cpr_stage1<float>(const LaunchCtx&, const DevParams&, const Geo&, std::vector<MGLevel>&, int,
                                        const float*, float*);
+
+cudaError_t mg_species_setup(const LaunchCtx& Lc, const DevParams& p, const Geo& g, const double* z, const double* gb,
+                             const void* jn, bool jn_f32, double dt, std::vector<MGLevel>* lv, int npairs) {
+    if (p.order != 1) return cudaErrorInvalidValue;
+    const double mdt = (p.V / 8.0) / dt;
+    for (int k = 0; k < npairs; ++k) {
+        if (lv[k].empty()) return cudaErrorInvalidValue;
+        const int m0 = 2 * k, m1 = 2 * k + 1 < p.nl ? 2 * k + 1 : -1;
+        const int grid = nb(p.n_cell, 128);
+        if (p.nf == 10) {
+            if (jn_f32) k_sp_dg1<ChemTO, float><<<grid, 128, 0, Lc.st>>>(p, g, z, gb, (const float*)jn, dt, mdt, m0, m1, lv[k][0]);
+            else k_sp_dg1<ChemTO, double><<<grid, 128, 0, Lc.st>>>(p, g, z, gb, (const double*)jn, dt, mdt, m0, m1, lv[k][0]);
+        } else {
+            if (jn_f32) k_sp_dg1<ChemR3, float><<<grid, 128, 0, Lc.st>>>(p, g, z, gb, (const float*)jn, dt, mdt, m0, m1, lv[k][0]);
+            else k_sp_dg1<ChemR3, double><<<grid, 128, 0, Lc.st>>>(p, g, z, gb, (const double*)jn, dt, mdt, m0, m1, lv[k][0]);
+        }
+        *Lc.counter += 1;
+        cudaError_t e = mg_hierarchy(Lc, lv[k]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+// y += sum over the pairs of P V-cycle(P^T v) on the species of each pair
+template <class S>
+cudaError_t mg_species_apply(const LaunchCtx& Lc, const DevParams& p, std::vector<MGLevel>* lv, int npairs, const S* v,
+                             S* y) {
+    for (int k = 0; k < npairs; ++k) {
+        const int m0 = 2 * k, m1 = 2 * k + 1 < p.nl ? 2 * k + 1 : -1;
+        k_sp_restrict<S><<<nb(p.n_cell, 256), 256, 0, Lc.st>>>(p, v, m0, m1, lv[k][0]);
+        *Lc.counter += 1;
+        vcycle(Lc, lv[k], 0);
+        k_sp_prolong_add<S><<<nb((int64_t)p.n_cell * 8, 256), 256, 0, Lc.st>>>(p, lv[k][0], m0, m1, y);
+        *Lc.counter += 1;
+    }
+    return cudaGetLastError();
+}
+template cudaError_t mg_species_apply<double>(const LaunchCtx&, const DevParams&, std::vector<MGLevel>*, int,
+                                              const double*, double*);
+template cudaError_t mg_species_apply<float>(const LaunchCtx&, const DevParams&, std::vector<MGLevel>*, int,
+                                             const float*, float*);
 
 }  // namespace dgls

@@ -32,7 +32,7 @@ class Params(C.Structure):
                 ("newton_rtol", C.c_double), ("newton_atol", C.c_double), ("newton_max_it", C.c_int32),
                 ("eta_max", C.c_double), ("eta_min", C.c_double), ("hbm_budget_bytes", C.c_int64),
                 ("preconditioner", C.c_int32), ("mg_cycles", C.c_int32), ("precond_every", C.c_int32),
-                ("newton_stall_rtol", C.c_double), ("reorth", C.c_int32)]
+                ("newton_stall_rtol", C.c_double), ("reorth", C.c_int32), ("species_mg", C.c_int32)]
 
 
 class StepInfo(C.Structure):

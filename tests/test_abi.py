@@ -39,6 +39,7 @@ def test_params_default_and_argument_checks(lib):
     assert p.order == 1 and p.chemistry == 1 and p.gmres_restart == 30 and p.newton_rtol == 1e-10
     assert abs(p.T - 298.15) < 1e-12
     assert p.preconditioner == 2 and p.precond_every == 0 and p.reorth == 2 and p.eta_min == 1e-3 and p.newton_stall_rtol == 1e-8
+    assert p.species_mg == 2
     import ctypes as C
     bad = dgls.Params()
     assert lib.dg_params_default(C.byref(bad), 7, 0) == dgls.ERR_ARG
