@@ -93,10 +93,11 @@ typedef struct {
                                   orthogonalisation, the solver of Sec. 2.7; default); 0 = a second
                                   pass when the first cancelled, ||w'|| < ||w|| / sqrt(2)
                                   (Daniel-Gragg-Kaufman-Stewart); 1 = always two passes (CGS2) */
-    int32_t species_mg;        /* DG1 with preconditioner 1 or 2: coarse correction of the liquid species
-                                  rows (an aggregation multigrid per pair of species on P^T S J P: the
-                                  storage and own-species reaction diagonal plus the interior-penalty
-                                  diffusion conductances of Eq. 46), applied together with the potential
+    int32_t species_mg;        /* with preconditioner 1 or 2: coarse correction of the liquid species rows
+                                  (an aggregation multigrid per pair of species on P^T S J P, P the
+                                  voxel-constant prolongation: the storage and own-species reaction
+                                  diagonal plus the diffusion conductances of Eq. 48, or of the interior
+                                  penalty of Eq. 46 for DG1), applied together with the potential
                                   correction in the multiplicative form (one more Jacobian-vector product
                                   per application).  0 = off; 1 = on; 2 = on when
                                   max_m D_m^0 dt / h^2 >= 10, the steps where diffusion reaches past

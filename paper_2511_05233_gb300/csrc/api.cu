@@ -364,7 +364,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         need += (njn + 2 * ngam + nface + dg1_lin_flux_len(P)) * (mixed ? 4 : 8);
     }
     if (prm->preconditioner != 0) {   // multigrid hierarchies: 153 bytes a voxel on level 0, 8/7 over all levels
-        const int hier = 1 + (prm->order == 1 && prm->species_mg != 0 ? (P.nl + 1) / 2 : 0);
+        const int hier = 1 + (prm->species_mg != 0 ? (P.nl + 1) / 2 : 0);
         need += hier * ncell * 175;
     }
     if (prm->hbm_budget_bytes > 0 && need > prm->hbm_budget_bytes) {
@@ -430,7 +430,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         delete ctx;
         return DG_ERR_OOM;
     }
-    if (prm->preconditioner != 0 && prm->order == 1 && prm->species_mg != 0) {
+    if (prm->preconditioner != 0 && prm->species_mg != 0) {
         ctx->sp_pairs = (P.nl + 1) / 2;
         for (int k = 0; k < ctx->sp_pairs; ++k)
             if (mg_levels_alloc(ctx->mgsp[k], nx, ny, nz, ctx->allocs, &ctx->ws_bytes) != cudaSuccess) {
@@ -561,8 +561,8 @@ static dg_status build_precond(dg_ctx* ctx, const double* z, double t, double dt
     }
     if (ctx->sp_on) {
         const double* gbz = (ctx->has_lin && !ctx->lin.f32) ? ctx->lin.gb : ctx->gb;
-        const void* jn = ctx->lin.f32 ? (const void*)ctx->lin.jn32 : (const void*)ctx->lin.jn;
-        e = mg_species_setup(ctx->L, ctx->P, ctx->G, z, gbz, jn, ctx->lin.f32, dt, ctx->mgsp, ctx->sp_pairs);
+        const void* jn = !ctx->has_lin ? nullptr : ctx->lin.f32 ? (const void*)ctx->lin.jn32 : (const void*)ctx->lin.jn;
+        e = mg_species_setup(ctx->L, ctx->P, ctx->G, z, gbz, jn, ctx->lin.f32, t, dt, ctx->mgsp, ctx->sp_pairs);
         if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("species multigrid setup: ") + cudaGetErrorString(e));
     }
     return DG_OK;

@@ -125,10 +125,10 @@ cudaError_t mg_setup(const LaunchCtx& L, const DevParams& p, const Geo& g, const
 template <class S>
 cudaError_t cpr_stage1(const LaunchCtx& L, const DevParams& p, const Geo& g, std::vector<MGLevel>& lv, int cycles,
                        const S* v, S* y);
-// species coarse level (DG1): one two-field hierarchy per pair of liquid species (2k, 2k+1), level 0
-// from the transport factors gb and the node Jacobians jn (FP32 when jn_f32) at the linearisation point
+// species coarse level: one two-field hierarchy per pair of liquid species (2k, 2k+1), level 0 from the
+// transport factors gb and, for DG1, the node Jacobians jn (FP32 when jn_f32) at the linearisation point
 cudaError_t mg_species_setup(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* gb,
-                             const void* jn, bool jn_f32, double dt, std::vector<MGLevel>* lv, int npairs);
+                             const void* jn, bool jn_f32, double t, double dt, std::vector<MGLevel>* lv, int npairs);
 // y += sum over the pairs of P V-cycle(P^T v) on the pair's species rows
 template <class S>
 cudaError_t mg_species_apply(const LaunchCtx& L, const DevParams& p, std::vector<MGLevel>* lv, int npairs, const S* v,

@@ -420,7 +420,7 @@ __global__ void k_cpr_prolong(const DevParams p, const Geo g, MGLevel L, S* __re
     if (s >= 0) y[p.off[fS] + (int64_t)n * p.flen[fS] + s] = (S)L.x[(int64_t)L.n + cell];
 }
 
-// ------------------------------------------------------------------ species coarse level (DG1)
+// ------------------------------------------------------------------ species coarse level
 // At large dt the rows of a liquid species are dominated by diffusion, whose smooth error the node
 // blocks cannot remove.  With the voxel-constant prolongation P, P^T (S J) P of species m keeps,
 // of Eqs. 45-47, the node terms and the interior penalty only (the volume integral and the
@@ -488,13 +488,66 @@ __global__ void k_sp_dg1(const DevParams p, const Geo g, const double* __restric
     L.st[cell] = m1 >= 0 ? 1 : 0;
 }
 
-// b = P^T v of the pair's two species (sum over the 8 nodes of the voxel)
+// DG0: the species block of S J itself (P = identity): conductance dt rscale_m h D_m^0 H(g_P, g_Q)
+// (Eq. 48), diagonal dt rscale_m (V eps_L / dt - V dS_m/dc_m), and the anode exchange for Li+.
+template <class Chem>
+__global__ void k_sp_dg0(const DevParams p, const Geo g, const double* __restrict__ z, const double* __restrict__ gb,
+                         double t, double dt, int m0, int m1, MGLevel L) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    constexpr int NL = Chem::NL;
+    int i, j, k;
+    ijk(cell, p.nx, p.ny, i, j, k);
+    const int ph = g.phase[cell];
+    const int sidx = g.cmap[cell];
+    const double s = dt * p.rscale[m0];
+    const double D0 = p.D0[m0], D1 = m1 >= 0 ? p.D0[m1] : 0.0;
+    const double gP = gb[cell];
+    for (int d = 0; d < 3; ++d) {
+        int qi = i + (d == 0), qj = j + (d == 1), qk = k + (d == 2);
+        double hg = 0.0;
+        if (qi < p.nx && qj < p.ny && qk < p.nz) hg = s * p.h * harm(gP, gb[qi + p.nx * (qj + p.ny * qk)]);
+        L.gL[(int64_t)d * L.n + cell] = hg * D0;
+        L.gS[(int64_t)d * L.n + cell] = hg * D1;
+    }
+    double es[2] = {0.0, 0.0};
+    if (ph == 1)
+        for (int q = 0; q < Chem::NS; ++q) es[q] = z[p.off[NL + q] + sidx];
+    const double vdt = p.V / dt * liquid_fraction<Chem, double>(p, ph, es);
+    double d0 = vdt, d1 = m1 >= 0 ? vdt : 0.0;
+    if (ph == 1) {
+        typedef Dual<double> T;
+        for (int w = 0; w < 2; ++w) {
+            const int m = w == 0 ? m0 : m1;
+            if (m < 0) continue;
+            T c[NL], e2[2], Sv[NL], Ss[2], qL, qS;
+            for (int l = 0; l < NL; ++l) c[l] = mkd(z[p.off[l] + cell], l == m ? 1.0 : 0.0);
+            e2[0] = mkd(es[0], 0.0);
+            e2[1] = mkd(es[1], 0.0);
+            T phiL = mkd(z[p.off[Chem::PHIL] + cell], 0.0);
+            T phiS = mkd(z[p.off[Chem::PHIS] + sidx], 0.0);
+            sources<Chem, T>(p, c, e2, phiL, phiS, smooth_step(t), Sv, Ss, qL, qS);
+            (w == 0 ? d0 : d1) += -p.V * Sv[m].d;
+        }
+    }
+    if (m0 == 0 && i == p.nx - 1) {
+        Dual<double> r = anode_rate<Dual<double>>(p, mkd(z[p.off[0] + cell], 1.0), mkd(z[p.off[Chem::PHIL] + cell], 0.0));
+        d0 += p.A * p.kAno * r.d;
+    }
+    L.a[cell] = 0.0;
+    L.dL[cell] = s * d0;
+    L.dS[cell] = s * d1;
+    L.st[cell] = m1 >= 0 ? 1 : 0;
+}
+
+// b = P^T v of the pair's two species (sum over the nodes of the voxel: 8 for DG1, 1 for DG0)
 template <class S>
 __global__ void k_sp_restrict(const DevParams p, const S* __restrict__ v, int m0, int m1, MGLevel L) {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= p.n_cell) return;
+    const int nn = p.order == 1 ? 8 : 1;
     double b0 = 0.0, b1 = 0.0;
-    for (int n = 0; n < 8; ++n) {
+    for (int n = 0; n < nn; ++n) {
         b0 += (double)v[p.off[m0] + (int64_t)n * p.flen[m0] + cell];
         if (m1 >= 0) b1 += (double)v[p.off[m1] + (int64_t)n * p.flen[m1] + cell];
     }
@@ -506,7 +559,7 @@ __global__ void k_sp_restrict(const DevParams p, const S* __restrict__ v, int m0
 template <class S>
 __global__ void k_sp_prolong_add(const DevParams p, MGLevel L, int m0, int m1, S* __restrict__ y) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= (int64_t)p.n_cell * 8) return;
+    if (b >= (int64_t)p.n_cell * (p.order == 1 ? 8 : 1)) return;
     const int n = (int)(b / p.n_cell);
     const int cell = (int)(b - (int64_t)n * p.n_cell);
     y[p.off[m0] + (int64_t)n * p.flen[m0] + cell] += (S)L.x[cell];
@@ -630,14 +683,17 @@ template cudaError_t cpr_stage1<float>(const LaunchCtx&, const DevParams&, const
                                        const float*, float*);
 
 cudaError_t mg_species_setup(const LaunchCtx& Lc, const DevParams& p, const Geo& g, const double* z, const double* gb,
-                             const void* jn, bool jn_f32, double dt, std::vector<MGLevel>* lv, int npairs) {
-    if (p.order != 1) return cudaErrorInvalidValue;
+                             const void* jn, bool jn_f32, double t, double dt, std::vector<MGLevel>* lv, int npairs) {
+    if (p.order == 1 && !jn) return cudaErrorInvalidValue;
     const double mdt = (p.V / 8.0) / dt;
     for (int k = 0; k < npairs; ++k) {
         if (lv[k].empty()) return cudaErrorInvalidValue;
         const int m0 = 2 * k, m1 = 2 * k + 1 < p.nl ? 2 * k + 1 : -1;
         const int grid = nb(p.n_cell, 128);
-        if (p.nf == 10) {
+        if (p.order == 0) {
+            if (p.nf == 10) k_sp_dg0<ChemTO><<<grid, 128, 0, Lc.st>>>(p, g, z, gb, t, dt, m0, m1, lv[k][0]);
+            else k_sp_dg0<ChemR3><<<grid, 128, 0, Lc.st>>>(p, g, z, gb, t, dt, m0, m1, lv[k][0]);
+        } else if (p.nf == 10) {
             if (jn_f32) k_sp_dg1<ChemTO, float><<<grid, 128, 0, Lc.st>>>(p, g, z, gb, (const float*)jn, dt, mdt, m0, m1, lv[k][0]);
             else k_sp_dg1<ChemTO, double><<<grid, 128, 0, Lc.st>>>(p, g, z, gb, (const double*)jn, dt, mdt, m0, m1, lv[k][0]);
         } else {
@@ -660,7 +716,7 @@ cudaError_t mg_species_apply(const LaunchCtx& Lc, const DevParams& p, std::vecto
         k_sp_restrict<S><<<nb(p.n_cell, 256), 256, 0, Lc.st>>>(p, v, m0, m1, lv[k][0]);
         *Lc.counter += 1;
         vcycle(Lc, lv[k], 0);
-        k_sp_prolong_add<S><<<nb((int64_t)p.n_cell * 8, 256), 256, 0, Lc.st>>>(p, lv[k][0], m0, m1, y);
+        k_sp_prolong_add<S><<<nb((int64_t)p.n_cell * (p.order == 1 ? 8 : 1), 256), 256, 0, Lc.st>>>(p, lv[k][0], m0, m1, y);
         *Lc.counter += 1;
     }
     return cudaGetLastError();

@@ -1,6 +1,7 @@
 """A complete galvanostatic discharge on one synthetic structure: Tab. 6 equilibrium state, the
 parabolic relaxation of Sec. 2.8 (40 steps of 0.1 s), then the naive controller (Fig. 4) at the
-given C-rate down to the 1.9 V cut-off.  Prints one JSON line with the discharge curve (time, cell
+given C-rate down to the 1.9 V cut-off; DG1 with the vertex-based slope limiter after each accepted
+step (App. B), unless --no-limiter.  Prints one JSON line with the discharge curve (time, cell
 voltage U_cell (Eq. A1), specific capacity c_m (App. B)), the step statistics and the wall time;
 with --compare, the same discharge in the other precision and the largest relative difference of
 the two curves at the common accepted times.
@@ -16,7 +17,7 @@ import time
 import numpy as np
 
 
-def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, h=1e-6):
+def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, species_mg=2, t_end=0.0, h=1e-6):
     import torch
 
     from . import dgls, inputs
@@ -28,7 +29,7 @@ def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, 
             phase = ph
             break
     prm = dgls.default_params(dgls.TRADEOFF, order, f_C=f_C, eps_struct=1.0 - porosity,
-                              precision=dgls.MIXED if precision == "mixed" else dgls.FP64)
+                              precision=dgls.MIXED if precision == "mixed" else dgls.FP64, species_mg=species_mg)
     ctx = dgls.Context(phase, h, prm)
     z = ctx.new_state()
     ctx.equilibrium_state(z)
@@ -38,15 +39,18 @@ def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, 
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     res = ctx.discharge(z, controller=dgls.NAIVE, dt0=1e-3, dt_min=1e-6, dt_max=10.0, cutoff_V=1.9,
-                        max_steps=max_steps, limiter=limiter)
+                        t_end=t_end, max_steps=max_steps, limiter=limiter)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     out = {"n": n, "order": order, "porosity": porosity, "corr_len": corr_len, "f_C": f_C, "precision": precision,
+           "limiter": bool(limiter), "species_mg": species_mg,
            "n_dof": ctx.n_dof, "status": res["status"], "steps": int(len(res["t"])), "attempts": res["attempts"],
            "failures": res["failures"], "reached_cutoff": bool(len(res["U_cell"]) and res["U_cell"][-1] <= 1.9),
            "t_end_s": float(res["t"][-1]) if len(res["t"]) else 0.0,
            "capacity_ah_per_kg": float(res["c_m"][-1]) if len(res["c_m"]) else 0.0,
            "newton_total": int(np.sum(res["newton_its"])), "gmres_total": int(np.sum(res["gmres_its"])),
+           "U_end": float(res["U_cell"][-1]) if len(res["U_cell"]) else None,
+           "dt_max_reached": float(res["dt"].max()) if len(res["dt"]) else 0.0,
            "wall_relax_s": t1 - t0, "wall_discharge_s": t2 - t1,
            "curve": {"t": res["t"].tolist(), "U_cell": res["U_cell"].tolist(), "c_m": res["c_m"].tolist()}}
     ctx.close()
@@ -73,16 +77,26 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--max-steps", type=int, default=5000)
-    ap.add_argument("--limiter", action="store_true")
+    ap.add_argument("--no-limiter", action="store_true",
+                    help="DG1 without the vertex-based slope limiter (on by default for DG1, as in App. B)")
+    ap.add_argument("--species-mg", type=int, default=2, choices=[0, 1, 2],
+                    help="species coarse level of the preconditioner: off, on, on at large dt (default)")
+    ap.add_argument("--t-end", type=float, default=0.0, help="stop at this time in s (0: at the cut-off)")
+    ap.add_argument("--no-curve", action="store_true", help="print the summary without the curve arrays")
     ap.add_argument("--compare", action="store_true", help="also run the other precision and compare")
     a = ap.parse_args()
-    r = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, a.precision, a.seed, a.max_steps, a.limiter)
+    lim = a.order == 1 and not a.no_limiter
+    r = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, a.precision, a.seed, a.max_steps, lim, a.species_mg, a.t_end)
     out = {"run": r}
     if a.compare:
         other = "mixed" if a.precision == "fp64" else "fp64"
-        r2 = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, other, a.seed, a.max_steps, a.limiter)
+        r2 = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, other, a.seed, a.max_steps, lim, a.species_mg, a.t_end)
         out["other"] = r2
         out["comparison"] = curve_diff(r, r2)
+    if a.no_curve:
+        for v in out.values():
+            if isinstance(v, dict):
+                v.pop("curve", None)
     print(json.dumps(out), flush=True)
 
 
