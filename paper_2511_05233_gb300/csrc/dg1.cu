@@ -856,7 +856,15 @@ __global__ void __launch_bounds__(128) k_lin_line_gather(const DevParams p, cons
 // touches the node terms (cached Jacobian), the transport factors of this voxel (node n and the
 // face points of the three lines through n), the volume term of each of those lines and the two
 // faces at the ends of each line, where node n enters through its trace (weight ALPHA or BETA)
-// and the normal-derivative term (+-sqrt(3)/h).  One thread per (node, voxel); FMAs only.
+// and the normal-derivative term (+-sqrt(3)/h).  Every column's tangent is a combination of five
+// seeds, so one pass over the three lines accumulates the responses to them:
+//   X, Y   the transport factors moving with a unit tangent of eps_L (X) or of c_S (Y): the
+//          tangent of g at a point is g (gam d eps_L - visc d c_S);
+//   Dd, DL a unit tangent of species m at node n itself: rows m and Phi^L;
+//   Pp     a unit tangent of Phi^L at node n: the charged species rows and Phi^L;
+//   dS     a unit tangent of Phi^S at node n: row Phi^S.
+// Column c is then J[:, c] + (species c: wS_c Y + Dd/DL; solid: -X; Phi^L: Pp; Phi^S: dS).
+// One thread per (node, voxel); FMAs only.
 template <class Chem, class S>
 __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g, const S* __restrict__ z,
                                                  const S* __restrict__ gb, const S* __restrict__ gam,
@@ -874,14 +882,133 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
     const bool st = ph == 1;
     const int an[3] = {n & 1, (n >> 1) & 1, (n >> 2) & 1};
     const S vol = S(3.0 * p.h / 8.0), wf = S(0.25 * p.h * p.h), gq = S(SQ3 / p.h), pen = S(p.penalty / p.h);
+    const S visc = S(p.visc);
     auto Z = [&](int f, int nn) { return z[p.off[f] + (int64_t)nn * p.flen[f] + cell]; };
+    S X[NF], Y[NF], Pp[NF], Dd[NL], DL[NL], dS = S(0.0);
+#pragma unroll
+    for (int r = 0; r < NF; ++r) X[r] = Y[r] = Pp[r] = S(0.0);
+#pragma unroll
+    for (int m = 0; m < NL; ++m) Dd[m] = DL[m] = S(0.0);
+    // tangent of g at node n per unit eps_L tangent (gxN) and per unit c_S tangent (gyN)
+    const S gxN = gb[(int64_t)n * p.n_cell + cell] * gam[(int64_t)n * p.n_cell + cell];
+    const S gyN = -gb[(int64_t)n * p.n_cell + cell] * visc;
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+        const int u = d == 0 ? an[1] : an[0];
+        const int w = d == 2 ? an[1] : an[2];
+        const int q = u + 2 * w;
+        int n0, n1;
+        line_nodes(d, q, n0, n1);
+        const bool a1 = n == n1;
+        const S sgn = a1 ? S(1.0) : -S(1.0);
+        const int coord = d == 0 ? i : d == 1 ? j : k;
+        const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
+        const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+        // ---- volume term of the line
+        {
+            const S gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
+            const S gown = a1 ? gN1 : gN0;
+            const S dPhi = Z(PHIL, n1) - Z(PHIL, n0);
+            const S gsum = gN0 + gN1;
+            const S sv = sgn * vol;
+            S fLg = S(0.0), fLp = S(0.0);
+#pragma unroll
+            for (int m = 0; m < NL; ++m) {
+                const S C0 = Z(m, n0), C1 = Z(m, n1);
+                const S dc = C1 - C0, Cown = a1 ? C1 : C0;
+                // transport-factor seed: d gsum = d g_n, d msum = d g_n C_n (per unit d g_n)
+                S fg = relax ? S(0.0) : dc * S(p.D0[m]);
+                // own-species seed: d dc = sgn, d msum = g_n
+                S fd = relax ? S(0.0) : gsum * sgn * S(p.D0[m]);
+                S fLd = S(0.0);
+                if (p.zc[m] != S(0.0)) {
+                    const S msum = gN0 * C0 + gN1 * C1;
+                    if (!relax) {
+                        fg += Cown * dPhi * S(p.kappa_m[m]);
+                        fd += gown * dPhi * S(p.kappa_m[m]);
+                        Pp[m] += msum * sgn * S(p.kappa_m[m]) * sv;     // Phi^L seed: d dPhi = sgn
+                    }
+                    fLg += dc * S(p.Kd[m]) + Cown * dPhi * S(p.Km[m]);
+                    fLd = gsum * sgn * S(p.Kd[m]) + gown * dPhi * S(p.Km[m]);
+                    fLp += msum * sgn * S(p.Km[m]);
+                }
+                X[m] += fg * gxN * sv;
+                Y[m] += fg * gyN * sv;
+                Dd[m] += fd * sv;
+                DL[m] += fLd * sv;
+            }
+            X[PHIL] += fLg * gxN * sv;
+            Y[PHIL] += fLg * gyN * sv;
+            Pp[PHIL] += fLp * sv;
+            if (st) dS += S(2.0) * S(p.kappa_s) * vol;
+        }
+        // ---- the two faces of the line: own voxel left (+d face) or right (-d face)
+#pragma unroll 1
+        for (int side = 1; side >= -1; side -= 2) {
+            const bool left = side > 0;
+            const S tw = left ? (a1 ? S(ALPHA) : S(BETA)) : (a1 ? S(BETA) : S(ALPHA));   // own trace weight
+            const S dBown = left ? tw * pen - S(0.5) * gq * sgn : -tw * pen - S(0.5) * gq * sgn;
+            const S wrow = left ? wf * tw : -wf * tw;
+            const bool inside = left ? coord + 1 < ext : coord > 0;
+            if (!inside) {
+                if (left && d == 0) {   // anode face: r_Ano(c_Li, Phi^L) at the face point
+                    const S* Fo = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
+                    const S drc = Fo[0] * tw, drp = Fo[(int64_t)p.n_cell] * tw;
+                    if (!relax) {
+                        Dd[0] += drc * S(p.kAno) * wrow;
+                        Pp[0] += drp * S(p.kAno) * wrow;
+                    }
+                    DL[0] += drc * S(p.F) * S(p.kAno) * wrow;
+                    Pp[PHIL] += drp * S(p.F) * S(p.kAno) * wrow;
+                }
+                continue;
+            }
+            const int fc = left ? cell : cell - stride;        // voxel owning the face data
+            const int oc = left ? cell + stride : cell - stride;   // the other voxel
+            const S* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + fc;
+            auto F = [&](int kk) { return Fd[(int64_t)kk * p.n_cell]; };
+            const int64_t so = (int64_t)face_slot(d, side, q) * p.n_cell + cell;
+            const S gxo = gb[so] * gam[so] * tw, gyo = -gb[so] * visc * tw;   // own g tangent per seed
+            const S dHg1 = left ? F(1) : F(2);                   // d Hg per unit own g tangent
+            const S Hg = F(0), BL = F(3 + NL);
+            S fLg = S(0.0), fLp = S(0.0);
+#pragma unroll
+            for (int m = 0; m < NL; ++m) {
+                const S tg = dHg1 * F(3 + m);                    // transport-factor seed
+                const S td = Hg * dBown;                         // own-species seed (d B = dBown)
+                S fg = relax ? S(0.0) : tg * S(p.D0[m]);
+                S fd = relax ? S(0.0) : td * S(p.D0[m]);
+                if (p.zc[m] != S(0.0)) {
+                    const int base = 4 + NL + 5 * SH::ci(m);
+                    const S mg = (left ? F(base + 1) : F(base + 3)) * BL;
+                    const S md = (left ? F(base + 2) : F(base + 4)) * tw * BL;
+                    const S mp = F(base) * dBown;                // Phi^L seed (d BL = dBown)
+                    if (!relax) {
+                        fg += mg * S(p.kappa_m[m]);
+                        fd += md * S(p.kappa_m[m]);
+                        Pp[m] += mp * S(p.kappa_m[m]) * wrow;
+                    }
+                    fLg += tg * S(p.Kd[m]) + mg * S(p.Km[m]);
+                    DL[m] += (td * S(p.Kd[m]) + md * S(p.Km[m])) * wrow;
+                    fLp += mp * S(p.Km[m]);
+                }
+                X[m] += fg * gxo * wrow;
+                Y[m] += fg * gyo * wrow;
+                Dd[m] += fd * wrow;
+            }
+            X[PHIL] += fLg * gxo * wrow;
+            Y[PHIL] += fLg * gyo * wrow;
+            Pp[PHIL] += fLp * wrow;
+            if (st && g.phase[oc] == 1) dS += dBown * S(p.kappa_s) * wrow;
+        }
+    }
     const S* J = st ? jn + (int64_t)n * NF * NF * p.n_struct + g.cmap[cell] : nullptr;
     const S ddc = S(ph == 2 ? nd.c_sep : nd.c_pore), ddphi = S(nd.phi);
     double* B = blk + b * NF * NF;
 #pragma unroll 1
     for (int c = 0; c < NF; ++c) {
         if (p.is_struct[c] && !st) {
-            for (int r = 0; r < NF; ++r) B[r * NF + c] = r == c ? S(1.0) : S(0.0);
+            for (int r = 0; r < NF; ++r) B[r * NF + c] = r == c ? 1.0 : 0.0;
             continue;
         }
         S col[NF];
@@ -892,101 +1019,26 @@ __global__ void __launch_bounds__(128) k_lin_blk(const DevParams p, const Geo g,
 #pragma unroll
             for (int r = 0; r < NF; ++r) col[r] = r != c ? S(0.0) : (r < NL ? ddc : (r == PHIL ? ddphi : S(0.0)));
         }
-        const int dm = c < NL ? c : -1;                      // perturbed species
-        const bool dPL = c == PHIL, dPS = c == PHIS;
-        const S dcs = c < NL ? S(p.wS[c]) : S(0.0);          // tangent of c_S at node n
-        const S del = (NS == 2 && st && (c == NL || c == NL + 1)) ? -S(1.0) : S(0.0);   // of eps_L
-        auto dg_at = [&](int slot, S w) {
-            const int64_t o = (int64_t)slot * p.n_cell + cell;
-            return gb[o] * (gam[o] * del - S(p.visc) * dcs) * w;
-        };
-        const S dgN = dg_at(n, S(1.0));
-#pragma unroll 1
-        for (int d = 0; d < 3; ++d) {
-            const int u = d == 0 ? an[1] : an[0];
-            const int w = d == 2 ? an[1] : an[2];
-            const int q = u + 2 * w;
-            int n0, n1;
-            line_nodes(d, q, n0, n1);
-            const bool a1 = n == n1;
-            const S sgn = a1 ? S(1.0) : -S(1.0);
-            const int coord = d == 0 ? i : d == 1 ? j : k;
-            const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
-            const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
-            // ---- volume term of the line
-            {
-                const S gN0 = gb[(int64_t)n0 * p.n_cell + cell], gN1 = gb[(int64_t)n1 * p.n_cell + cell];
-                const S dgN0 = a1 ? S(0.0) : dgN, dgN1 = a1 ? dgN : S(0.0);
-                const S P0 = Z(PHIL, n0), P1 = Z(PHIL, n1);
-                const S dPhi = P1 - P0, ddPhi = dPL ? sgn : S(0.0);
-                const S gsum = gN0 + gN1, dgsum = dgN0 + dgN1;
-                S fLsum = S(0.0);
+        if (c < NL) {
+            const S dcs = S(p.wS[c]);                            // tangent of c_S
 #pragma unroll
-                for (int m = 0; m < NL; ++m) {
-                    const S C0 = Z(m, n0), C1 = Z(m, n1);
-                    const S dC0 = (m == dm && !a1) ? S(1.0) : S(0.0), dC1 = (m == dm && a1) ? S(1.0) : S(0.0);
-                    const S dc = C1 - C0, ddc = dC1 - dC0;
-                    S fl = relax ? S(0.0) : (dgsum * dc + gsum * ddc) * S(p.D0[m]);
-                    if (p.zc[m] != S(0.0)) {
-                        const S msum = gN0 * C0 + gN1 * C1;
-                        const S dmsum = dgN0 * C0 + gN0 * dC0 + dgN1 * C1 + gN1 * dC1;
-                        if (!relax) fl += (dmsum * dPhi + msum * ddPhi) * S(p.kappa_m[m]);
-                        fLsum += (dgsum * dc + gsum * ddc) * S(p.Kd[m]) + (dmsum * dPhi + msum * ddPhi) * S(p.Km[m]);
-                    }
-                    col[m] += sgn * fl * vol;
-                }
-                col[PHIL] += sgn * fLsum * vol;
-                if (st && dPS) col[PHIS] += S(2.0) * S(p.kappa_s) * vol;
-            }
-            // ---- the two faces of the line: own voxel left (+d face) or right (-d face)
-#pragma unroll 1
-            for (int side = 1; side >= -1; side -= 2) {
-                const bool left = side > 0;
-                const S tw = left ? (a1 ? S(ALPHA) : S(BETA)) : (a1 ? S(BETA) : S(ALPHA));   // own trace weight
-                const S dBown = left ? tw * pen - S(0.5) * gq * sgn : -tw * pen - S(0.5) * gq * sgn;
-                const S wrow = left ? wf * tw : -wf * tw;
-                const bool inside = left ? coord + 1 < ext : coord > 0;
-                if (!inside) {
-                    if (left && d == 0) {   // anode face: r_Ano(c_Li, Phi^L) at the face point
-                        const S* Fo = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + cell;
-                        const S drA = Fo[0] * (dm == 0 ? tw : S(0.0)) + Fo[(int64_t)p.n_cell] * (dPL ? tw : S(0.0));
-                        if (!relax) col[0] += drA * S(p.kAno) * wrow;
-                        col[PHIL] += drA * S(p.F) * S(p.kAno) * wrow;
-                    }
-                    continue;
-                }
-                const int fc = left ? cell : cell - stride;        // voxel owning the face data
-                const int oc = left ? cell + stride : cell - stride;   // the other voxel
-                const S* Fd = face + (int64_t)((d * 4 + q) * SH::NFD) * p.n_cell + fc;
-                auto F = [&](int kk) { return Fd[(int64_t)kk * p.n_cell]; };
-                const S dgo = dg_at(face_slot(d, side, q), tw);   // own g at this face point
-                const S dHg = (left ? F(1) : F(2)) * dgo;
-                const S Hg = F(0), BL = F(3 + NL);
-                const S dBL = dPL ? dBown : S(0.0);
-                S fL = S(0.0);
+            for (int r = 0; r < NF; ++r) col[r] += dcs * Y[r];
 #pragma unroll
-                for (int m = 0; m < NL; ++m) {
-                    const S dB = m == dm ? dBown : S(0.0);
-                    const S dco = m == dm ? tw : S(0.0);
-                    const S dterm = dHg * F(3 + m) + Hg * dB;
-                    S f = relax ? S(0.0) : dterm * S(p.D0[m]);
-                    if (p.zc[m] != S(0.0)) {
-                        const int base = 4 + NL + 5 * SH::ci(m);
-                        const S dHm = left ? F(base + 1) * dgo + F(base + 2) * dco : F(base + 3) * dgo + F(base + 4) * dco;
-                        const S mterm = dHm * BL + F(base) * dBL;
-                        if (!relax) f += mterm * S(p.kappa_m[m]);
-                        fL += dterm * S(p.Kd[m]) + mterm * S(p.Km[m]);
-                    }
-                    col[m] += f * wrow;
-                }
-                col[PHIL] += fL * wrow;
-                if (st && dPS && g.phase[oc] == 1) col[PHIS] += dBown * S(p.kappa_s) * wrow;
-            }
+            for (int m = 0; m < NL; ++m)
+                if (m == c) { col[m] += Dd[m]; col[PHIL] += DL[m]; }
+        } else if (c == PHIL) {
+#pragma unroll
+            for (int r = 0; r < NF; ++r) col[r] += Pp[r];
+        } else if (c == PHIS) {
+            col[PHIS] += dS;
+        } else if (NS == 2 && st) {                              // a solid fraction: d eps_L = -1
+#pragma unroll
+            for (int r = 0; r < NF; ++r) col[r] -= X[r];
         }
 #pragma unroll
         for (int r = 0; r < NF; ++r) {
             double o = double(col[r]) * dt * p.rscale[r];
-            if (p.is_struct[r] && !st) o = r == c ? S(1.0) : S(0.0);
+            if (p.is_struct[r] && !st) o = r == c ? 1.0 : 0.0;
             B[r * NF + c] = o;
         }
     }
