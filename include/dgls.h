@@ -82,7 +82,8 @@ typedef struct {
     int32_t preconditioner;    /* 0: cell-block Jacobi; 1: two-stage (CPR): multigrid on the potential
                                   block, then block Jacobi on the remainder; 2: the additive form of the
                                   same two levels, no Jacobian-vector product inside (default) */
-    int32_t mg_cycles;         /* V-cycles of the potential multigrid per application (1) */
+    int32_t mg_cycles;         /* V-cycles of the potential multigrid per application (1; 1 to 16): a later cycle
+                                  starts from the current iterate of the finest level */
     int32_t precond_every;     /* rebuild the preconditioner every k-th Newton iteration of a step
                                   (0: once per step, at its first iteration) */
     double newton_stall_rtol;  /* a Newton solve whose line search can no longer reduce ||S R|| counts as

@@ -226,6 +226,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         return DG_ERR_ARG;
     if (prm->reorth < 0 || prm->reorth > 2) return DG_ERR_ARG;
     if (prm->species_mg < 0 || prm->species_mg > 2) return DG_ERR_ARG;
+    if (prm->preconditioner != 0 && (prm->mg_cycles < 1 || prm->mg_cycles > 16)) return DG_ERR_ARG;
     if (!(prm->newton_stall_rtol >= 0.0)) return DG_ERR_ARG;
     const int64_t ncell64 = (int64_t)s->nx * s->ny * s->nz;
     if (ncell64 > 2000000000LL) return DG_ERR_ARG;

@@ -643,16 +643,18 @@ cudaError_t mg_setup(const LaunchCtx& Lc, const DevParams& p, const Geo& g, cons
     return mg_hierarchy(Lc, lv);
 }
 
-static void vcycle(const LaunchCtx& Lc, std::vector<MGLevel>& lv, size_t l) {
+// One V-cycle on level l.  warm: start from the current x of level l (a repeated cycle on the finest
+// level); otherwise from zero (the first cycle, and every coarse level, which solves for a correction).
+static void vcycle(const LaunchCtx& Lc, std::vector<MGLevel>& lv, size_t l, bool warm = false) {
     MGLevel& L = lv[l];
     const double w = 0.8;
     if (l + 1 == lv.size()) {
-        k_mg_dense_solve<<<1, 128, 0, Lc.st>>>(L);
+        k_mg_dense_solve<<<1, 128, 0, Lc.st>>>(L);   // exact: a warm start changes nothing
         *Lc.counter += 1;
         return;
     }
     const int g = nb(L.n, 256);
-    k_mg_jacobi<<<g, 256, 0, Lc.st>>>(L, L.x, L.xt, w, 1);
+    k_mg_jacobi<<<g, 256, 0, Lc.st>>>(L, L.x, L.xt, w, warm ? 0 : 1);
     k_mg_jacobi<<<g, 256, 0, Lc.st>>>(L, L.xt, L.x, w, 0);
     k_mg_restrict<<<nb(lv[l + 1].n, 256), 256, 0, Lc.st>>>(L, lv[l + 1]);
     *Lc.counter += 3;
@@ -670,8 +672,7 @@ cudaError_t cpr_stage1(const LaunchCtx& Lc, const DevParams& p, const Geo& g, st
     MGLevel& L0 = lv[0];
     k_cpr_restrict<S><<<nb(p.n_cell, 256), 256, 0, Lc.st>>>(p, g, v, L0);
     *Lc.counter += 1;
-    (void)cycles;
-    vcycle(Lc, lv, 0);
+    for (int c = 0; c < cycles; ++c) vcycle(Lc, lv, 0, c > 0);
     const int nn = p.order == 1 ? 8 : 1;
     k_cpr_prolong<S><<<nb((int64_t)p.n_cell * nn, 256), 256, 0, Lc.st>>>(p, g, L0, y);
     *Lc.counter += 1;

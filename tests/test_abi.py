@@ -45,3 +45,21 @@ def test_params_default_and_argument_checks(lib):
     assert lib.dg_params_default(C.byref(bad), 7, 0) == dgls.ERR_ARG
     h = C.c_void_p()
     assert lib.dg_setup(None, C.byref(p), None, C.byref(h)) == dgls.ERR_ARG
+
+
+def test_setup_rejects_out_of_range_solver_switches(lib):
+    """Argument checks that dg_setup makes before it touches the device: Gram-Schmidt rule,
+    species coarse level, V-cycles per application."""
+    import ctypes as C
+
+    import numpy as np
+
+    ph = np.zeros((2, 2, 4), dtype=np.uint8)
+    ph[:, :, 0] = 1
+    s = dgls.Structure(4, 2, 2, 1e-6, ph.ctypes.data_as(C.POINTER(C.c_uint8)))
+    for field, value in (("reorth", 3), ("species_mg", 3), ("species_mg", -1), ("mg_cycles", 0), ("mg_cycles", 17)):
+        p = dgls.default_params(dgls.TRADEOFF, 1)
+        setattr(p, field, value)
+        h = C.c_void_p()
+        assert lib.dg_setup(C.byref(s), C.byref(p), None, C.byref(h)) == dgls.ERR_ARG, (field, value)
+        assert not h.value
