@@ -151,6 +151,21 @@ def oracle_sample(a, budget_s=15.0):
                        f"in {el:.1f} s, one core"), el, n_eval
 
 
+def reduce_over_ranks(dist, elapsed_ms, units, device):
+    """Whole-job figures of a run over several ranks, each stepping its own replica of the cell
+    (weak scaling): the slowest rank's time and the units processed by all ranks.  dist is
+    torch.distributed (initialised) or None for a single process."""
+    if dist is None:
+        return elapsed_ms, units
+    import torch
+
+    tt = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    uu = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(uu.item())
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -258,13 +273,7 @@ def main():
     ctx.profile(False)
     evals = sum(i.residual_evals + i.jvp_evals for i in infos)
     units = evals * N
-    if dist:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-        uu = torch.tensor([float(units)], device="cuda")
-        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
-        units = uu.item()
+    elapsed_ms, units = reduce_over_ranks(dist, elapsed_ms, units, "cuda")
     value = units / (elapsed_ms / 1e3) / 1e9
 
     # ---- dominant kernel roofline (live CUDA-event timing inside the timed steps).  The FP64
@@ -299,19 +308,22 @@ def main():
 
     # ---- end to end through the host-buffer C-ABI call
     e2e = None
-    if not a.no_e2e and rank == 0:
+    if not a.no_e2e:   # every rank, like the device-timed steps; whole-job figures as for value
         zn_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
         zn_h.copy_(zn)
         z_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
         zn_np, z_np = zn_h.numpy(), z_h.numpy()
         ev = 0
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(a.steps):
             st, info = ctx.step_host(zn_np, z_np, t, dt, check=False)
             ev += info.residual_evals + info.jvp_evals
-        el = time.perf_counter() - t0
-        e2e = {"value": ev * N / el / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
+        el_ms, e2e_units = reduce_over_ranks(dist, 1e3 * (time.perf_counter() - t0), ev * N, "cuda")
+        e2e = {"value": e2e_units / (el_ms / 1e3) / 1e9, "unit": "GDoF/s",
+               "h2d_bytes_per_step": 8 * N * world, "d2h_bytes_per_step": 8 * N * world}
 
     # ---- the same step with the mixed-precision Krylov loop (FP32 JVP, basis and block Jacobi
     # inside the FP64 Newton iteration), and its distance from the FP64 result
