@@ -17,7 +17,8 @@ import time
 import numpy as np
 
 
-def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, species_mg=2, t_end=0.0, h=1e-6):
+def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, species_mg=2, t_end=0.0, h=1e-6,
+        stall_rtol=None):
     import torch
 
     from . import dgls, inputs
@@ -29,7 +30,8 @@ def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, 
             phase = ph
             break
     prm = dgls.default_params(dgls.TRADEOFF, order, f_C=f_C, eps_struct=1.0 - porosity,
-                              precision=dgls.MIXED if precision == "mixed" else dgls.FP64, species_mg=species_mg)
+                              precision=dgls.MIXED if precision == "mixed" else dgls.FP64, species_mg=species_mg,
+                              **({"newton_stall_rtol": stall_rtol} if stall_rtol is not None else {}))
     ctx = dgls.Context(phase, h, prm)
     z = ctx.new_state()
     ctx.equilibrium_state(z)
@@ -43,7 +45,7 @@ def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, 
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     out = {"n": n, "order": order, "porosity": porosity, "corr_len": corr_len, "f_C": f_C, "precision": precision,
-           "limiter": bool(limiter), "species_mg": species_mg,
+           "limiter": bool(limiter), "species_mg": species_mg, "newton_stall_rtol": prm.newton_stall_rtol,
            "n_dof": ctx.n_dof, "status": res["status"], "steps": int(len(res["t"])), "attempts": res["attempts"],
            "failures": res["failures"], "reached_cutoff": bool(len(res["U_cell"]) and res["U_cell"][-1] <= 1.9),
            "t_end_s": float(res["t"][-1]) if len(res["t"]) else 0.0,
@@ -82,15 +84,18 @@ def main():
     ap.add_argument("--species-mg", type=int, default=2, choices=[0, 1, 2],
                     help="species coarse level of the preconditioner: off, on, on at large dt (default)")
     ap.add_argument("--t-end", type=float, default=0.0, help="stop at this time in s (0: at the cut-off)")
+    ap.add_argument("--stall-rtol", type=float, default=None,
+                    help="Newton: a stalled line search counts as converged below this fraction of the initial "
+                         "scaled residual (library default 1e-8)")
     ap.add_argument("--no-curve", action="store_true", help="print the summary without the curve arrays")
     ap.add_argument("--compare", action="store_true", help="also run the other precision and compare")
     a = ap.parse_args()
     lim = a.order == 1 and not a.no_limiter
-    r = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, a.precision, a.seed, a.max_steps, lim, a.species_mg, a.t_end)
+    r = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, a.precision, a.seed, a.max_steps, lim, a.species_mg, a.t_end, stall_rtol=a.stall_rtol)
     out = {"run": r}
     if a.compare:
         other = "mixed" if a.precision == "fp64" else "fp64"
-        r2 = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, other, a.seed, a.max_steps, lim, a.species_mg, a.t_end)
+        r2 = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, other, a.seed, a.max_steps, lim, a.species_mg, a.t_end, stall_rtol=a.stall_rtol)
         out["other"] = r2
         out["comparison"] = curve_diff(r, r2)
     if a.no_curve:
