@@ -1,7 +1,8 @@
 """A complete galvanostatic discharge on one synthetic structure: Tab. 6 equilibrium state, the
 parabolic relaxation of Sec. 2.8 (40 steps of 0.1 s), then the naive controller (Fig. 4) at the
 given C-rate down to the 1.9 V cut-off; DG1 with the vertex-based slope limiter after each accepted
-step (App. B), unless --no-limiter.  Prints one JSON line with the discharge curve (time, cell
+step (App. B), unless --no-limiter; a Newton solve whose line search stalls within 1e-7 of its initial
+scaled residual counts as converged (--stall-rtol).  Prints one JSON line with the discharge curve (time, cell
 voltage U_cell (Eq. A1), specific capacity c_m (App. B)), the step statistics and the wall time;
 with --compare, the same discharge in the other precision and the largest relative difference of
 the two curves at the common accepted times.
@@ -84,9 +85,10 @@ def main():
     ap.add_argument("--species-mg", type=int, default=2, choices=[0, 1, 2],
                     help="species coarse level of the preconditioner: off, on, on at large dt (default)")
     ap.add_argument("--t-end", type=float, default=0.0, help="stop at this time in s (0: at the cut-off)")
-    ap.add_argument("--stall-rtol", type=float, default=None,
+    ap.add_argument("--stall-rtol", type=float, default=1e-7,
                     help="Newton: a stalled line search counts as converged below this fraction of the initial "
-                         "scaled residual (library default 1e-8)")
+                         "scaled residual (1e-7 here, one decade above the rounding level measured on DG1 "
+                         "mid-discharge states; the library default is 1e-8)")
     ap.add_argument("--no-curve", action="store_true", help="print the summary without the curve arrays")
     ap.add_argument("--compare", action="store_true", help="also run the other precision and compare")
     a = ap.parse_args()
