@@ -19,14 +19,14 @@ import numpy as np
 
 
 def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, species_mg=2, t_end=0.0, h=1e-6,
-        stall_rtol=None):
+        stall_rtol=None, single_cluster=False):
     import torch
 
     from . import dgls, inputs
 
     phase = None
     for s in range(seed, seed + 50):
-        ph = inputs.make_structure(n, porosity, corr_len, s)
+        ph = inputs.make_structure(n, porosity, corr_len, s, single_cluster=single_cluster)
         if np.any(ph[:, :, 0] == inputs.STRUCT):
             phase = ph
             break
@@ -47,6 +47,7 @@ def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, 
     t2 = time.perf_counter()
     out = {"n": n, "order": order, "porosity": porosity, "corr_len": corr_len, "f_C": f_C, "precision": precision,
            "limiter": bool(limiter), "species_mg": species_mg, "newton_stall_rtol": prm.newton_stall_rtol,
+           "single_cluster": bool(single_cluster),
            "n_dof": ctx.n_dof, "status": res["status"], "steps": int(len(res["t"])), "attempts": res["attempts"],
            "failures": res["failures"], "reached_cutoff": bool(len(res["U_cell"]) and res["U_cell"][-1] <= 1.9),
            "t_end_s": float(res["t"][-1]) if len(res["t"]) else 0.0,
@@ -90,14 +91,18 @@ def main():
                          "scaled residual (1e-7 here, one decade above the rounding level measured on DG1 "
                          "mid-discharge states; the library default is 1e-8)")
     ap.add_argument("--no-curve", action="store_true", help="print the summary without the curve arrays")
+    ap.add_argument("--single-cluster", action="store_true",
+                    help="keep only the largest structure cluster touching the current collector")
     ap.add_argument("--compare", action="store_true", help="also run the other precision and compare")
     a = ap.parse_args()
     lim = a.order == 1 and not a.no_limiter
-    r = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, a.precision, a.seed, a.max_steps, lim, a.species_mg, a.t_end, stall_rtol=a.stall_rtol)
+    r = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, a.precision, a.seed, a.max_steps, lim, a.species_mg, a.t_end, stall_rtol=a.stall_rtol,
+            single_cluster=a.single_cluster)
     out = {"run": r}
     if a.compare:
         other = "mixed" if a.precision == "fp64" else "fp64"
-        r2 = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, other, a.seed, a.max_steps, lim, a.species_mg, a.t_end, stall_rtol=a.stall_rtol)
+        r2 = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, other, a.seed, a.max_steps, lim, a.species_mg, a.t_end, stall_rtol=a.stall_rtol,
+            single_cluster=a.single_cluster)
         out["other"] = r2
         out["comparison"] = curve_diff(r, r2)
     if a.no_curve:

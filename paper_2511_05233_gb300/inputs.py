@@ -59,10 +59,11 @@ def _label6(mask: np.ndarray):
 
 
 def make_structure(n, porosity: float, corr_len: float, seed: int, n_sep: int | None = None,
-                   clean: bool = True) -> np.ndarray:
+                   clean: bool = True, single_cluster: bool = False) -> np.ndarray:
     """Phase map uint8[nz, ny, nx] (x fastest) for a cubic (int n) or (nx, ny, nz) grid.
 
-    Phases: 0 pore, 1 structure, 2 separator.
+    Phases: 0 pore, 1 structure, 2 separator.  single_cluster: keep only the largest structure
+    cluster touching the current collector (x = 0); smaller ones that touch it too become pore.
     """
     if np.isscalar(n):
         nx = ny = nz = int(n)
@@ -79,16 +80,21 @@ def make_structure(n, porosity: float, corr_len: float, seed: int, n_sep: int | 
     phase = np.full((nz, ny, nx), SEP, dtype=np.uint8)
     phase[:, :, :ncat] = np.where(cat < thr, PORE, STRUCT).astype(np.uint8)
     if clean:
-        phase = clean_connectivity(phase)
+        phase = clean_connectivity(phase, single_cluster)
     return phase
 
 
-def clean_connectivity(phase: np.ndarray) -> np.ndarray:
-    """Flip floating structure clusters to pore and isolated pore clusters to structure."""
+def clean_connectivity(phase: np.ndarray, single_cluster: bool = False) -> np.ndarray:
+    """Flip floating structure clusters to pore and isolated pore clusters to structure; with
+    single_cluster, also every structure cluster but the largest of those touching x = 0."""
     phase = phase.copy()
     lab, nlab = _label6(phase == STRUCT)
     if nlab:
         touching = np.unique(lab[:, :, 0])
+        touching = touching[touching > 0]
+        if single_cluster and touching.size > 1:
+            sizes = np.bincount(lab.ravel(), minlength=nlab + 1)
+            touching = touching[[int(np.argmax(sizes[touching]))]]
         keep = np.zeros(nlab + 1, dtype=bool)
         keep[touching] = True
         keep[0] = False

@@ -397,6 +397,25 @@ def test_structure_generator():
     assert set(np.unique(lab[:, :, 0])) - {0} == set(range(1, n + 1))
 
 
+def test_structure_single_cluster_option():
+    """single_cluster keeps the largest structure cluster touching the collector and turns every
+    other structure voxel to pore (10^3, seed 3 has several clusters on the collector); off by
+    default, so the default structures are unchanged."""
+    from scipy import ndimage
+
+    six = ndimage.generate_binary_structure(3, 1)
+    a = inputs.make_structure(10, 0.5, 4.0, 3)
+    b = inputs.make_structure(10, 0.5, 4.0, 3, single_cluster=True)
+    lab_a, n_a = ndimage.label(a == inputs.STRUCT, structure=six)
+    lab_b, n_b = ndimage.label(b == inputs.STRUCT, structure=six)
+    assert n_a > 1 and n_b == 1
+    sizes = np.bincount(lab_a.ravel())[1:]
+    largest = lab_a == 1 + int(np.argmax(sizes))
+    assert np.array_equal(b == inputs.STRUCT, largest)
+    assert np.all((a != b) <= ((a == inputs.STRUCT) & (b == inputs.PORE)))
+    assert np.array_equal(inputs.make_structure(32, 0.6, 4.0, 1), inputs.make_structure(32, 0.6, 4.0, 1, single_cluster=False))
+
+
 @pytest.mark.parametrize("level,expect", [(1e-9, True), (1e-6, False)])
 def test_newton_stall_rule(monkeypatch, level, expect):
     """A Newton solve that stagnates at a residual floor is converged if the floor is below 1e-8 of
