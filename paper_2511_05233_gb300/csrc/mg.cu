@@ -310,14 +310,18 @@ __global__ void k_mg_prolong(MGLevel F, MGLevel C) {
 
 // coarsest level (n <= 64 voxels, m = 2n <= 128 unknowns): dense inverse at set-up by in-place
 // Gauss-Jordan elimination in shared memory (m x m doubles, at most 128 KB) in one thread block of
-// 1024 threads; the operator is a symmetric M-matrix, so no pivoting is needed.  One dense
-// matrix-vector product per V-cycle.
+// 1024 threads.  A connected, grounded operator is a symmetric M-matrix and needs no pivoting, but
+// the structure can hold parts that are neither: a voxel whose Phi^S has no structure neighbour and
+// no surface left (a_V = 0) has an empty row, and a cluster that nothing grounds is singular.  So a
+// row whose diagonal is not positive becomes an identity row, and a pivot that has lost all but
+// rounding of its row's diagonal leaves its unknown out of the coarse correction (row and column of
+// the inverse set to zero) instead of dividing by it.  One dense matrix-vector product per V-cycle.
 constexpr int DENSE_THREADS = 1024;
 constexpr int DENSE_MAX = 128;
 
 __global__ void __launch_bounds__(DENSE_THREADS) k_mg_dense_build(MGLevel L) {
     extern __shared__ double A[];            // [m][m] row-major: L fields 0..n-1, S fields n..2n-1
-    __shared__ double rowk[DENSE_MAX], colk[DENSE_MAX];
+    __shared__ double rowk[DENSE_MAX], colk[DENSE_MAX], diag0[DENSE_MAX];
     const int m = 2 * L.n;
     const int tid = threadIdx.x;
     for (int e = tid; e < m * m; e += DENSE_THREADS) A[e] = 0.0;
@@ -354,12 +358,20 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_mg_dense_build(MGLevel L) {
             for (int c = 0; c < m; ++c) row[c] = 0.0;
             row[r] = 1.0;
         }
+        // an empty row (no conductance, no coupling, no diagonal term) has an empty column too
+        // (the operator is symmetric): make it an identity row
+        if (!(row[r] > 0.0)) {
+            for (int c = 0; c < m; ++c) row[c] = 0.0;
+            row[r] = 1.0;
+        }
+        diag0[r] = row[r];
     }
     __syncthreads();
     // pivot k: row k <- row k / p (entry k <- 1/p); row i != k <- row i - A[i][k] row k (entry k <- -A[i][k]/p)
     for (int kk = 0; kk < m; ++kk) {
         if (tid < m) {
-            const double pinv = 1.0 / A[(int64_t)kk * m + kk];
+            const double piv = A[(int64_t)kk * m + kk];
+            const double pinv = (piv > 1e-14 * diag0[kk]) ? 1.0 / piv : 0.0;
             rowk[tid] = tid == kk ? pinv : A[(int64_t)kk * m + tid] * pinv;
             colk[tid] = A[(int64_t)tid * m + kk];
         }
@@ -620,9 +632,10 @@ static cudaError_t mg_hierarchy(const LaunchCtx& Lc, std::vector<MGLevel>& lv) {
     }
     const int m = 2 * lv.back().n;
     const size_t smem = (size_t)m * m * sizeof(double);
-    // opt in to more than 48 KB of dynamic shared memory (once per process; thread-safe static init)
-    static const cudaError_t attr = cudaFuncSetAttribute(k_mg_dense_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         DENSE_MAX * DENSE_MAX * (int)sizeof(double));
+    // opt in to more than 48 KB of dynamic shared memory; the attribute belongs to the current
+    // device, so it is set on every build (a host call, cheap next to the build itself)
+    const cudaError_t attr = cudaFuncSetAttribute(k_mg_dense_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  DENSE_MAX * DENSE_MAX * (int)sizeof(double));
     if (attr != cudaSuccess) return attr;
     k_mg_dense_build<<<1, DENSE_THREADS, smem, Lc.st>>>(lv.back());
     *Lc.counter += 1;

@@ -92,6 +92,47 @@ def run_one(req, stream=None, precision=None, keep_state=False):
     return out
 
 
+class Admission:
+    """Host-side admission of the serving loop: first come, first served into free slots while the
+    request's workspace fits in what is left of the HBM budget.  A request that could never fit
+    (its workspace alone exceeds the whole budget) is rejected when it arrives, so it cannot block
+    the queue behind it."""
+
+    def __init__(self, slots, budget, size_of):
+        self.free_slots = slots
+        self.budget = budget
+        self.total = budget
+        self.size_of = size_of
+        self.queue = []
+        self.rejected = []
+
+    def arrive(self, req):
+        need = self.size_of(req)
+        if need > self.total:
+            req.result = {"status": f"rejected: workspace {need} B exceeds the HBM budget {self.total} B"}
+            self.rejected.append(req)
+            return False
+        heapq.heappush(self.queue, (req.arrival, req.rid, req, need))
+        return True
+
+    def admit(self):
+        """Pop every request that fits now: [(req, need)]."""
+        out = []
+        while self.queue and self.free_slots > 0 and self.queue[0][3] <= self.budget:
+            _, _, req, need = heapq.heappop(self.queue)
+            self.free_slots -= 1
+            self.budget -= need
+            out.append((req, need))
+        return out
+
+    def release(self, need):
+        self.free_slots += 1
+        self.budget += need
+
+    def idle(self):
+        return not self.queue
+
+
 class _null:
     def __enter__(self):
         return None
@@ -107,7 +148,7 @@ def serve(requests, slots=4, hbm_budget=150 << 30, time_scale=1.0, precision=Non
     t0 = time.perf_counter()
     pending = sorted(requests, key=lambda r: r.arrival)
     lock = threading.Condition()
-    state = {"free_slots": slots, "budget": hbm_budget, "running": 0}
+    adm = Admission(slots, hbm_budget, workspace_estimate)
     streams = [torch.cuda.Stream() for _ in range(slots)]
     free_streams = list(range(slots))
     threads = []
@@ -120,34 +161,25 @@ def serve(requests, slots=4, hbm_budget=150 << 30, time_scale=1.0, precision=Non
             req.result = {"status": f"error: {e}"}
         req.end = time.perf_counter() - t0
         with lock:
-            state["free_slots"] += 1
-            state["budget"] += need
+            adm.release(need)
             free_streams.append(sidx)
             lock.notify_all()
 
-    queue = []
     i = 0
-    while i < len(pending) or queue:
+    while i < len(pending) or not adm.idle():
         now = time.perf_counter() - t0
-        while i < len(pending) and pending[i].arrival * time_scale <= now:
-            heapq.heappush(queue, (pending[i].arrival, pending[i].rid, pending[i]))
-            i += 1
-        admitted = False
         with lock:
-            while queue:
-                req = queue[0][2]
-                need = workspace_estimate(req)
-                if state["free_slots"] == 0 or need > state["budget"]:
-                    break
-                heapq.heappop(queue)
-                state["free_slots"] -= 1
-                state["budget"] -= need
+            while i < len(pending) and pending[i].arrival * time_scale <= now:
+                if not adm.arrive(pending[i]):
+                    pending[i].start = pending[i].end = now
+                i += 1
+            started = adm.admit()
+            for req, need in started:
                 sidx = free_streams.pop()
                 th = threading.Thread(target=worker, args=(req, sidx, need), daemon=True)
                 threads.append(th)
                 th.start()
-                admitted = True
-            if not admitted:
+            if not started:
                 wait = 0.01
                 if i < len(pending):
                     wait = max(0.0, min(0.05, pending[i].arrival * time_scale - now))
