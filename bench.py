@@ -74,6 +74,35 @@ LIN_JVP_DG1_FLOP_PER_DOF = 90.44
 LIN_JVP_DG1_DRAM_BYTES_PER_DOF = 263.8
 
 
+# kernels behind the profiled "jvp" category of each precision (the Krylov-loop products)
+JVP_KERNELS = {"fp64": "jvp (linearised DG1 apply: k_lin_g, k_lin_nodes_apply, k_lin_nodes_diag, "
+                       "k_lin_face_flux, k_lin_line_gather)",
+               "mixed": "jvp (fused matrix-free FP32 DG1 product: k_jvp1_fused)"}
+# DRAM bytes per unknown of one fused FP32 product (ncu dram__bytes_read.sum + write.sum at 64^3 /
+# unknowns), or None when the kernel has changed since the counters were taken
+FUSED_F32_DRAM_BYTES_PER_DOF = None
+
+
+def kernel_rates(prof, N, n_pot, hbm, precision):
+    """Residual and Jacobian-vector product rates from the per-category CUDA-event times of the
+    timed steps, each against HBM with the algorithmic bytes of one evaluation: the residual reads
+    z and z^n and writes R (24 B per time-dependent unknown, 16 B per potential unknown, which has
+    no z^n term); the product reads z and v and writes J v (24 B per unknown in FP64, 12 B in FP32)."""
+    out = {}
+    for cat in ("residual", "jvp"):
+        ms, calls = prof[cat]
+        if not calls:
+            continue
+        avg = ms / calls
+        if cat == "residual":
+            bytes_ = 24.0 * N - 8.0 * n_pot
+        else:
+            bytes_ = (24.0 if precision == "fp64" else 12.0) * N
+        out[cat] = {"avg_ms": avg, "calls": calls, "gdof_s": N / (avg / 1e3) / 1e9, "bytes_per_dof": bytes_ / N,
+                    "hbm_gbs": bytes_ / (avg / 1e3) / 1e9, "hbm_frac": bytes_ / (avg / 1e3) / 1e9 / hbm}
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -122,33 +151,86 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def oracle_sample(a, budget_s=15.0):
-    """The CPU oracle (numpy, one core) evaluating residuals and complex-step JVPs of the same
-    model on a 24^3 crop of the workload structure, repeated for about budget_s seconds."""
-    from oracle import chemistry as ch, init, lis, newton
-    from paper_2511_05233_gb300 import inputs
+_ORACLE_CASES = {}
 
-    phase = make_inputs(a)
-    m = min(24, a.n)
-    crop = inputs.clean_connectivity(phase[:m, :m, :m].copy())
-    if not np.any(crop[:, :, 0] == inputs.STRUCT):
-        crop[:, :, 0] = inputs.STRUCT
-    crop[:, :, -max(2, m // 8):] = inputs.SEP
-    chem = ch.tradeoff() if a.chem == "tradeoff" else ch.reduced3()
-    model = lis.Model(chem, order=a.order, f_C=WORKLOAD["f_C"], eps_struct=1 - WORKLOAD["porosity"])
-    grid = lis.Grid(crop, WORKLOAD["h"])
-    z0 = init.uniform_state(model, grid, init.equilibrium_fields(model))
-    z = init.perturb(model, grid, z0, inputs.uniform_noise(z0.size, WORKLOAD["noise_seed"]))
-    v = inputs.normal_noise(z.size, 5)
-    n_eval, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
+
+def _oracle_worker(args):
+    """One host process of the CPU baseline: residual + complex-step JVP evaluations of the oracle on
+    its own crop of the workload structure, repeated until budget_s has passed.  A top-level
+    function so that a spawn pool can run it."""
+    a_n, a_order, a_chem, m, k0, budget_s = args
+    from oracle import newton
+
+    key = (a_n, a_order, a_chem, m, k0)
+    if key not in _ORACLE_CASES:    # set up once per process (the pool's processes serve every step)
+        from oracle import chemistry as ch, init, lis
+        from paper_2511_05233_gb300 import inputs
+
+        phase = inputs.make_structure(a_n, WORKLOAD["porosity"], WORKLOAD["corr_len"], WORKLOAD["structure_seed"])
+        crop = inputs.clean_connectivity(phase[k0:k0 + m, :m, :m].copy())
+        if not np.any(crop[:, :, 0] == inputs.STRUCT):
+            crop[:, :, 0] = inputs.STRUCT
+        crop[:, :, -max(2, m // 8):] = inputs.SEP
+        chem = ch.tradeoff() if a_chem == "tradeoff" else ch.reduced3()
+        model = lis.Model(chem, order=a_order, f_C=WORKLOAD["f_C"], eps_struct=1 - WORKLOAD["porosity"])
+        grid = lis.Grid(crop, WORKLOAD["h"])
+        z0 = init.uniform_state(model, grid, init.equilibrium_fields(model))
+        z = init.perturb(model, grid, z0, inputs.uniform_noise(z0.size, WORKLOAD["noise_seed"]))
+        _ORACLE_CASES[key] = (model, grid, z0, z, inputs.normal_noise(z.size, 5))
+    model, grid, z0, z, v = _ORACLE_CASES[key]
+    from oracle import lis
+    n_res = n_jvp = 0
+    t_res = t_jvp = 0.0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s or n_res == 0:
+        t1 = time.perf_counter()
         lis.residual(model, grid, z, z0, WORKLOAD["dt"], WORKLOAD["dt"])
+        t2 = time.perf_counter()
         newton.jvp(model, grid, z, z0, WORKLOAD["dt"], WORKLOAD["dt"], v)
-        n_eval += 2
-    el = time.perf_counter() - t0
-    return dict(value=n_eval * z.size / el / 1e9, unit="GDoF/s", cores=1, kind="oracle",
-                sample=f"{n_eval} residual/JVP evaluations of the oracle on a {m}^3 crop ({z.size} unknowns) "
-                       f"in {el:.1f} s, one core"), el, n_eval
+        t3 = time.perf_counter()
+        n_res += 1
+        n_jvp += 1
+        t_res += t2 - t1
+        t_jvp += t3 - t2
+    return dict(dof=int(z.size), n_res=n_res, n_jvp=n_jvp, t_res=t_res, t_jvp=t_jvp, wall=time.perf_counter() - t0)
+
+
+def oracle_pool(procs=None):
+    """A spawn process pool with one process per host core for the CPU oracle (spawn: safe to start
+    after CUDA is initialised in this process)."""
+    import multiprocessing as mp
+
+    return mp.get_context("spawn").Pool(procs or os.cpu_count() or 1)
+
+
+def oracle_sample(a, budget_s=15.0, pool=None, m=32):
+    """The CPU oracle (numpy, as it stands) timed on the host cores: one process per core, each
+    evaluating residuals and complex-step JVPs of the same model on its own m^3 crop of the workload
+    structure (crops at different z offsets) for about budget_s seconds.  value = unknowns evaluated
+    by all processes / wall time."""
+    own = pool is None
+    if own:
+        pool = oracle_pool()
+    procs = pool._processes
+    m = min(m, a.n)
+    offs = [(i * m) % max(1, a.n - m + 1) for i in range(procs)]
+    try:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(a.n, a.order, a.chem, m, k0, budget_s) for k0 in offs], chunksize=1)
+        wall = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    evals = sum(r["n_res"] + r["n_jvp"] for r in res)
+    units = sum((r["n_res"] + r["n_jvp"]) * r["dof"] for r in res)
+    dof = res[0]["dof"]
+    one_core = {"residual_gdof_s": float(np.mean([r["dof"] * r["n_res"] / r["t_res"] for r in res]) / 1e9),
+                "jvp_gdof_s": float(np.mean([r["dof"] * r["n_jvp"] / r["t_jvp"] for r in res]) / 1e9)}
+    return dict(value=units / wall / 1e9, unit="GDoF/s", cores=procs, kind="oracle",
+                sample=f"{evals} residual/JVP evaluations of the oracle by {procs} processes, each on its own "
+                       f"{m}^3 crop of the {a.n}^3 workload structure ({dof} unknowns), in {wall:.1f} s wall",
+                per_core=one_core, host_cpu_count=os.cpu_count()), wall, evals
 
 
 def reduce_over_ranks(dist, elapsed_ms, units, device):
@@ -169,23 +251,26 @@ def reduce_over_ranks(dist, elapsed_ms, units, device):
 def run_reference(a, rank, world):
     if rank != 0:
         return
-    total_el, total_n, dof = 0.0, 0, None
-    for _ in range(a.warmup):
-        oracle_sample(a, budget_s=2.0)
-    vals = []
-    t_all = time.perf_counter()
-    for _ in range(a.steps):
-        cb, el, n = oracle_sample(a, budget_s=10.0)
-        vals.append(cb["value"])
-        total_el += el
-        total_n += n
-    ms = 1e3 * (time.perf_counter() - t_all) / max(a.steps, 1)
+    pool = oracle_pool()
+    try:
+        for _ in range(a.warmup):        # the first one also sets every process up
+            oracle_sample(a, budget_s=1.0, pool=pool)
+        vals = []
+        t_all = time.perf_counter()
+        for _ in range(a.steps):
+            cb, el, n = oracle_sample(a, budget_s=5.0, pool=pool)
+            vals.append(cb["value"])
+        ms = 1e3 * (time.perf_counter() - t_all) / max(a.steps, 1)
+    finally:
+        pool.close()
+        pool.join()
     value = float(np.mean(vals))
     line = {"impl": "reference", "metric": "residual/JVP GDoF/s", "value": value, "unit": "GDoF/s",
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(a),
-            "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"], "per_core": cb["per_core"]},
             "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -280,30 +365,26 @@ def main():
     # linearised DG1 product is FP64-ALU-bound on GB300 (FP64 pipe 83-89 % busy, DRAM below half),
     # so it is set against the FP64 peak; other categories against HBM bandwidth.
     peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "of measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "of fallback (6.8 TB/s)"
+    n_pot = ctx.lengths[ctx.n_fields - 2] + ctx.lengths[ctx.n_fields - 1]
+    kern = kernel_rates(prof, N, n_pot, hbm, a.precision)
     cat = max(("residual", "jvp", "precond_build", "precond_apply", "krylov"), key=lambda k: prof[k][0])
-    ms_tot, calls = prof[cat]
     roof = None
-    if calls:
-        avg_ms = ms_tot / calls
+    if cat in kern:
+        k = kern[cat]
+        roof = {"kernel": {"residual": "residual", "jvp": JVP_KERNELS[a.precision]}[cat], "bound": "hbm",
+                "achieved": k["hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": k["hbm_frac"],
+                "traffic": None, "bytes_per_dof": k["bytes_per_dof"], "avg_launch_ms": k["avg_ms"],
+                "peak_source": hbm_src}
         if cat == "jvp" and a.order == 1 and a.chem == "tradeoff" and a.precision == "fp64":
-            achieved = LIN_JVP_DG1_FLOP_PER_DOF * N / (avg_ms / 1e3) / 1e9
-            roof = {"kernel": "jvp (linearised DG1 apply: k_lin_g, k_lin_nodes_apply, k_lin_face_flux, "
-                              "k_lin_line_gather)",
-                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": achieved / FP64_PEAK_GFLOPS,
-                    "traffic": LIN_JVP_DG1_DRAM_BYTES_PER_DOF * N if LIN_JVP_DG1_DRAM_BYTES_PER_DOF else None,
-                    "flop_per_dof": LIN_JVP_DG1_FLOP_PER_DOF, "avg_launch_ms": avg_ms,
-                    "peak_source": "derived FP64 peak (152 SMs x 4 FLOP/clk x 2.07 GHz)",
-                    "hbm_frac_of_measured": (LIN_JVP_DG1_DRAM_BYTES_PER_DOF * N / (avg_ms / 1e3) / 1e9
-                                             / peaks.get("hbm_gbs", 6800.0)) if LIN_JVP_DG1_DRAM_BYTES_PER_DOF else None}
-        else:
-            bpd = {"residual": 24.0, "jvp": 24.0 if a.precision == "fp64" else 12.0}.get(cat)
-            if bpd:
-                achieved = bpd * N / (avg_ms / 1e3) / 1e9
-                pk = peaks.get("hbm_gbs", 6800.0)
-                roof = {"kernel": cat, "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
-                        "frac": achieved / pk, "traffic": None, "bytes_per_dof": bpd, "avg_launch_ms": avg_ms,
-                        "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+            # the FP64 product is bound by the FP64 pipe on this part, far below its HBM bytes
+            gfl = LIN_JVP_DG1_FLOP_PER_DOF * N / (k["avg_ms"] / 1e3) / 1e9
+            roof["traffic"] = LIN_JVP_DG1_DRAM_BYTES_PER_DOF * N if LIN_JVP_DG1_DRAM_BYTES_PER_DOF else None
+            roof["fp64_pipe"] = {"achieved_gflops": gfl, "peak_gflops": FP64_PEAK_GFLOPS,
+                                 "frac": gfl / FP64_PEAK_GFLOPS, "flop_per_dof": LIN_JVP_DG1_FLOP_PER_DOF,
+                                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz "
+                                                "(a DFMA probe measured 1200 GFLOP/s on the same part)"}
     breakdown = {k: {"ms": v[0], "calls": v[1]} for k, v in prof.items()}
 
     # ---- end to end through the host-buffer C-ABI call
@@ -360,10 +441,19 @@ def main():
             ref = torch.cat([z64[lay[f][0]:lay[f][0] + lay[f][1]] for f in fields])
             got = torch.cat([z32[lay[f][0]:lay[f][0] + lay[f][1]] for f in fields])
             errs[kname] = float((got - ref).abs().max() / ref.abs().max())
+        k32 = kernel_rates(prof32, N, n_pot, hbm, "mixed")
+        roof32 = None
+        if "jvp" in k32:
+            kj = k32["jvp"]
+            roof32 = {"kernel": JVP_KERNELS["mixed"], "bound": "hbm", "achieved": kj["hbm_gbs"], "peak": hbm,
+                      "unit": "GB/s", "frac": kj["hbm_frac"], "bytes_per_dof": kj["bytes_per_dof"],
+                      "avg_launch_ms": kj["avg_ms"], "peak_source": hbm_src,
+                      "traffic": FUSED_F32_DRAM_BYTES_PER_DOF * N if FUSED_F32_DRAM_BYTES_PER_DOF else None}
         mixed = {"value": ev32 * N / (ms32 / 1e3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms32 / a.steps,
                  "converged": bool(inf32.converged), "newton_iterations": inf32.newton_iterations,
                  "gmres_iterations": inf32.gmres_iterations,
                  "max_rel_diff_vs_fp64": errs, "speedup_vs_fp64_step": (elapsed_ms / a.steps) / (ms32 / a.steps),
+                 "kernels": k32, "roofline_jvp": roof32,
                  "kernel_breakdown_ms": {k: {"ms": v[0], "calls": v[1]} for k, v in prof32.items()}}
         ctx32.close()
         del z32
@@ -381,7 +471,7 @@ def main():
                 "gmres_iterations": [i.gmres_iterations for i in infos],
                 "converged": [bool(i.converged) for i in infos],
                 "evals_per_step": evals / a.steps, "gpu_launches": launches,
-                "gram_schmidt_second_passes": reorth, "roofline": roof,
+                "gram_schmidt_second_passes": reorth, "roofline": roof, "kernels": kern,
                 "kernel_breakdown_ms": breakdown, "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
                 "mixed_precision": mixed}
         print(json.dumps(line), flush=True)

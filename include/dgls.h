@@ -103,6 +103,11 @@ typedef struct {
                                   per application).  0 = off; 1 = on; 2 = on when
                                   max_m D_m^0 dt / h^2 >= 10, the steps where diffusion reaches past
                                   the neighbouring voxels (default) */
+    int32_t jvp_form;          /* DG1 Jacobian-vector products inside the Krylov loop: 0 = automatic
+                                  (fused for an FP32 Krylov loop, cached linearisation for FP64;
+                                  default); 1 = cached linearisation (node Jacobians and face data,
+                                  built once per Newton iteration); 2 = fused matrix-free kernel
+                                  (dual numbers, one launch, nothing cached) */
 } dg_params;
 
 typedef struct {
@@ -116,6 +121,18 @@ typedef struct {
 
 typedef enum { DG_CTRL_NAIVE = 0, DG_CTRL_H211B = 1, DG_CTRL_FIXED = 2 } dg_controller;
 
+/* Controller state between two calls of dg_discharge (checkpoint / resume).  Together with the
+ * state vector it is everything the discharge loop carries from one accepted step to the next,
+ * so a run split at any accepted step and resumed from this record and the state continues
+ * bitwise as the uninterrupted run (all reductions have a fixed order). */
+typedef struct {
+    double t;                  /* time of the state, s */
+    double dt;                 /* step size of the next attempt, s */
+    double err_prev, dt_prev;  /* H211b filter history (Eq. 51): last accepted error and step */
+    int32_t sct;               /* naive controller (Fig. 4): successes since the last growth */
+    int32_t halvings;          /* consecutive halvings so far */
+} dg_controller_state;
+
 typedef struct {
     int32_t controller;        /* dg_controller */
     double t0, dt0, dt_min, dt_max;
@@ -127,6 +144,8 @@ typedef struct {
     const double* replay_dt;   /* host array: if non-NULL take these step sizes (n_replay) */
     int32_t n_replay;
     int32_t limiter;           /* DG1: 1 applies dg_limit to the state after every accepted step */
+    const dg_controller_state* resume;  /* non-NULL: continue a checkpointed run; its t and dt
+                                           replace t0 and dt0 */
 } dg_discharge_opts;
 
 typedef struct {               /* caller-allocated host arrays of length n_max */
@@ -140,6 +159,8 @@ typedef struct {               /* caller-allocated host arrays of length n_max *
     int32_t* gmres_its;
     int32_t status;            /* dg_status of the run: DG_OK (cut-off, t_end or max_steps) */
     int32_t attempts, failures;
+    dg_controller_state* checkpoint;  /* non-NULL: receives the controller state when the call
+                                         returns (pass it as opts.resume with the returned state) */
 } dg_curve;
 
 /* Default parameters of the paper (Tabs. 1, 2, 5) for a chemistry and DG order. */
@@ -192,6 +213,16 @@ dg_status dg_residual_noalloc(dg_ctx* ctx, const double* z_dev, const double* zo
 dg_status dg_jvp(dg_ctx* ctx, const double* z_dev, double t, double dt,
                  const double* v_dev, double* jv_dev);
 
+/* Jacobian-vector product J(z) v of dg_jvp by the fused matrix-free kernel (one launch that reads
+ * z and v once and writes J v once; forward-mode dual numbers, Eqs. 43-48 with the Tab. 4 system):
+ * the product the Krylov loop of a mixed-precision context runs.  precision DG_PREC_FP64: v_dev and
+ * jv_dev are n_dof doubles and the arithmetic is FP64; DG_PREC_MIXED: they are n_dof floats, z is
+ * rounded to FP32 on the device and the arithmetic is FP32 (the context must have been set up with
+ * precision DG_PREC_MIXED, which holds the FP32 copy of z).  Rows unscaled, as dg_jvp.  DG1 contexts
+ * only (DG_ERR_ARG otherwise).  Asynchronous. */
+dg_status dg_jvp_fused(dg_ctx* ctx, const double* z_dev, double t, double dt, int32_t precision,
+                       const void* v_dev, void* jv_dev);
+
 /* Apply the cell-block-Jacobi preconditioner built at z: out = B(z)^{-1} v, where B holds the
  * diagonal blocks of S J (S the Newton row scales; DG0 full voxel blocks, DG1 per-node field
  * blocks).  Asynchronous. */
@@ -222,7 +253,9 @@ dg_status dg_cell_voltage(dg_ctx* ctx, const double* z_dev, double* U_cell);
 dg_status dg_ledger(dg_ctx* ctx, const double* z_dev, double out[5]);
 
 /* Galvanostatic discharge from z_dev (in place) under the chosen controller until the
- * cut-off voltage, t_end or max_steps; one curve point per accepted step.  Synchronous. */
+ * cut-off voltage, t_end or max_steps; one curve point per accepted step.  With
+ * out->checkpoint the controller state at return is written there; with opts->resume the run
+ * continues from such a record (checkpoint / resume of a long discharge).  Synchronous. */
 dg_status dg_discharge(dg_ctx* ctx, double* z_dev, const dg_discharge_opts* opts, dg_curve* out);
 
 /* Kernel timing by category, recorded with CUDA events on the context stream while enabled:

@@ -108,6 +108,59 @@ def assemble_jacobian(model, grid, z, zn, t, dt, relax=False):
     return sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
 
 
+def _abs_jac_group(args):
+    """|J| w restricted to the columns seeded in one (colour, field, node) group (see
+    ``abs_jacobian_times``); a top-level function so that a spawn pool can run it."""
+    model, grid, z, zn, t, dt, w, relax, c = args
+    nz, ny, nx = grid.nz, grid.ny, grid.nx
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    color = ((ii + 2 * jj + 3 * kk) % 7).ravel()
+    ci, cj, ck = ii.ravel(), jj.ravel(), kk.ravel()
+    maps, nn = _dof_maps(model, grid)
+    N = lis.n_dof(model, grid)
+    row_cell = np.empty(N, dtype=np.int64)
+    for f, off, ln, st, loc in maps:
+        cells = grid.struct_idx if st else np.arange(grid.n_cell)
+        for nd in range(nn):
+            row_cell[off + nd * ln: off + (nd + 1) * ln] = cells
+    offs = np.array([(0, 0, -1), (0, -1, 0), (-1, 0, 0), (0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)])
+    pc = color[row_cell]
+    need = (c - pc) % 7
+    need = np.where(need > 3, need - 7, need)
+    qi, qj, qk = ci[row_cell] + offs[need + 3, 0], cj[row_cell] + offs[need + 3, 1], ck[row_cell] + offs[need + 3, 2]
+    inb = (qi >= 0) & (qi < nx) & (qj >= 0) & (qj < ny) & (qk >= 0) & (qk < nz)
+    qcell = np.where(inb, qi + nx * (qj + ny * qk), 0)
+    out = np.zeros(N)
+    for f, off, ln, st, loc in maps:
+        seeded = np.flatnonzero((color == c) & (loc >= 0))
+        if seeded.size == 0:
+            continue
+        qloc = np.where(inb, loc[qcell], -1)
+        for nd in range(nn):
+            v = np.zeros(N)
+            v[off + nd * ln + loc[seeded]] = 1.0
+            Jv = jvp(model, grid, z, zn, t, dt, v, relax)
+            ok = inb & (qloc >= 0)
+            r = np.flatnonzero(ok)
+            out[r] += np.abs(Jv[r]) * np.abs(w[off + nd * ln + qloc[r]])
+    return out
+
+
+def abs_jacobian_times(model, grid, z, zn, t, dt, w, relax=False, workers=1):
+    """|J| |w| (entrywise absolute Jacobian times |w|) by the colouring of ``assemble_jacobian``:
+    each seeded complex-step product gives, in every row, the one Jacobian entry of that row's
+    seeded column.  workers > 1 spreads the seven colours over a spawn process pool."""
+    tasks = [(model, grid, z, zn, t, dt, w, relax, c) for c in range(7)]
+    if workers <= 1:
+        parts = [_abs_jac_group(a) for a in tasks]
+    else:
+        import multiprocessing as mp
+
+        with mp.get_context("spawn").Pool(min(workers, 7)) as pool:
+            parts = pool.map(_abs_jac_group, tasks)
+    return np.sum(parts, axis=0)
+
+
 @dataclass
 class NewtonInfo:
     converged: bool

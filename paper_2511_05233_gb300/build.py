@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdgls.so")
-SOURCES = ["api.cu", "dg0.cu", "dg1.cu", "la.cu", "mg.cu"]
+SOURCES = ["api.cu", "dg0.cu", "dg1.cu", "jvp1.cu", "la.cu", "mg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -1,6 +1,7 @@
 // C-ABI layer of libdgls: context setup, parameters of the paper, Newton-GMRES implicit Euler
 // steps, time-step controllers and the discharge loop.  Kernels live in dg0.cu, dg1.cu, la.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -190,6 +191,7 @@ extern "C" dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t 
     p->eta_max = 1e-2;
     p->eta_min = 1e-3;
     p->hbm_budget_bytes = 0;
+    p->jvp_form = 0;
     return DG_OK;
 }
 
@@ -228,6 +230,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     if (prm->species_mg < 0 || prm->species_mg > 2) return DG_ERR_ARG;
     if (prm->preconditioner != 0 && (prm->mg_cycles < 1 || prm->mg_cycles > 16)) return DG_ERR_ARG;
     if (!(prm->newton_stall_rtol >= 0.0)) return DG_ERR_ARG;
+    if (prm->jvp_form < 0 || prm->jvp_form > 2) return DG_ERR_ARG;
     const int64_t ncell64 = (int64_t)s->nx * s->ny * s->nz;
     if (ncell64 > 2000000000LL) return DG_ERR_ARG;
     dg_ctx* ctx = new dg_ctx();
@@ -503,8 +506,14 @@ static dg_status residual_(dg_ctx* ctx, const double* z, const double* zn, doubl
 // J v through the kernels for this context: the cached linearisation when it is valid and stored in
 // the product's precision (DG1), otherwise forward-mode dual numbers.
 template <class S>
+static bool use_fused(const dg_ctx* ctx) {
+    return ctx->P.order == 1 && (ctx->prm.jvp_form == 2 || (ctx->prm.jvp_form == 0 && std::is_same<S, float>::value));
+}
+
+template <class S>
 static cudaError_t jvp_kernels(dg_ctx* ctx, const S* z, const S* v, double t, double dt, int relax, double sc_dt, S* out,
                                S* gb, S* gbd) {
+    if (use_fused<S>(ctx)) return dg1_jvp_fused<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out);
     if (ctx->has_lin && ctx->lin_valid && std::is_same<S, float>::value == ctx->lin.f32)
         return dg1_lin_apply<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, ctx->lin);
     return ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd)
@@ -648,6 +657,24 @@ extern "C" dg_status dg_jvp(dg_ctx* ctx, const double* z, double t, double dt, c
     dg_status s = jvp_<double>(ctx, z, v, t, dt, 0, 0.0, jv, ctx->gb, ctx->gbd);
     ctx->lin_valid = false;
     return s;
+}
+
+extern "C" dg_status dg_jvp_fused(dg_ctx* ctx, const double* z, double t, double dt, int32_t precision, const void* v,
+                                  void* jv) {
+    if (!ctx || !z || !v || !jv || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_jvp_fused: bad argument");
+    if (ctx->P.order != 1) return fail(ctx, DG_ERR_ARG, "dg_jvp_fused: DG1 contexts only");
+    if (precision == DG_PREC_FP64) {
+        ProfScope ps(ctx, 1);
+        CK(dg1_jvp_fused<double>(ctx->L, ctx->P, ctx->G, z, (const double*)v, t, dt, 0, 0.0, (double*)jv));
+        return DG_OK;
+    }
+    if (precision != DG_PREC_MIXED) return fail(ctx, DG_ERR_ARG, "dg_jvp_fused: precision must be FP64 or MIXED");
+    if (ctx->prm.precision != DG_PREC_MIXED || !ctx->z32)
+        return fail(ctx, DG_ERR_ARG, "dg_jvp_fused: an FP32 product needs a context set up with DG_PREC_MIXED");
+    CK(to_f32(ctx->L, ctx->z32, z, ctx->ndof));
+    ProfScope ps(ctx, 1);
+    CK(dg1_jvp_fused<float>(ctx->L, ctx->P, ctx->G, ctx->z32, (const float*)v, t, dt, 0, 0.0, (float*)jv));
+    return DG_OK;
 }
 
 extern "C" dg_status dg_block_jacobi(dg_ctx* ctx, const double* z, double t, double dt, const double* v, double* out) {
@@ -992,6 +1019,15 @@ extern "C" dg_status dg_discharge(dg_ctx* ctx, double* z, const dg_discharge_opt
     const double t_end = o->t_end > 0 ? o->t_end : INFINITY;
     const int max_steps = std::min(o->max_steps > 0 ? o->max_steps : out->n_max, out->n_max);
     double err_prev = o->tol, dt_prev = dt;
+    if (o->resume) {   // continue a checkpointed run
+        if (!(o->resume->dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_discharge: resume record with dt <= 0");
+        t = o->resume->t;
+        dt = o->resume->dt;
+        err_prev = o->resume->err_prev;
+        dt_prev = o->resume->dt_prev;
+        sct = o->resume->sct;
+        halv = o->resume->halvings;
+    }
     dg_status result = DG_OK;
     while (n < max_steps && t < t_end) {
         dg_step_info info;
@@ -1083,6 +1119,14 @@ extern "C" dg_status dg_discharge(dg_ctx* ctx, double* z, const dg_discharge_opt
     CK(cudaMemcpyAsync(z, cur, N * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
     dg_status s = sync_(ctx);
     out->status = result;
+    if (out->checkpoint) {
+        out->checkpoint->t = t;
+        out->checkpoint->dt = dt;
+        out->checkpoint->err_prev = err_prev;
+        out->checkpoint->dt_prev = dt_prev;
+        out->checkpoint->sct = sct;
+        out->checkpoint->halvings = halv;
+    }
     return result != DG_OK ? result : s;
 }
 
@@ -1097,7 +1141,9 @@ namespace {
 constexpr int64_t NOALLOC_MAX_VOXELS = 2097152;   // 128^3 voxels
 __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_VOXELS];
 constexpr int NOALLOC_MAX_DEVICES = 64;
-double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+// device address of the array per device, looked up once; atomic because several host threads
+// (one per serving slot) may make their first call on a device at the same time
+std::atomic<double*> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
 }  // namespace
 
 extern "C" dg_status dg_residual_noalloc(dg_ctx* ctx, const double* z, const double* zold, double t, double dt,
@@ -1112,17 +1158,19 @@ extern "C" dg_status dg_residual_noalloc(dg_ctx* ctx, const double* z, const dou
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(ctx, DG_ERR_ARG, "dg_residual_noalloc: device index too large");
-    if (!g_noalloc_ptr[dev]) {
+    double* scratch = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!scratch) {
         // once per device, with that device current: the host-side name of a __device__ array is
-        // not a device address, so ask the runtime for it
+        // not a device address, so ask the runtime for it (two racing first calls store the same value)
         void* ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = (double*)ptr;
+        scratch = (double*)ptr;
+        g_noalloc_ptr[dev].store(scratch, std::memory_order_release);
     }
     int64_t launches = 0;
     LaunchCtx L{ctx->L.st, &launches};
-    e = dg0_residual(L, ctx->P, ctx->G, z, zold, t, dt, 0, r, g_noalloc_ptr[dev]);
+    e = dg0_residual(L, ctx->P, ctx->G, z, zold, t, dt, 0, r, scratch);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("dg_residual_noalloc: ") + cudaGetErrorString(e));
     return DG_OK;
 }

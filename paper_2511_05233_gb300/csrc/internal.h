@@ -84,6 +84,12 @@ template <class S>
 cudaError_t dg1_lin_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v,
                           double t, double dt, int relax, double sc_dt, S* out, const DG1Lin& lin);
 
+// Fused matrix-free DG1 product (jvp1.cu): out = J(z) v (times dt rscale per row when sc_dt > 0)
+// in one launch, forward-mode dual numbers in the arithmetic type S; nothing cached.
+template <class S>
+cudaError_t dg1_jvp_fused(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v, double t,
+                          double dt, int relax, double sc_dt, S* out);
+
 // ------------------------------------------------------------------ linear algebra (la.cu)
 // Block-Jacobi: invert nblk blocks of nf x nf (row-major) in place; identity rows for absent
 // fields are set by the builders.  Returns the count of singular blocks in *bad (device).

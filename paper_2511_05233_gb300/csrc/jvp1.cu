@@ -1,0 +1,335 @@
+// Fused matrix-free DG1 Jacobian-vector product: J(z) v in one launch, reading z and v once and
+// writing J v once (the 12 bytes per unknown of an FP32 product, 24 of an FP64 one).
+//
+// J v is the directional derivative of the DG1 residual (Eqs. 43-48 with the Tab. 4 system and
+// the Tab. 3 sources) at z along v, evaluated with forward-mode dual numbers; nothing is cached
+// between products, so the Krylov loop of the mixed-precision solver streams only its vectors.
+//
+// Mapping: one thread block per 32 consecutive voxels, one warp per DG1 node (8 warps), lane =
+// voxel.  Every field of a node plane is contiguous in the node-major layout, so each warp load is
+// one 128-byte (FP32) request.
+//   phase 0  the block's nodal values of z and v go to shared memory;
+//   phase 1  each thread evaluates, at its node, the transport factor g (Eqs. 2-3, 18) and the
+//            node terms (storage, Eq. 50, and reaction sources), and g at the three face points
+//            on its side of its three nodal lines;
+//   phase 2  per direction, the volume term of the thread's line (both nodes of a line are in the
+//            block) and the interior-penalty flux (Eq. 46) through the face point on its side, from
+//            its own traces and the neighbour voxel's: the x-neighbour of an inner lane is read
+//            from shared memory, other neighbours from global memory (L1/L2: the neighbouring
+//            blocks read the same lines);
+//   phase 3  each node adds its own face flux (trace weight ALPHA) and its line partner's (BETA)
+//            from shared memory and stores its row-scaled outputs.
+// Each interior face point is evaluated by the voxels on both of its sides.
+#include "dg1_shared.cuh"
+
+namespace dgls {
+
+namespace {
+constexpr int FT = 32;   // voxels per block
+
+// per-call constants in the arithmetic type of the product (FP32 products stay on the FP32 pipe)
+template <class S>
+struct FusedK {
+    S wf, vol, pen, gq2;            // face weight (h/2)^2, volume weight 3h/8, penalty / h, sqrt(3) / (2h)
+    S D0[6], km[6], Kd[6], Km[6];   // species row: D0 and z F/(RT) D0 (zero while relaxing); Phi^L row
+    S kSv, kS;                      // Phi^S: 2 kappa_s vol in the volume, kappa_s at faces
+    S aLi, aL;                      // anode: k_Ano on the Li+ row (zero while relaxing), F k_Ano on Phi^L
+    S rs[DG_MAXF];                  // row scales of the outputs (Newton rows) or 1
+    int charged;                    // bit m: species m carries charge
+};
+
+// line index q of node n in direction d (the node's two coordinates across d)
+__device__ __forceinline__ int line_of(int d, int n) {
+    const int a = n & 1, b = (n >> 1) & 1, c = (n >> 2) & 1;
+    return d == 0 ? b + 2 * c : d == 1 ? a + 2 * c : a + 2 * b;
+}
+
+template <class Chem>
+__host__ __device__ constexpr bool struct_field(int f) {
+    return (f >= Chem::NL && f < Chem::NL + Chem::NS) || f == Chem::PHIS;
+}
+
+template <class Chem, class S>
+constexpr size_t fused_smem() {
+    return (size_t)(2 * Chem::NF * 8 * FT + 2 * 32 * FT + 8 * 3 * (Chem::NL + 2) * FT) * sizeof(S) + 2 * FT * sizeof(int);
+}
+}  // namespace
+
+template <class Chem, class S>
+__global__ void __launch_bounds__(256) k_jvp1_fused(const DevParams p, const Geo g, const S* __restrict__ z,
+                                                    const S* __restrict__ v, const FusedK<S> K, double tH,
+                                                    double dt, int relax, S* __restrict__ out) {
+    typedef Dual<S> T;
+    constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
+    constexpr int NE = NL + 2;   // transport equations: the species, Phi^L, Phi^S
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* sZ = reinterpret_cast<S*>(smem_raw);   // [NF][8][FT]
+    S* sV = sZ + NF * 8 * FT;                 // [NF][8][FT]
+    S* sG = sV + NF * 8 * FT;                 // [32 slots][FT] transport factors (value)
+    S* sGd = sG + 32 * FT;                    // [32 slots][FT] (tangent)
+    S* sF = sGd + 32 * FT;                    // [8 nodes][3 dirs][NE][FT] near-face flux tangents, signed and weighted
+    int* sPh = reinterpret_cast<int*>(sF + 8 * 3 * NE * FT);
+    int* sSi = sPh + FT;
+
+    const int n = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * FT + lane;
+    const bool active = c < p.n_cell;
+    const S al = S(ALPHA), be = S(BETA);
+
+    // ---- phase 0: the block's nodal values
+    int ph = 0, si = -1;
+    if (active) {
+        ph = g.phase[c];
+        si = g.cmap[c];
+    }
+    if (n == 0) {
+        sPh[lane] = ph;
+        sSi[lane] = si;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        S zz = S(0), vv = S(0);
+        if (active && (!struct_field<Chem>(f) || ph == 1)) {
+            const int64_t o = p.off[f] + (int64_t)n * p.flen[f] + (struct_field<Chem>(f) ? si : c);
+            zz = z[o];
+            vv = v[o];
+        }
+        sZ[(f * 8 + n) * FT + lane] = zz;
+        sV[(f * 8 + n) * FT + lane] = vv;
+    }
+    __syncthreads();
+    auto zv = [&](int f, int node, int l) -> T { return mkd(sZ[(f * 8 + node) * FT + l], sV[(f * 8 + node) * FT + l]); };
+
+    // ---- phase 1: transport factors at the node and its three face points; node terms
+    S acc[NF];
+    {
+        T cn[NL], es[2];
+#pragma unroll
+        for (int m = 0; m < NL; ++m) cn[m] = zv(m, n, lane);
+        es[0] = es[1] = Make<T>::c(0.0);
+        if (NS == 2 && ph == 1) {
+            es[0] = zv(NL, n, lane);
+            es[1] = zv(NL + 1, n, lane);
+        }
+        {
+            const T gg = transport_factor<Chem, T>(p, liquid_fraction<Chem, T>(p, ph, es), cn);
+            sG[n * FT + lane] = gg.v;
+            sGd[n * FT + lane] = gg.d;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int pn = n ^ (1 << d);
+            const int side = (n >> d) & 1 ? 1 : -1;
+            T ct[NL], et[2];
+#pragma unroll
+            for (int m = 0; m < NL; ++m) ct[m] = cn[m] * al + zv(m, pn, lane) * be;
+            et[0] = et[1] = Make<T>::c(0.0);
+            if (NS == 2 && ph == 1) {
+                et[0] = es[0] * al + zv(NL, pn, lane) * be;
+                et[1] = es[1] * al + zv(NL + 1, pn, lane) * be;
+            }
+            const T gg = transport_factor<Chem, T>(p, liquid_fraction<Chem, T>(p, ph, et), ct);
+            const int slot = face_slot(d, side, line_of(d, n));
+            sG[slot * FT + lane] = gg.v;
+            sGd[slot * FT + lane] = gg.d;
+        }
+        // storage and sources of this node (the previous time level enters only as constants)
+        const T phiL = zv(PHIL, n, lane);
+        const T phiS = ph == 1 ? zv(PHIS, n, lane) : Make<T>::c(0.0);
+        double old[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) old[f] = 0.0;
+        T R[NF];
+        node_terms<Chem, T>(p, ph, cn, es, phiL, phiS, old, tH, dt, relax, R);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc[f] = R[f].d;
+    }
+    __syncthreads();
+
+    // ---- phase 2: per direction, the line's volume term and the flux through this node's face point
+    int ci = 0, cj = 0, ck = 0;
+    if (active) cell_ijk(p, c, ci, cj, ck);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int pn = n ^ (1 << d);
+        const int mc = (n >> d) & 1;         // this node's coordinate along d (1: next to the +d face)
+        const int n0 = mc ? pn : n, n1 = mc ? n : pn;
+        // volume term of the line (n0, n1): n1 gets +fl, n0 gets -fl
+        {
+            const S sgn = mc ? S(1) : S(-1);
+            const T gN0 = mkd(sG[n0 * FT + lane], sGd[n0 * FT + lane]);
+            const T gN1 = mkd(sG[n1 * FT + lane], sGd[n1 * FT + lane]);
+            const T gsum = gN0 + gN1;
+            const T dPhi = zv(PHIL, n1, lane) - zv(PHIL, n0, lane);
+            S accL = S(0);
+#pragma unroll
+            for (int m = 0; m < NL; ++m) {
+                const T C0 = zv(m, n0, lane), C1 = zv(m, n1, lane);
+                const T gdc = gsum * (C1 - C0);
+                S fl = (gdc * K.D0[m]).d;
+                if ((K.charged >> m) & 1) {
+                    const T mdp = (gN0 * C0 + gN1 * C1) * dPhi;
+                    fl += (mdp * K.km[m]).d;
+                    accL += (gdc * K.Kd[m] + mdp * K.Km[m]).d;
+                }
+                acc[m] += sgn * K.vol * fl;
+            }
+            acc[PHIL] += sgn * K.vol * accL;
+            if (ph == 1) acc[PHIS] += sgn * K.kSv * (sV[(PHIS * 8 + n1) * FT + lane] - sV[(PHIS * 8 + n0) * FT + lane]);
+        }
+        // flux through the face point on this node's side of the line
+        S Fe[NE];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) Fe[e] = S(0);
+        const int coord = d == 0 ? ci : d == 1 ? cj : ck;
+        const int ext = d == 0 ? p.nx : d == 1 ? p.ny : p.nz;
+        const int stride = d == 0 ? 1 : d == 1 ? p.nx : p.nx * p.ny;
+        const bool hasQ = active && (mc ? coord + 1 < ext : coord > 0);
+        if (hasQ) {
+            const int qc = c + (mc ? stride : -stride);
+            const int ql = lane + (mc ? 1 : -1);
+            const bool local = d == 0 && ql >= 0 && ql < FT;
+            const int qph = local ? sPh[ql] : g.phase[qc];
+            const int qsi = local ? sSi[ql] : g.cmap[qc];
+            // neighbour values at its node `node` (its near node is pn, its far node n)
+            auto nb = [&](int f, int node) -> T {
+                if (local) return zv(f, node, ql);
+                if (struct_field<Chem>(f) && qph != 1) return Make<T>::c(0.0);
+                const int64_t o = p.off[f] + (int64_t)node * p.flen[f] + (struct_field<Chem>(f) ? qsi : qc);
+                return mkd(z[o], v[o]);
+            };
+            const int q = line_of(d, n);
+            const int slotP = face_slot(d, mc ? 1 : -1, q);
+            const T gP = mkd(sG[slotP * FT + lane], sGd[slotP * FT + lane]);
+            T gQ;
+            if (local) {
+                const int slotQ = face_slot(d, mc ? -1 : 1, q);
+                gQ = mkd(sG[slotQ * FT + ql], sGd[slotQ * FT + ql]);
+            } else {
+                T ct[NL], et[2];
+#pragma unroll
+                for (int m = 0; m < NL; ++m) ct[m] = nb(m, pn) * al + nb(m, n) * be;
+                et[0] = et[1] = Make<T>::c(0.0);
+                if (NS == 2 && qph == 1) {
+                    et[0] = nb(NL, pn) * al + nb(NL, n) * be;
+                    et[1] = nb(NL + 1, pn) * al + nb(NL + 1, n) * be;
+                }
+                gQ = transport_factor<Chem, T>(p, liquid_fraction<Chem, T>(p, qph, et), ct);
+            }
+            const T gl = mc ? gP : gQ, gr = mc ? gQ : gP;
+            const T Hg = harm(gl, gr);
+            // jump (left minus right) and mean normal derivative of a field across the face
+            auto bracket = [&](T own_n, T own_f, T nb_n, T nb_f, T& t_own, T& t_nb) -> T {
+                t_own = own_n * al + own_f * be;
+                t_nb = nb_n * al + nb_f * be;
+                const T jump = mc ? t_own - t_nb : t_nb - t_own;
+                const T dn = ((mc ? own_n - own_f : own_f - own_n) + (mc ? nb_f - nb_n : nb_n - nb_f)) * K.gq2;
+                return jump * K.pen - dn;
+            };
+            T tPo, tPn;
+            const T bL = bracket(zv(PHIL, n, lane), zv(PHIL, pn, lane), nb(PHIL, pn), nb(PHIL, n), tPo, tPn);
+            S fL = S(0);
+#pragma unroll
+            for (int m = 0; m < NL; ++m) {
+                T to, tn;
+                const T b = bracket(zv(m, n, lane), zv(m, pn, lane), nb(m, pn), nb(m, n), to, tn);
+                const T dterm = b * Hg;
+                S f = (dterm * K.D0[m]).d;
+                if ((K.charged >> m) & 1) {
+                    const T cl = mc ? to : tn, cr = mc ? tn : to;
+                    const T mterm = bL * harm(gl * cl, gr * cr);
+                    f += (mterm * K.km[m]).d;
+                    fL += (dterm * K.Kd[m] + mterm * K.Km[m]).d;
+                }
+                Fe[m] = f;
+            }
+            Fe[NL] = fL;
+            if (ph == 1 && qph == 1) {
+                const S jn = sV[(PHIS * 8 + n) * FT + lane], jf = sV[(PHIS * 8 + pn) * FT + lane];
+                const S qn = nb(PHIS, pn).d, qf = nb(PHIS, n).d;
+                const S to = jn * al + jf * be, tn = qn * al + qf * be;
+                const S jump = mc ? to - tn : tn - to;
+                const S dn = ((mc ? jn - jf : jf - jn) + (mc ? qf - qn : qn - qf)) * K.gq2;
+                Fe[NL + 1] = (jump * K.pen - dn) * K.kS;
+            }
+        } else if (active && d == 0 && mc && ci == p.nx - 1) {
+            // anode face (Eqs. 26-27): exchange rate at the face trace of c_Li and Phi^L
+            const T cLi = zv(0, n, lane) * al + zv(0, pn, lane) * be;
+            const T phL = zv(PHIL, n, lane) * al + zv(PHIL, pn, lane) * be;
+            const S rA = anode_rate<T>(p, cLi, phL).d;
+            Fe[0] = rA * K.aLi;
+            Fe[NL] = rA * K.aL;
+        }
+        // the left voxel of a face gets +f, the right one -f (face weight folded in)
+        const S sw = mc ? K.wf : -K.wf;
+#pragma unroll
+        for (int e = 0; e < NE; ++e) sF[((n * 3 + d) * NE + e) * FT + lane] = Fe[e] * sw;
+    }
+    __syncthreads();
+
+    // ---- phase 3: own face flux (near node, ALPHA) and the partner's (far node, BETA); store
+    if (!active) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int pn = n ^ (1 << d);
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+            const int f = e < NL ? e : e == NL ? PHIL : PHIS;
+            acc[f] += al * sF[((n * 3 + d) * NE + e) * FT + lane] + be * sF[((pn * 3 + d) * NE + e) * FT + lane];
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        if (struct_field<Chem>(f) && ph != 1) continue;
+        const int64_t o = p.off[f] + (int64_t)n * p.flen[f] + (struct_field<Chem>(f) ? si : c);
+        out[o] = acc[f] * K.rs[f];
+    }
+}
+
+template <class Chem, class S>
+static cudaError_t fused_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v, double t,
+                              double dt, int relax, double sc_dt, S* out) {
+    FusedK<S> K;
+    const double h = p.h;
+    K.wf = S(0.25 * h * h);
+    K.vol = S(3.0 * h / 8.0);
+    K.pen = S(p.penalty / h);
+    K.gq2 = S(0.5 * 1.7320508075688772935 / h);
+    K.charged = 0;
+    for (int m = 0; m < 6; ++m) {
+        const bool on = m < Chem::NL;
+        K.D0[m] = S(on && !relax ? p.D0[m] : 0.0);
+        K.km[m] = S(on && !relax ? p.kappa_m[m] : 0.0);
+        K.Kd[m] = S(on ? p.Kd[m] : 0.0);
+        K.Km[m] = S(on ? p.Km[m] : 0.0);
+        if (on && p.zc[m] != 0.0) K.charged |= 1 << m;
+    }
+    K.kSv = S(2.0 * p.kappa_s * 3.0 * h / 8.0);
+    K.kS = S(p.kappa_s);
+    K.aLi = S(relax ? 0.0 : p.kAno);
+    K.aL = S(p.F * p.kAno);
+    for (int f = 0; f < DG_MAXF; ++f) K.rs[f] = S(f < Chem::NF && sc_dt > 0.0 ? sc_dt * p.rscale[f] : 1.0);
+    const size_t smem = fused_smem<Chem, S>();
+    // more than 48 KB of dynamic shared memory needs an opt-in, which belongs to the current device
+    cudaError_t e = cudaFuncSetAttribute(k_jvp1_fused<Chem, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = (p.n_cell + FT - 1) / FT;
+    k_jvp1_fused<Chem, S><<<blocks, 8 * FT, smem, L.st>>>(p, g, z, v, K, smooth_step(t), dt, relax, out);
+    *L.counter += 1;
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t dg1_jvp_fused(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v, double t,
+                          double dt, int relax, double sc_dt, S* out) {
+    if (p.order != 1) return cudaErrorInvalidValue;
+    return p.nf == 10 ? fused_impl<ChemTO, S>(L, p, g, z, v, t, dt, relax, sc_dt, out)
+                      : fused_impl<ChemR3, S>(L, p, g, z, v, t, dt, relax, sc_dt, out);
+}
+
+template cudaError_t dg1_jvp_fused<double>(const LaunchCtx&, const DevParams&, const Geo&, const double*,
+                                           const double*, double, double, int, double, double*);
+template cudaError_t dg1_jvp_fused<float>(const LaunchCtx&, const DevParams&, const Geo&, const float*, const float*,
+                                          double, double, int, double, float*);
+
+}  // namespace dgls

@@ -32,7 +32,8 @@ class Params(C.Structure):
                 ("newton_rtol", C.c_double), ("newton_atol", C.c_double), ("newton_max_it", C.c_int32),
                 ("eta_max", C.c_double), ("eta_min", C.c_double), ("hbm_budget_bytes", C.c_int64),
                 ("preconditioner", C.c_int32), ("mg_cycles", C.c_int32), ("precond_every", C.c_int32),
-                ("newton_stall_rtol", C.c_double), ("reorth", C.c_int32), ("species_mg", C.c_int32)]
+                ("newton_stall_rtol", C.c_double), ("reorth", C.c_int32), ("species_mg", C.c_int32),
+                ("jvp_form", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -43,18 +44,27 @@ class StepInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ControllerState(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("err_prev", C.c_double), ("dt_prev", C.c_double),
+                ("sct", C.c_int32), ("halvings", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class DischargeOpts(C.Structure):
     _fields_ = [("controller", C.c_int32), ("t0", C.c_double), ("dt0", C.c_double), ("dt_min", C.c_double),
                 ("dt_max", C.c_double), ("tol", C.c_double), ("cutoff_V", C.c_double), ("t_end", C.c_double),
                 ("max_steps", C.c_int32), ("max_halvings", C.c_int32), ("replay_dt", C.POINTER(C.c_double)),
-                ("n_replay", C.c_int32), ("limiter", C.c_int32)]
+                ("n_replay", C.c_int32), ("limiter", C.c_int32), ("resume", C.POINTER(ControllerState))]
 
 
 class Curve(C.Structure):
     _fields_ = [("n_max", C.c_int32), ("n", C.c_int32), ("t", C.POINTER(C.c_double)), ("dt", C.POINTER(C.c_double)),
                 ("U_cell", C.POINTER(C.c_double)), ("c_m", C.POINTER(C.c_double)),
                 ("newton_its", C.POINTER(C.c_int32)), ("gmres_its", C.POINTER(C.c_int32)),
-                ("status", C.c_int32), ("attempts", C.c_int32), ("failures", C.c_int32)]
+                ("status", C.c_int32), ("attempts", C.c_int32), ("failures", C.c_int32),
+                ("checkpoint", C.POINTER(ControllerState))]
 
 
 _LIB = None
@@ -85,6 +95,7 @@ def lib():
             "dg_residual": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P]),
             "dg_residual_noalloc": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P]),
             "dg_jvp": (C.c_int, [_P, _P, C.c_double, C.c_double, _P, _P]),
+            "dg_jvp_fused": (C.c_int, [_P, _P, C.c_double, C.c_double, C.c_int32, _P, _P]),
             "dg_block_jacobi": (C.c_int, [_P, _P, C.c_double, C.c_double, _P, _P]),
             "dg_row_scales": (C.c_int, [_P, C.c_double, _P]),
             "dg_step": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.POINTER(StepInfo)]),
@@ -209,6 +220,23 @@ class Context:
         self._check(self._lib.dg_jvp(self._h, _ptr(z), t, dt, _ptr(v), _ptr(out)))
         return out
 
+    def jvp_fused(self, z, t, dt, v, out):
+        """dg_jvp_fused: the one-launch matrix-free product; FP64 for float64 v/out, FP32 (mixed
+        contexts) for float32 v/out."""
+        import torch
+
+        if v.dtype == torch.float32:
+            prec = MIXED
+            ok = out.dtype == torch.float32 and v.is_cuda and out.is_cuda and v.is_contiguous() and out.is_contiguous()
+            if not ok:
+                raise TypeError("expected contiguous float32 CUDA tensors for v and out")
+            vp, op = C.c_void_p(v.data_ptr()), C.c_void_p(out.data_ptr())
+        else:
+            prec = FP64
+            vp, op = _ptr(v), _ptr(out)
+        self._check(self._lib.dg_jvp_fused(self._h, _ptr(z), t, dt, prec, vp, op))
+        return out
+
     def block_jacobi(self, z, t, dt, v, out):
         self._check(self._lib.dg_block_jacobi(self._h, _ptr(z), t, dt, _ptr(v), _ptr(out)))
         return out
@@ -246,8 +274,14 @@ class Context:
         return list(out)
 
     def discharge(self, z, controller=NAIVE, dt0=1e-3, dt_min=1e-6, dt_max=10.0, tol=1e-5, cutoff_V=1.9,
-                  t_end=0.0, max_steps=100000, max_halvings=30, replay_dt=None, t0=0.0, limiter=False):
+                  t_end=0.0, max_steps=100000, max_halvings=30, replay_dt=None, t0=0.0, limiter=False,
+                  resume=None):
+        """Run dg_discharge; res["checkpoint"] is the controller state at return (a dict), which
+        resume= takes to continue the run from the returned state."""
         n_max = max_steps if replay_dt is None else len(replay_dt)
+        rs = None
+        if resume is not None:
+            rs = ControllerState(**resume)
         arr = {k: np.zeros(n_max) for k in ("t", "dt", "U_cell", "c_m")}
         nit = np.zeros(n_max, dtype=np.int32)
         git = np.zeros(n_max, dtype=np.int32)
@@ -256,14 +290,17 @@ class Context:
             rp = np.ascontiguousarray(replay_dt, dtype=np.float64)
         o = DischargeOpts(controller, t0, dt0, dt_min, dt_max, tol, cutoff_V, t_end, max_steps, max_halvings,
                           rp.ctypes.data_as(C.POINTER(C.c_double)) if rp is not None else None,
-                          len(rp) if rp is not None else 0, 1 if limiter else 0)
+                          len(rp) if rp is not None else 0, 1 if limiter else 0,
+                          C.pointer(rs) if rs is not None else None)
+        ck = ControllerState()
         cv = Curve(n_max, 0, *[arr[k].ctypes.data_as(C.POINTER(C.c_double)) for k in ("t", "dt", "U_cell", "c_m")],
-                   nit.ctypes.data_as(C.POINTER(C.c_int32)), git.ctypes.data_as(C.POINTER(C.c_int32)), 0, 0, 0)
+                   nit.ctypes.data_as(C.POINTER(C.c_int32)), git.ctypes.data_as(C.POINTER(C.c_int32)), 0, 0, 0,
+                   C.pointer(ck))
         st = self._lib.dg_discharge(self._h, _ptr(z), C.byref(o), C.byref(cv))
         n = cv.n
         res = {k: v[:n].copy() for k, v in arr.items()}
         res.update(newton_its=nit[:n].copy(), gmres_its=git[:n].copy(), status=STATUS.get(st, st),
-                   attempts=cv.attempts, failures=cv.failures)
+                   attempts=cv.attempts, failures=cv.failures, checkpoint=ck.as_dict())
         if st not in (OK, ERR_ABORTED, ERR_NOCONV):
             self._check(st)
         return res

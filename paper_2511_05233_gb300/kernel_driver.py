@@ -2,7 +2,8 @@
 
     python -m paper_2511_05233_gb300.kernel_driver --n 64 --order 1 --chem tradeoff --op jvp --reps 5
 
-Prints the mean device time per call (CUDA events on the library's stream).
+Prints the mean device time per call (CUDA events on the library's stream).  --op jvp_fused times
+dg_jvp_fused: FP64 with --precision fp64, the FP32 product of the mixed Krylov loop with mixed.
 """
 from __future__ import annotations
 
@@ -18,7 +19,7 @@ def main():
     ap.add_argument("--order", type=int, default=1)
     ap.add_argument("--chem", default="tradeoff")
     ap.add_argument("--porosity", type=float, default=0.5)
-    ap.add_argument("--op", default="jvp", choices=["residual", "jvp", "step"])
+    ap.add_argument("--op", default="jvp", choices=["residual", "jvp", "jvp_fused", "step"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=5)
     a = ap.parse_args()
@@ -40,6 +41,7 @@ def main():
     z[: ctx.offsets[nl]] *= 1.0 + 0.01 * noise[: ctx.offsets[nl]]
     v = torch.from_numpy(inputs.normal_noise(N, 5)).cuda() * (z.abs() + 1e-3)
     out = torch.empty_like(z)
+    v32, o32 = v.float(), torch.empty(N, dtype=torch.float32, device="cuda")
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -48,6 +50,11 @@ def main():
             ctx.residual(z, z0, 1e-3, 1e-3, out)
         elif a.op == "jvp":
             ctx.jvp(z, 1e-3, 1e-3, v, out)
+        elif a.op == "jvp_fused":
+            if a.precision == "mixed":
+                ctx.jvp_fused(z, 1e-3, 1e-3, v32, o32)
+            else:
+                ctx.jvp_fused(z, 1e-3, 1e-3, v, out)
         else:
             ctx.step(z, out, 0.0, 1e-3, check=False)
 
@@ -61,7 +68,8 @@ def main():
     ms = e0.elapsed_time(e1) / a.reps
     print(json.dumps({"op": a.op, "n": a.n, "order": a.order, "chem": a.chem, "precision": a.precision,
                       "n_dof": N, "ms_per_call": ms, "gdof_per_s": N / (ms / 1e3) / 1e9,
-                      "finite": bool(np.isfinite(out.cpu().numpy()).all())}))
+                      "finite": bool(np.isfinite((o32 if a.op == "jvp_fused" and a.precision == "mixed" else out)
+                                                 .cpu().numpy()).all())}))
 
 
 if __name__ == "__main__":

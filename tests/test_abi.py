@@ -57,7 +57,8 @@ def test_setup_rejects_out_of_range_solver_switches(lib):
     ph = np.zeros((2, 2, 4), dtype=np.uint8)
     ph[:, :, 0] = 1
     s = dgls.Structure(4, 2, 2, 1e-6, ph.ctypes.data_as(C.POINTER(C.c_uint8)))
-    for field, value in (("reorth", 3), ("species_mg", 3), ("species_mg", -1), ("mg_cycles", 0), ("mg_cycles", 17)):
+    for field, value in (("reorth", 3), ("species_mg", 3), ("species_mg", -1), ("mg_cycles", 0), ("mg_cycles", 17),
+                         ("jvp_form", 3), ("jvp_form", -1)):
         p = dgls.default_params(dgls.TRADEOFF, 1)
         setattr(p, field, value)
         h = C.c_void_p()

@@ -70,3 +70,113 @@ def test_h211b_discharge_matches_oracle():
     assert np.allclose(res["dt"], rec.dt, rtol=1e-6, atol=0)
     assert np.allclose(res["U_cell"], rec.U, rtol=1e-8, atol=0)
     assert_state_close(model, grid, to_host(zd), zf, 1e-8)
+
+
+def test_cutoff_on_the_first_accepted_step():
+    """Cut-off (Sec. 3: the discharge ends when U_cell reaches the cut-off; reading: the first
+    accepted step with U_cell <= cut-off): with the cut-off above the cell voltage the run stops
+    after exactly one accepted step, as the oracle's controller does."""
+    from paper_2511_05233_gb300 import dgls
+
+    model, grid, phase, z0, z = make_case("tradeoff", 0, (6, 4, 3))
+
+    def step(zz, t, dt):
+        z1, info = newton.implicit_euler_step(model, grid, zz, t, dt)
+        return info.converged, z1
+
+    def cut(zz):
+        U = lis.cell_voltage(model, grid, zz)
+        return U <= 3.0, U
+    zf, rec = control.naive(step, cut, z0, dt0=1e-3, max_steps=7)
+    assert rec.status == "cutoff" and len(rec.t) == 1
+    ctx = gpu_context(model, phase)
+    zd = to_dev(z0)
+    res = ctx.discharge(zd, controller=dgls.NAIVE, dt0=1e-3, max_steps=7, cutoff_V=3.0)
+    assert res["status"] == "DG_OK" and len(res["t"]) == 1
+    assert np.allclose(res["U_cell"], rec.U, rtol=1e-8, atol=0)
+    assert_state_close(model, grid, to_host(zd), zf, 1e-8)
+
+
+def test_cutoff_in_the_middle_of_a_run():
+    """A cut-off between the cell voltages of the 3rd and 4th accepted steps stops both the
+    GPU run and the oracle's after the 4th step."""
+    from paper_2511_05233_gb300 import dgls
+
+    model, grid, phase, z0, z = make_case("tradeoff", 0, (6, 4, 3))
+    _, full = _oracle_run(model, grid, z0, "naive", 7)
+    U = np.array(full.U)
+    assert np.all(np.diff(U[:5]) < 0)                  # the voltage falls over the first steps
+    cutv = 0.5 * (U[2] + U[3])
+
+    def step(zz, t, dt):
+        z1, info = newton.implicit_euler_step(model, grid, zz, t, dt)
+        return info.converged, z1
+
+    def cut(zz):
+        u = lis.cell_voltage(model, grid, zz)
+        return u <= cutv, u
+    zf, rec = control.naive(step, cut, z0, dt0=1e-3, max_steps=7)
+    assert rec.status == "cutoff" and len(rec.t) == 4
+    ctx = gpu_context(model, phase)
+    zd = to_dev(z0)
+    res = ctx.discharge(zd, controller=dgls.NAIVE, dt0=1e-3, max_steps=7, cutoff_V=cutv)
+    assert res["status"] == "DG_OK" and len(res["t"]) == 4
+    assert np.allclose(res["U_cell"], rec.U, rtol=1e-8, atol=0)
+    assert_state_close(model, grid, to_host(zd), zf, 1e-8)
+
+
+def _golden():
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "discharge_dg0_tradeoff_6.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+def test_full_discharge_to_cutoff_replayed_against_oracle():
+    """The oracle's full discharge to the 1.9 V cut-off (tests/golden/make_discharge_golden.py: 6^3
+    DG0 cell with a single collector cluster, 1C, relaxation of Sec. 2.8, naive controller of
+    Fig. 4) replayed on the GPU with the oracle's accepted step sizes: the relaxed state, the
+    cell voltage of Eq. A1 after every step (1e-8 relative) and the final state (1e-8) agree, and
+    the GPU run stops on the same step, the first with U_cell <= 1.9 V."""
+    from oracle import chemistry as ch
+    from paper_2511_05233_gb300 import dgls
+
+    gd = _golden()
+    assert gd["status"] == "cutoff" and gd["U_cell"][-1] <= 1.9 < gd["U_cell"][-2]
+    phase = np.array(gd["phase"], dtype=np.uint8)
+    grid = lis.Grid(phase, gd["h"])
+    model = lis.Model(ch.tradeoff(), order=0, f_C=gd["f_C"], eps_struct=1.0 - gd["porosity"])
+    ctx = gpu_context(model, phase)
+    z = ctx.new_state()
+    ctx.equilibrium_state(z)
+    ctx.relax(z, gd["relax"]["dt"], gd["relax"]["steps"])
+    zr = np.array(gd["z_relaxed"])
+    assert_state_close(model, grid, to_host(z), zr, 1e-8)
+    zd = to_dev(zr)
+    res = ctx.discharge(zd, controller=dgls.NAIVE, replay_dt=np.array(gd["dt"]), cutoff_V=1.9)
+    assert res["status"] == "DG_OK"
+    assert len(res["t"]) == len(gd["t"])
+    assert np.allclose(res["t"], gd["t"], rtol=1e-14, atol=0)
+    rel = np.abs(res["U_cell"] - np.array(gd["U_cell"])) / np.abs(gd["U_cell"])
+    assert rel.max() <= 1e-8, (rel.max(), int(rel.argmax()), rel.tolist())
+    assert_state_close(model, grid, to_host(zd), np.array(gd["z_final"]), 1e-8)
+
+
+def test_full_discharge_free_running_reaches_cutoff():
+    """The same cell discharged by the GPU's own naive controller (not replayed) reaches the cut-off;
+    its capacity at the cut-off is within 2 % of the oracle's (the two controllers may take
+    different steps once a Newton solve fails in one and not in the other)."""
+    from oracle import chemistry as ch
+    from paper_2511_05233_gb300 import dgls
+
+    gd = _golden()
+    phase = np.array(gd["phase"], dtype=np.uint8)
+    model = lis.Model(ch.tradeoff(), order=0, f_C=gd["f_C"], eps_struct=1.0 - gd["porosity"])
+    ctx = gpu_context(model, phase)
+    zd = to_dev(np.array(gd["z_relaxed"]))
+    res = ctx.discharge(zd, controller=dgls.NAIVE, dt0=1e-3, dt_max=10.0, cutoff_V=1.9, max_steps=2000)
+    assert res["status"] == "DG_OK"
+    assert res["U_cell"][-1] <= 1.9 < res["U_cell"][-2]
+    assert abs(res["t"][-1] / gd["t"][-1] - 1.0) <= 0.02

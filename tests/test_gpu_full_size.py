@@ -27,29 +27,58 @@ def _lib():
 
 
 def _crop(model, grid, U, k, j, i):
-    """Oracle grid and flat state of the crop around voxel (k, j, i): 3 x 3 voxels across, and in x
-    one more layer on the -x side, marked as structure so that the crop has a collector face (the
-    oracle requires one).  That layer is two voxels from the centre and does not reach it."""
-    sl = (slice(k - 1, k + 2), slice(j - 1, j + 2), slice(i - 2, i + 2))
+    """Oracle model, grid and flat-state packer for the crop around voxel (k, j, i), and the centre's
+    index in the crop.  The crop is 3 x 3 voxels across; along x it keeps two layers on each side
+    where the grid has them.  The oracle requires a collector face, so an interior crop's first
+    layer is marked as structure (two voxels from the centre, out of its reach).  A crop at the real
+    collector (i = 0) keeps the real collector face: its model takes the collector current density
+    per structure face of the full grid (Eq. 25 with reading 5's rescaling), j_el adjusted for the
+    crop's face count.  A crop at the anode (i = nx - 1) keeps the real anode face (Eqs. 26-27)."""
+    from dataclasses import replace
+
+    nx = grid.nx
+    if i == 0:
+        xs = slice(0, 3)
+        centre = (1, 1, 0)
+    elif i == nx - 1:
+        xs = slice(nx - 4, nx)
+        centre = (1, 1, 3)
+    else:
+        xs = slice(i - 2, i + 2)
+        centre = (1, 1, 2)
+    sl = (slice(k - 1, k + 2), slice(j - 1, j + 2), xs)
     ph = grid.phase[sl].copy()
-    ph[:, :, 0] = lis.STRUCT
+    if i != 0:
+        ph[:, :, 0] = lis.STRUCT
     g = lis.Grid(ph, grid.h)
-    d = {f: a[(slice(None),) * 3 + sl] for f, a in U.items()}
-    return g, lis.pack(model, g, d)
+    m = model
+    if i == 0:
+        j_face = lis.j_el(model, grid) * grid.ny * grid.nz / grid.n_cc
+        m = replace(model, j_el=j_face * g.n_cc / (g.ny * g.nz))
+
+    def pack(Uf):
+        d = {f: a[(slice(None),) * 3 + sl] for f, a in Uf.items()}
+        return lis.pack(m, g, d)
+    return m, g, pack, centre
 
 
-CENTRE = (1, 1, 2)
-
-
-def _centre(model, g, r):
+def _centre(model, g, r, centre):
     """Values of the centre voxel (all nodes, all fields present there) of a crop's flat vector."""
     R = lis.unpack(model, g, r)
-    st = g.phase[CENTRE] == lis.STRUCT
-    return np.concatenate([R[f][(slice(None),) * 3 + CENTRE].ravel() for f in model.chem.fields
+    st = g.phase[centre] == lis.STRUCT
+    return np.concatenate([R[f][(slice(None),) * 3 + centre].ravel() for f in model.chem.fields
                            if st or not model.chem.is_struct_field(f)])
 
 
 def test_dg1_128_sampled_residual_and_jvp():
+    """Interior voxels (structure and pore), collector-face structure voxels (x = 0) and anode-face
+    voxels (x = nx - 1): residual (1e-12 of the terms' size), the FP64 product of dg_jvp and of the
+    fused kernel (1e-12 |J||v|), and the fused FP32 product of the mixed-precision Krylov loop
+    (1e-5 |J||v|, the bound derived in test_gpu_fused_jvp)."""
+    import torch
+
+    from paper_2511_05233_gb300 import dgls
+
     phase = inputs.make_structure(N_SIDE, POROSITY, CORR, STRUCT_SEED)
     grid = lis.Grid(phase, 1e-6)
     model = lis.Model(ch.tradeoff(), order=1, f_C=F_C, eps_struct=1.0 - POROSITY)
@@ -57,14 +86,24 @@ def test_dg1_128_sampled_residual_and_jvp():
     z = init.perturb(model, grid, z0, inputs.uniform_noise(z0.size, NOISE_SEED))
     v = inputs.normal_noise(z0.size, 5) * (np.abs(z) + 1e-3)
     t, dt = 1.5, 1e-3
-    ctx = gpu_context(model, phase)
+    ctx = gpu_context(model, phase)                  # FP64: linearised dg_jvp and the fused FP64 kernel
     zd, z0d, vd = to_dev(z), to_dev(z0), to_dev(v)
     r = to_dev(np.zeros_like(z))
     ctx.residual(zd, z0d, t, dt, r)
-    jv = to_dev(np.zeros_like(z))
-    ctx.jvp(zd, t, dt, vd, jv)
-    R, JV = lis.unpack(model, grid, to_host(r)), lis.unpack(model, grid, to_host(jv))
-    del r, jv, zd, z0d, vd
+    R = lis.unpack(model, grid, to_host(r))
+    ctx.jvp(zd, t, dt, vd, r)
+    JV = lis.unpack(model, grid, to_host(r))
+    ctx.jvp_fused(zd, t, dt, vd, r)
+    JF = lis.unpack(model, grid, to_host(r))
+    del r
+    ctx.close()
+    ctx = gpu_context(model, phase, precision=dgls.MIXED)   # the FP32 product of the mixed Krylov loop
+    v32 = vd.float()
+    o32 = torch.empty_like(v32)
+    ctx.jvp_fused(zd, t, dt, v32, o32)
+    J32 = lis.unpack(model, grid, o32.double().cpu().numpy())
+    ctx.close()
+    del v32, o32, zd, z0d, vd
     U, U0, Uv = lis.unpack(model, grid, z), lis.unpack(model, grid, z0), lis.unpack(model, grid, v)
     rng = np.random.default_rng(0)
     picks = []
@@ -73,18 +112,26 @@ def test_dg1_128_sampled_residual_and_jvp():
         want_struct = len(picks) % 2 == 0
         if (phase[k, j, i] == lis.STRUCT) == want_struct:
             picks.append((k, j, i))
+    cc = 0
+    while cc < 3:                  # structure voxels on the collector face
+        k, j = rng.integers(1, N_SIDE - 1), rng.integers(1, N_SIDE - 1)
+        if phase[k, j, 0] == lis.STRUCT:
+            picks.append((k, j, 0))
+            cc += 1
+    for _ in range(3):             # anode-face voxels (separator)
+        picks.append((rng.integers(1, N_SIDE - 1), rng.integers(1, N_SIDE - 1), N_SIDE - 1))
     for k, j, i in picks:
-        g, zc = _crop(model, grid, U, k, j, i)
-        _, z0c = _crop(model, grid, U0, k, j, i)
-        _, vc = _crop(model, grid, Uv, k, j, i)
+        m, g, pack, centre = _crop(model, grid, U, k, j, i)
+        zc, z0c, vc = pack(U), pack(U0), pack(Uv)
         st = phase[k, j, i] == lis.STRUCT
         fields = [f for f in model.chem.fields if st or not model.chem.is_struct_field(f)]
-        got_r = np.concatenate([R[f][:, :, :, k, j, i].ravel() for f in fields])
-        got_jv = np.concatenate([JV[f][:, :, :, k, j, i].ravel() for f in fields])
-        ref_r = _centre(model, g, lis.residual(model, g, zc, z0c, t, dt))
-        mag_r = _centre(model, g, lis.residual_magnitude(model, g, zc, z0c, t, dt))
-        assert np.all(np.abs(got_r - ref_r) <= 1e-12 * mag_r), (k, j, i)
-        ref_jv = _centre(model, g, newton.jvp(model, g, zc, z0c, t, dt, vc))
-        mag_jv, _ = jvp_magnitude(model, g, zc, z0c, t, dt, vc)
-        mag_jv = _centre(model, g, mag_jv)
-        assert np.all(np.abs(got_jv - ref_jv) <= 1e-12 * mag_jv + 1e-300), (k, j, i)
+        pick = lambda A: np.concatenate([A[f][:, :, :, k, j, i].ravel() for f in fields])  # noqa: E731
+        ref_r = _centre(m, g, lis.residual(m, g, zc, z0c, t, dt), centre)
+        mag_r = _centre(m, g, lis.residual_magnitude(m, g, zc, z0c, t, dt), centre)
+        assert np.all(np.abs(pick(R) - ref_r) <= 1e-12 * mag_r), (k, j, i)
+        ref_jv = _centre(m, g, newton.jvp(m, g, zc, z0c, t, dt, vc), centre)
+        mag_jv, _ = jvp_magnitude(m, g, zc, z0c, t, dt, vc)
+        mag_jv = _centre(m, g, mag_jv, centre)
+        assert np.all(np.abs(pick(JV) - ref_jv) <= 1e-12 * mag_jv + 1e-300), (k, j, i)
+        assert np.all(np.abs(pick(JF) - ref_jv) <= 1e-12 * mag_jv + 1e-300), (k, j, i)
+        assert np.all(np.abs(pick(J32) - ref_jv) <= 1e-5 * mag_jv + 1e-30), (k, j, i)
