@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--batch", type=int, default=64, help="instances of the batched workload (0: skip)")
+    ap.add_argument("--serve", type=int, default=24, help="requests of the serving workload (0: skip)")
+    ap.add_argument("--serve-steps", type=int, default=3)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrivals per second")
     return ap.parse_args()
 
 
@@ -275,6 +280,134 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batch_specs(n, seed=11, side=(24, 96)):
+    """Instances of the batched workload: cubic sides uniform in side, porosity uniform in 0.4-0.8,
+    correlation length uniform in 2-8 voxels, C-rate log-uniform in 0.1-2 per hour, DG0 or DG1 at
+    50/50 (seeded)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        out.append(dict(side=int(rng.integers(side[0], side[1] + 1)), porosity=float(rng.uniform(0.4, 0.8)),
+                        corr=float(rng.uniform(2.0, 8.0)), f_C=float(np.exp(rng.uniform(np.log(0.1), np.log(2.0)))),
+                        order=int(k % 2), seed=100 + k))
+    return out
+
+
+def run_batch(a, dgls, torch, reps=5):
+    """Batched instances: FP32 Jacobian-vector products of all instances as one launch per kind
+    against the same products one instance at a time, and one implicit step of every instance run
+    concurrently against the same steps one after another (all mixed precision).  Wall clock with the
+    device synchronised around each measurement."""
+    from paper_2511_05233_gb300 import inputs
+
+    specs = batch_specs(a.batch)
+    ctxs, zs, vs, outs = [], [], [], []
+    for sp in specs:
+        phase = None
+        for s_ in range(sp["seed"], sp["seed"] + 50):
+            ph = inputs.make_structure(sp["side"], sp["porosity"], sp["corr"], s_)
+            if np.any(ph[:, :, 0] == inputs.STRUCT):
+                phase = ph
+                break
+        prm = dgls.default_params(dgls.TRADEOFF, sp["order"], f_C=sp["f_C"], eps_struct=1 - sp["porosity"],
+                                  precision=dgls.MIXED)
+        ctx = dgls.Context(phase, WORKLOAD["h"], prm, stream=torch.cuda.Stream())
+        z = ctx.new_state()
+        ctx.equilibrium_state(z)
+        noise = torch.from_numpy(inputs.uniform_noise(ctx.n_dof, sp["seed"])).cuda()
+        z[: ctx.offsets[6]] *= 1.0 + 0.01 * noise[: ctx.offsets[6]]
+        ctxs.append(ctx)
+        zs.append(z)
+        vs.append((torch.from_numpy(inputs.normal_noise(ctx.n_dof, sp["seed"] + 1)).cuda() * (z.abs() + 1e-3)).float())
+        outs.append(torch.empty_like(vs[-1]))
+    torch.cuda.synchronize()
+    units = sum(c.n_dof for c in ctxs)
+    ts, dts = [0.0] * len(ctxs), [WORKLOAD["dt"]] * len(ctxs)
+    st = torch.cuda.current_stream()
+    batch = dgls.Batch(ctxs, stream=st)
+    choice = batch.autotune(zs, ts, dts, vs, outs)
+
+    def wall(fn):
+        """Wall-clock ms per call with the device synchronised before and after (launch overheads
+        included: batching removes them)."""
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t0) / reps
+
+    l0 = batch.launch_count()
+    ms_b = wall(lambda: batch.jvp(zs, ts, dts, vs, outs))
+    launches_b = (batch.launch_count() - l0) / (reps + 1)
+
+    def one_at_a_time():               # each instance's product, waiting for it before the next
+        for c, z, v, o in zip(ctxs, zs, vs, outs):
+            c.jvp_fused(z, 0.0, WORKLOAD["dt"], v, o)
+            c.stream.synchronize()
+
+    def streams():                     # every instance's product on its own stream, then one wait
+        for c, z, v, o in zip(ctxs, zs, vs, outs):
+            c.jvp_fused(z, 0.0, WORKLOAD["dt"], v, o)
+    ms_1 = wall(one_at_a_time)
+    ms_s = wall(streams)
+    # implicit steps: concurrently (one host thread per instance, each on its context's stream) and
+    # one after another, wall-clock (each step synchronises)
+    zo = [torch.empty_like(z) for z in zs]
+    batch.step(zs, zo, ts, dts)                      # warm-up
+    t0 = time.perf_counter()
+    sts, infos = batch.step(zs, zo, ts, dts)
+    ms_step_b = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    for c, z, o in zip(ctxs, zs, zo):
+        c.step(z, o, 0.0, WORKLOAD["dt"], check=False)
+    ms_step_1 = 1e3 * (time.perf_counter() - t0)
+    res = {"instances": len(ctxs), "n_dof_total": units,
+           "sides": [sp["side"] for sp in specs], "orders": [sp["order"] for sp in specs],
+           "workload": f"{len(ctxs)} instances, sides uniform 24-96, porosity 0.4-0.8, correlation length 2-8, "
+                       f"C-rate log-uniform 0.1-2, DG0/DG1 alternating, mixed precision (FP32 products)",
+           "schedule": {"dg1_block_order": ["instance after instance", "round robin"][choice[0]],
+                        "dg0_block_size": choice[1]},
+           "jvp_batched_ms": ms_b, "jvp_one_at_a_time_ms": ms_1, "jvp_gain": ms_1 / ms_b,
+           "jvp_separate_streams_ms": ms_s, "jvp_gain_vs_streams": ms_s / ms_b, "timing": "wall clock, device synchronised",
+           "jvp_batched_gdof_s": units / (ms_b / 1e3) / 1e9, "jvp_batched_launches": launches_b,
+           "step_concurrent_ms": ms_step_b, "step_sequential_ms": ms_step_1, "step_gain": ms_step_1 / ms_step_b,
+           "steps_converged": int(sum(1 for s_, i in zip(sts, infos) if s_ == dgls.OK and i.converged))}
+    batch.close()
+    for c in ctxs:
+        c.close()
+    del zs, vs, outs, zo
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_serving(a, dgls):
+    """The serving workload: a seeded Poisson stream of discharge requests (cubic sides 32-128, DG0 and
+    DG1, C-rate log-uniform 0.1-2 per hour), each capped at a few accepted steps of the naive
+    controller; served with continuous batching (slots with pooled workspaces, an HBM budget of
+    150 GB, mixed precision) against the plain sequential FP64 loop on the same requests.  Structures
+    are generated before the clocks start."""
+    import copy
+
+    from paper_2511_05233_gb300 import serve
+
+    reqs = serve.make_requests(a.serve, rate_hz=a.serve_rate, seed=7, side_range=(32, 128), n_steps=a.serve_steps)
+    for r in reqs:
+        serve.request_structure(r)
+    served, wall = serve.serve(copy.deepcopy(reqs), slots=a.serve_slots, hbm_budget=150 << 30,
+                               precision=dgls.MIXED, keep_state=True)
+    seqd, wall_seq = serve.sequential(copy.deepcopy(reqs), precision=dgls.FP64, keep_state=True)
+    st_s, st_q = serve.latency_stats(served, wall), serve.latency_stats(seqd, wall_seq)
+    return {"requests": len(reqs), "steps_per_request": a.serve_steps, "slots": a.serve_slots,
+            "arrival_rate_hz": a.serve_rate, "hbm_budget_gb": 150,
+            "sides": [r.side for r in reqs], "orders": [r.order for r in reqs],
+            "served_mixed": st_s, "sequential_fp64": st_q,
+            "throughput_gain": st_s["sims_per_hr"] / st_q["sims_per_hr"], "p99_gain": st_q["p99_s"] / st_s["p99_s"],
+            "max_rel_diff_vs_fp64": serve.max_rel_diff(served, seqd),
+            "statuses": sorted({str(r.result.get("status")) for r in served})}
+
+
 def config_dict(a):
     return {"workload": f"{a.n}^3 voxel grid, DG{a.order}, {'Tradeoff Chemistry (6 liquid species, 2 solids, 2 potentials)' if a.chem == 'tradeoff' else 'three-species chemistry'}, "
                         f"Gaussian random-field structure porosity {WORKLOAD['porosity']}, correlation length {WORKLOAD['corr_len']} voxels, "
@@ -458,6 +591,25 @@ def main():
         ctx32.close()
         del z32
 
+    batched = None
+    if rank == 0 and (a.batch > 0 or a.serve > 0):   # the workload's own context is done: free its HBM
+        ctx.close()
+        del zn, z
+        torch.cuda.empty_cache()
+    if rank == 0 and a.batch > 0:
+        try:
+            batched = run_batch(a, dgls, torch)
+        except Exception as e:  # reported in the line, the main figures stand
+            batched = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+    serving = None
+    if rank == 0 and a.serve > 0:
+        try:
+            serving = run_serving(a, dgls)
+        except Exception as e:
+            serving = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu, _, _ = oracle_sample(a, budget_s=15.0)
@@ -473,7 +625,7 @@ def main():
                 "evals_per_step": evals / a.steps, "gpu_launches": launches,
                 "gram_schmidt_second_passes": reorth, "roofline": roof, "kernels": kern,
                 "kernel_breakdown_ms": breakdown, "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
-                "mixed_precision": mixed}
+                "mixed_precision": mixed, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -171,6 +171,19 @@ dg_status dg_params_default(dg_params* p, int32_t chemistry, int32_t order);
  * DG_ERR_ARG if no structure voxel touches the current collector or the anode layer is not
  * liquid; DG_ERR_OOM if the workspace exceeds hbm_budget_bytes.  Synchronous. */
 dg_status dg_setup(const dg_structure* s, const dg_params* p, void* cuda_stream, dg_ctx** out);
+
+/* Device bytes that dg_setup_in needs for this structure and these parameters (every workspace the
+ * context holds, each on a 256-byte boundary), computed without allocating or touching the device
+ * (no counterpart in the paper: it sizes admission and buffer reuse in a server).  DG_ERR_ARG as
+ * dg_setup.  Host only. */
+dg_status dg_workspace_estimate(const dg_structure* s, const dg_params* p, int64_t* bytes);
+
+/* dg_setup with every workspace carved from the caller's device buffer workspace_dev (256-byte
+ * aligned, workspace_bytes long, at least dg_workspace_estimate's bytes; DG_ERR_OOM if smaller) instead
+ * of cudaMalloc, so that a caller can keep a buffer and reuse it for the next context once this one is
+ * destroyed.  The caller owns the buffer and must keep it allocated until dg_destroy.  Synchronous. */
+dg_status dg_setup_in(const dg_structure* s, const dg_params* p, void* cuda_stream, void* workspace_dev,
+                      int64_t workspace_bytes, dg_ctx** out);
 dg_status dg_destroy(dg_ctx* ctx);
 const char* dg_last_error(const dg_ctx* ctx);
 
@@ -213,13 +226,14 @@ dg_status dg_residual_noalloc(dg_ctx* ctx, const double* z_dev, const double* zo
 dg_status dg_jvp(dg_ctx* ctx, const double* z_dev, double t, double dt,
                  const double* v_dev, double* jv_dev);
 
-/* Jacobian-vector product J(z) v of dg_jvp by the fused matrix-free kernel (one launch that reads
- * z and v once and writes J v once; forward-mode dual numbers, Eqs. 43-48 with the Tab. 4 system):
- * the product the Krylov loop of a mixed-precision context runs.  precision DG_PREC_FP64: v_dev and
- * jv_dev are n_dof doubles and the arithmetic is FP64; DG_PREC_MIXED: they are n_dof floats, z is
- * rounded to FP32 on the device and the arithmetic is FP32 (the context must have been set up with
- * precision DG_PREC_MIXED, which holds the FP32 copy of z).  Rows unscaled, as dg_jvp.  DG1 contexts
- * only (DG_ERR_ARG otherwise).  Asynchronous. */
+/* Jacobian-vector product J(z) v of dg_jvp by the matrix-free kernels the Krylov loop of a
+ * mixed-precision context runs (forward-mode dual numbers, nothing cached; Eqs. 43-48 with the
+ * Tab. 4 system): for DG1 the fused kernel, one launch that reads z and v once and writes J v once;
+ * for DG0 the two-launch product (transport factors, then voxels).  precision DG_PREC_FP64: v_dev
+ * and jv_dev are n_dof doubles and the arithmetic is FP64; DG_PREC_MIXED: they are n_dof floats, z
+ * is rounded to FP32 on the device and the arithmetic is FP32 (the context must have been set up
+ * with precision DG_PREC_MIXED, which holds the FP32 copy of z).  Rows unscaled, as dg_jvp.
+ * Asynchronous. */
 dg_status dg_jvp_fused(dg_ctx* ctx, const double* z_dev, double t, double dt, int32_t precision,
                        const void* v_dev, void* jv_dev);
 
@@ -274,6 +288,51 @@ dg_status dg_profile_read(const dg_ctx* ctx, double ms[5], int64_t calls[5]);
  * non-negative nodal concentrations.  Solid fractions and potentials are left alone.  DG_ERR_ARG for
  * DG0 contexts.  Asynchronous on the context's stream; uses the context's scratch. */
 dg_status dg_limit(dg_ctx* ctx, double* z_dev);
+
+/* ---- Batches: several independent cells (uneven grids, DG0 and DG1, one chemistry) evaluated
+ * together (no counterpart in the paper, which runs one cell per job).  The products and the DG0
+ * residual of all instances run as one launch per kind over the instances' concatenated blocks, with
+ * each instance's parameters, geometry and buffers in device job records; the blocks go through the
+ * same device functions as a single instance, so every instance gets the result it gets alone.  The
+ * batch keeps its own launch stream; its calls use the contexts' scratch buffers, so a context must
+ * not run work of its own while a batch call that contains it is in flight. */
+typedef struct dg_batch dg_batch;
+
+/* Batch of n contexts (all of one chemistry; DG_ERR_ARG otherwise) launching on cuda_stream (NULL:
+ * legacy default stream).  Allocates the schedules and job records once.  The contexts stay owned
+ * by the caller and must outlive the batch.  Synchronous. */
+dg_status dg_batch_create(dg_ctx* const* ctxs, int32_t n, void* cuda_stream, dg_batch** out);
+dg_status dg_batch_destroy(dg_batch* b);
+const char* dg_batch_last_error(const dg_batch* b);
+/* Kernels this batch has launched (monotone counter). */
+int64_t dg_batch_launch_count(const dg_batch* b);
+
+/* Per instance k: jv[k] = J_k(z[k]) v[k], the product dg_jvp_fused computes for that context (host
+ * arrays of n device pointers and n times; precision as dg_jvp_fused, MIXED needs mixed contexts).
+ * One launch for all DG1 instances, two for all DG0 instances (plus one FP32 rounding launch for
+ * MIXED).  Asynchronous on the batch stream. */
+dg_status dg_batch_jvp(dg_batch* b, const double* const* z_dev, const double* t, const double* dt,
+                       int32_t precision, const void* const* v_dev, void* const* jv_dev);
+
+/* Per instance k: r[k] = R_k(z[k]; zold[k], t[k], dt[k]) as dg_residual.  DG0 instances: two launches
+ * for all; DG1 instances: each instance's own face-once kernels, issued on the batch stream.
+ * Asynchronous on the batch stream. */
+dg_status dg_batch_residual(dg_batch* b, const double* const* z_dev, const double* const* zold_dev,
+                            const double* t, const double* dt, double* const* r_dev);
+
+/* Schedule autotuner: times the batch's products on these inputs (one warm-up and three timed
+ * launches per candidate, CUDA events on the batch stream) for each block order of the DG1 launch
+ * (0: instance after instance, 1: one block of every instance in turn) and each block size of the
+ * DG0 launches (64, 128, 256, 512 voxels), keeps the fastest for later calls and reports them in
+ * choice[0] (DG1 order) and choice[1] (DG0 block size).  Overwrites jv.  Synchronous. */
+dg_status dg_batch_autotune(dg_batch* b, const double* const* z_dev, const double* t, const double* dt,
+                            int32_t precision, const void* const* v_dev, void* const* jv_dev, int32_t choice[2]);
+
+/* One implicit Euler step of every instance (dg_step of each context, concurrently from host threads,
+ * each on its own context's stream): status[k] receives dg_step's status, info[k] (if info) its
+ * statistics.  Returns DG_OK unless the arguments are bad.  Synchronous. */
+dg_status dg_batch_step(dg_batch* b, const double* const* zn_dev, double* const* z_dev, const double* t,
+                        const double* dt, dg_step_info* info, int32_t* status);
 
 /* Number of CUDA kernels this context has launched (monotone counter). */
 int64_t dg_launch_count(const dg_ctx* ctx);

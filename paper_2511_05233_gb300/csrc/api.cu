@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dgls.h"
@@ -19,6 +20,7 @@ constexpr int DRES_ONE = 99;
 static const double kOne = 1.0;
 
 struct dg_ctx {
+    DevArena arena;                // workspace from a caller buffer (dg_setup_in) or counted (estimate)
     dg_params prm;
     DevParams P;
     Geo G;
@@ -60,6 +62,16 @@ struct dg_ctx {
     int sp_pairs = 0;
     bool sp_on = false;            // species correction built for the current preconditioner
     float* z32 = nullptr;
+    // products of dg_jvp_fused and of the FP32 Krylov loop run the batched kernels with a one-job
+    // table (the same compiled kernels as in a batch): a ring of job records, pinned staging and the
+    // events that say when the device has read a staging slot
+    static constexpr int RING = 4;
+    unsigned char* d_ring = nullptr;   // RING x JOB_SLOT bytes
+    unsigned char* h_ring = nullptr;
+    cudaEvent_t ring_ev[RING] = {};
+    int ring_next = 0;
+    int2* d_map_self = nullptr;        // (0, b) for every block of this grid (the largest block count of any kind)
+    int nblk_fused = 0, nblk_dg0 = 0;
     // discharge work states
     double *za = nullptr, *zb = nullptr, *zC = nullptr, *zF = nullptr;
     // reductions
@@ -200,15 +212,20 @@ template <class T>
 static cudaError_t dalloc(dg_ctx* ctx, T** ptr, int64_t n) {
     if (n <= 0) n = 1;
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, (size_t)n * sizeof(T));
+    cudaError_t e = ctx->arena.active ? arena_alloc(&ctx->arena, (size_t)n * sizeof(T), &q)
+                                      : cudaMalloc(&q, (size_t)n * sizeof(T));
     if (e != cudaSuccess) return e;
-    ctx->allocs.push_back(q);
+    if (!ctx->arena.active) ctx->allocs.push_back(q);
     ctx->ws_bytes += n * (int64_t)sizeof(T);
     *ptr = (T*)q;
     return cudaSuccess;
 }
 
 static void free_all(dg_ctx* ctx) {
+    for (int k = 0; k < dg_ctx::RING; ++k)
+        if (ctx->ring_ev[k]) { cudaEventDestroy(ctx->ring_ev[k]); ctx->ring_ev[k] = nullptr; }
+    if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
+    ctx->h_ring = nullptr;
     for (auto& e : ctx->ev) { ctx->ev_pool.push_back(e.second.first); ctx->ev_pool.push_back(e.second.second); }
     ctx->ev.clear();
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -219,7 +236,10 @@ static void free_all(dg_ctx* ctx) {
     ctx->hres = nullptr;
 }
 
-extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void* stream, dg_ctx** out) {
+// Set up a context; with arena the workspaces come from the caller's buffer, and with count the
+// allocations are only counted (*count receives the bytes) and no context is returned.
+static dg_status setup_impl(const dg_structure* s, const dg_params* prm, void* stream, const DevArena* arena,
+                            int64_t* count, dg_ctx** out) {
     if (!out) return DG_ERR_ARG;
     *out = nullptr;
     if (!s || !prm || !s->phase || s->nx < 2 || s->ny < 1 || s->nz < 1 || !(s->h > 0)) return DG_ERR_ARG;
@@ -234,6 +254,8 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     const int64_t ncell64 = (int64_t)s->nx * s->ny * s->nz;
     if (ncell64 > 2000000000LL) return DG_ERR_ARG;
     dg_ctx* ctx = new dg_ctx();
+    if (arena) ctx->arena = *arena;
+    if (count) ctx->arena = DevArena{nullptr, 0, 0, true};
     ctx->prm = *prm;
     ctx->L.st = (cudaStream_t)stream;
     ctx->L.counter = &ctx->launches;
@@ -326,6 +348,28 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     }
     P.penalty = prm->penalty;
     P.smooth = prm->smooth;
+    // derived constants (the kernels read them instead of forming them at run time) and their FP32 copies
+    P.icref = 1.0 / P.cref;
+    P.is8ref = 1.0 / P.s8ref;
+    P.ili2sref = 1.0 / P.li2sref;
+    for (int q = 0; q < 2; ++q) P.isqK[q] = 1.0 / P.sqK[q];
+    for (int k = 0; k < 6; ++k) P.FU2RT[k] = P.F_2RT * P.U0[k];
+    P.one_m_cbd = 1.0 - P.cbd;
+    P.eps_frozen_sum = P.eps_frozen[0] + P.eps_frozen[1];
+    {
+        DevParams::F32& f = P.f;
+        f.F = (float)P.F; f.F_2RT = (float)P.F_2RT; f.icref = (float)P.icref; f.visc = (float)P.visc;
+        f.eps_sep = (float)P.eps_sep; f.one_m_cbd = (float)P.one_m_cbd; f.eps_frozen_sum = (float)P.eps_frozen_sum;
+        f.aV0p = (float)P.aV0p; f.is8ref = (float)P.is8ref; f.ili2sref = (float)P.ili2sref;
+        for (int m = 0; m < 6; ++m) {
+            f.wS[m] = (float)P.wS[m]; f.kE[m] = (float)P.kE[m]; f.FU2RT[m] = (float)P.FU2RT[m];
+            f.eUf[m] = (float)P.eUf[m]; f.eUb[m] = (float)P.eUb[m];
+        }
+        for (int q = 0; q < 2; ++q) {
+            f.sqK[q] = (float)P.sqK[q]; f.isqK[q] = (float)P.isqK[q]; f.kC[q] = (float)P.kC[q];
+            f.eps_frozen[q] = (float)P.eps_frozen[q];
+        }
+    }
     const int nn = prm->order == 1 ? 8 : 1;
     const double M = prm->order == 1 ? P.V / 8.0 : P.V;
     int64_t off = 0;
@@ -371,7 +415,7 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         const int hier = 1 + (prm->species_mg != 0 ? (P.nl + 1) / 2 : 0);
         need += hier * ncell * 175;
     }
-    if (prm->hbm_budget_bytes > 0 && need > prm->hbm_budget_bytes) {
+    if (!count && prm->hbm_budget_bytes > 0 && need > prm->hbm_budget_bytes) {
         dg_status st = fail(ctx, DG_ERR_OOM, "workspace of " + std::to_string(need) + " bytes exceeds hbm_budget_bytes");
         delete ctx;
         return st;
@@ -394,6 +438,10 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     AL(ctx->zc, N); AL(ctx->zt, N); AL(ctx->R, N); AL(ctx->Rt, N); AL(ctx->dz, N); AL(ctx->zn, N);
     AL(ctx->za, N); AL(ctx->zb, N); AL(ctx->zC, N); AL(ctx->zF, N);
     AL(ctx->partial, (int64_t)RED_BLOCKS * MAXK + 64);
+    ctx->nblk_fused = (ncell + FUSED_VOXELS - 1) / FUSED_VOXELS;
+    ctx->nblk_dg0 = (ncell + 127) / 128;
+    AL(ctx->d_ring, (int64_t)dg_ctx::RING * JOB_SLOT);
+    AL(ctx->d_map_self, std::max(ctx->nblk_fused, ctx->nblk_dg0));
     AL(ctx->dres, 256);
     AL(ctx->d_vals, DG_MAXF);
     if (mixed) {
@@ -429,7 +477,8 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
         }
         ctx->has_lin = true;
     }
-    if (prm->preconditioner != 0 && mg_levels_alloc(ctx->mg, nx, ny, nz, ctx->allocs, &ctx->ws_bytes) != cudaSuccess) {
+    if (prm->preconditioner != 0 &&
+        mg_levels_alloc(ctx->mg, nx, ny, nz, ctx->allocs, &ctx->ws_bytes, &ctx->arena) != cudaSuccess) {
         free_all(ctx);
         delete ctx;
         return DG_ERR_OOM;
@@ -437,17 +486,39 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     if (prm->preconditioner != 0 && prm->species_mg != 0) {
         ctx->sp_pairs = (P.nl + 1) / 2;
         for (int k = 0; k < ctx->sp_pairs; ++k)
-            if (mg_levels_alloc(ctx->mgsp[k], nx, ny, nz, ctx->allocs, &ctx->ws_bytes) != cudaSuccess) {
+            if (mg_levels_alloc(ctx->mgsp[k], nx, ny, nz, ctx->allocs, &ctx->ws_bytes, &ctx->arena) != cudaSuccess) {
                 free_all(ctx);
                 delete ctx;
                 return DG_ERR_OOM;
             }
     }
 #undef AL
-    if (cudaMallocHost(&ctx->hres, 256 * sizeof(double)) != cudaSuccess) {
+    if (count) {   // sizing only: nothing was allocated
+        *count = ctx->arena.used;
+        delete ctx;
+        return DG_OK;
+    }
+    if (cudaMallocHost(&ctx->hres, 256 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_ring, dg_ctx::RING * JOB_SLOT) != cudaSuccess) {
         free_all(ctx);
         delete ctx;
         return DG_ERR_OOM;
+    }
+    for (int k = 0; k < dg_ctx::RING; ++k)
+        if (cudaEventCreateWithFlags(&ctx->ring_ev[k], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(ctx->ring_ev[k], (cudaStream_t)stream) != cudaSuccess) {
+            free_all(ctx);
+            delete ctx;
+            return DG_ERR_CUDA;
+        }
+    {
+        std::vector<int2> self(std::max(ctx->nblk_fused, ctx->nblk_dg0));
+        for (size_t b = 0; b < self.size(); ++b) self[b] = make_int2(0, (int)b);
+        if (cudaMemcpy(ctx->d_map_self, self.data(), self.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
+            free_all(ctx);
+            delete ctx;
+            return DG_ERR_CUDA;
+        }
     }
     cudaStream_t st = ctx->L.st;
     if (cudaMemcpyAsync(ctx->d_phase, s->phase, ncell, cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -465,6 +536,26 @@ extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void*
     ctx->G.sidx = ctx->d_sidx;
     *out = ctx;
     return DG_OK;
+}
+
+extern "C" dg_status dg_setup(const dg_structure* s, const dg_params* prm, void* stream, dg_ctx** out) {
+    return setup_impl(s, prm, stream, nullptr, nullptr, out);
+}
+
+extern "C" dg_status dg_setup_in(const dg_structure* s, const dg_params* prm, void* stream, void* workspace_dev,
+                                 int64_t workspace_bytes, dg_ctx** out) {
+    if (!workspace_dev || workspace_bytes <= 0 || ((uintptr_t)workspace_dev % 256) != 0) {
+        if (out) *out = nullptr;
+        return DG_ERR_ARG;
+    }
+    DevArena a{(char*)workspace_dev, workspace_bytes, 0, true};
+    return setup_impl(s, prm, stream, &a, nullptr, out);
+}
+
+extern "C" dg_status dg_workspace_estimate(const dg_structure* s, const dg_params* prm, int64_t* bytes) {
+    if (!bytes) return DG_ERR_ARG;
+    dg_ctx* none = nullptr;
+    return setup_impl(s, prm, nullptr, nullptr, bytes, &none);
 }
 
 extern "C" dg_status dg_destroy(dg_ctx* ctx) {
@@ -505,6 +596,45 @@ static dg_status residual_(dg_ctx* ctx, const double* z, const double* zn, doubl
 
 // J v through the kernels for this context: the cached linearisation when it is valid and stored in
 // the product's precision (DG1), otherwise forward-mode dual numbers.
+// One instance's product through the batched kernels (a one-job table): the record goes to the
+// next ring slot once the device has read that slot's previous upload.
+template <class S>
+static cudaError_t fused_self(dg_ctx* ctx, const S* z, const S* v, double t, double dt, int relax, double sc_dt, S* out,
+                              S* gb, S* gbd) {
+    const bool f32 = std::is_same<S, float>::value;
+    const int k = ctx->ring_next;
+    ctx->ring_next = (k + 1) % dg_ctx::RING;
+    cudaError_t e = cudaEventSynchronize(ctx->ring_ev[k]);
+    if (e != cudaSuccess) return e;
+    unsigned char* h = ctx->h_ring + (size_t)k * JOB_SLOT;
+    unsigned char* d = ctx->d_ring + (size_t)k * JOB_SLOT;
+    size_t bytes;
+    if (ctx->P.order == 1) {
+        dg1_fused_job(f32, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, h);
+        bytes = dg1_job_bytes(f32);
+    } else {
+        Job0<S>* J = reinterpret_cast<Job0<S>*>(h);
+        std::memset((void*)J, 0, sizeof(*J));
+        J->p = ctx->P;
+        J->g = ctx->G;
+        J->z = z;
+        J->v = v;
+        J->gb = gb;
+        J->gbd = gbd;
+        J->out = out;
+        J->t = t;
+        J->dt = dt;
+        J->sc_dt = sc_dt;
+        J->relax = relax;
+        bytes = sizeof(Job0<S>);
+    }
+    if ((e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, ctx->L.st)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ctx->ring_ev[k], ctx->L.st)) != cudaSuccess) return e;
+    const bool to = ctx->P.nf == 10;
+    if (ctx->P.order == 1) return dg1_jvp_fused_batched(ctx->L, f32, to, d, ctx->d_map_self, ctx->nblk_fused);
+    return dg0_batch<S>(ctx->L, to, 1, (const Job0<S>*)d, ctx->d_map_self, ctx->nblk_dg0, 128);
+}
+
 template <class S>
 static bool use_fused(const dg_ctx* ctx) {
     return ctx->P.order == 1 && (ctx->prm.jvp_form == 2 || (ctx->prm.jvp_form == 0 && std::is_same<S, float>::value));
@@ -513,7 +643,7 @@ static bool use_fused(const dg_ctx* ctx) {
 template <class S>
 static cudaError_t jvp_kernels(dg_ctx* ctx, const S* z, const S* v, double t, double dt, int relax, double sc_dt, S* out,
                                S* gb, S* gbd) {
-    if (use_fused<S>(ctx)) return dg1_jvp_fused<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out);
+    if (use_fused<S>(ctx)) return fused_self<S>(ctx, z, v, t, dt, relax, sc_dt, out, gb, gbd);
     if (ctx->has_lin && ctx->lin_valid && std::is_same<S, float>::value == ctx->lin.f32)
         return dg1_lin_apply<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, ctx->lin);
     return ctx->P.order == 0 ? dg0_jvp<S>(ctx->L, ctx->P, ctx->G, z, v, t, dt, relax, sc_dt, out, gb, gbd)
@@ -662,10 +792,9 @@ extern "C" dg_status dg_jvp(dg_ctx* ctx, const double* z, double t, double dt, c
 extern "C" dg_status dg_jvp_fused(dg_ctx* ctx, const double* z, double t, double dt, int32_t precision, const void* v,
                                   void* jv) {
     if (!ctx || !z || !v || !jv || !(dt > 0)) return fail(ctx, DG_ERR_ARG, "dg_jvp_fused: bad argument");
-    if (ctx->P.order != 1) return fail(ctx, DG_ERR_ARG, "dg_jvp_fused: DG1 contexts only");
     if (precision == DG_PREC_FP64) {
         ProfScope ps(ctx, 1);
-        CK(dg1_jvp_fused<double>(ctx->L, ctx->P, ctx->G, z, (const double*)v, t, dt, 0, 0.0, (double*)jv));
+        CK(fused_self<double>(ctx, z, (const double*)v, t, dt, 0, 0.0, (double*)jv, ctx->gb, ctx->gbd));
         return DG_OK;
     }
     if (precision != DG_PREC_MIXED) return fail(ctx, DG_ERR_ARG, "dg_jvp_fused: precision must be FP64 or MIXED");
@@ -673,7 +802,7 @@ extern "C" dg_status dg_jvp_fused(dg_ctx* ctx, const double* z, double t, double
         return fail(ctx, DG_ERR_ARG, "dg_jvp_fused: an FP32 product needs a context set up with DG_PREC_MIXED");
     CK(to_f32(ctx->L, ctx->z32, z, ctx->ndof));
     ProfScope ps(ctx, 1);
-    CK(dg1_jvp_fused<float>(ctx->L, ctx->P, ctx->G, ctx->z32, (const float*)v, t, dt, 0, 0.0, (float*)jv));
+    CK(fused_self<float>(ctx, ctx->z32, (const float*)v, t, dt, 0, 0.0, (float*)jv, ctx->gb32, ctx->gbd32));
     return DG_OK;
 }
 
@@ -1172,5 +1301,324 @@ extern "C" dg_status dg_residual_noalloc(dg_ctx* ctx, const double* z, const dou
     LaunchCtx L{ctx->L.st, &launches};
     e = dg0_residual(L, ctx->P, ctx->G, z, zold, t, dt, 0, r, scratch);
     if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("dg_residual_noalloc: ") + cudaGetErrorString(e));
+    return DG_OK;
+}
+
+// ------------------------------------------------------------------ batches of instances
+// Several contexts (uneven grids, either DG order, one chemistry) evaluated together: the fused
+// DG1 product, the DG0 product and the DG0 residual of all instances each run as one launch over
+// the instances' concatenated blocks (job records in device memory, block -> (instance, block)
+// maps as the schedule); implicit steps of all instances run concurrently, each on its own
+// context's stream.
+struct dg_batch {
+    std::vector<dg_ctx*> ctx;
+    LaunchCtx L{};
+    int64_t launches = 0;
+    std::string err;
+    bool tradeoff = true;
+    std::vector<int> k0, k1;                       // instances of order 0 and 1
+    static constexpr int N_SCHED1 = 2, N_BS0 = 4;  // DG1 block orders; DG0 block sizes
+    int2* d_map1[N_SCHED1] = {};
+    int nblk1 = 0;
+    int2* d_map0[N_BS0] = {};
+    int nblk0[N_BS0] = {};
+    int bs0[N_BS0] = {64, 128, 256, 512};
+    int2* d_mapc = nullptr;                        // FP32 conversion of every instance's z
+    int nblkc = 0;
+    int sched1 = 0, sched0 = 1;                    // schedules in use (dg_batch_autotune chooses)
+    size_t sz1 = 0;                                // bytes of one DG1 job record (the larger precision)
+    unsigned char *d_job1 = nullptr, *h_job1 = nullptr;
+    Job0<double>* d_job0 = nullptr;                // Job0<float> has the same size (pointers, doubles)
+    Job0<double>* h_job0 = nullptr;
+    ConvJob *d_conv = nullptr, *h_conv = nullptr;
+    cudaEvent_t staged = nullptr;                  // the device has read the staging buffers
+    std::vector<void*> dev, host;
+};
+
+// the host writes FP32 and FP64 DG0 job records into one array: they must have the same size
+static_assert(sizeof(Job0<float>) == sizeof(Job0<double>), "DG0 job records of both precisions");
+
+static dg_status bfail(dg_batch* b, dg_status s, const std::string& m) {
+    if (b) b->err = m;
+    return s;
+}
+#define BCK(x)                                                                                        \
+    do {                                                                                              \
+        cudaError_t e_ = (x);                                                                         \
+        if (e_ != cudaSuccess) return bfail(b, DG_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void batch_free(dg_batch* b) {
+    for (void* p : b->dev) cudaFree(p);
+    for (void* p : b->host) cudaFreeHost(p);
+    if (b->staged) cudaEventDestroy(b->staged);
+    b->dev.clear();
+    b->host.clear();
+}
+
+// block -> (instance, block) maps: instance after instance, or one block of each instance in turn
+static std::vector<int2> batch_map(const std::vector<int64_t>& nb, bool round_robin) {
+    std::vector<int2> m;
+    if (!round_robin) {
+        for (size_t j = 0; j < nb.size(); ++j)
+            for (int64_t q = 0; q < nb[j]; ++q) m.push_back(make_int2((int)j, (int)q));
+        return m;
+    }
+    int64_t most = 0;
+    for (int64_t x : nb) most = std::max(most, x);
+    for (int64_t q = 0; q < most; ++q)
+        for (size_t j = 0; j < nb.size(); ++j)
+            if (q < nb[j]) m.push_back(make_int2((int)j, (int)q));
+    return m;
+}
+
+extern "C" dg_status dg_batch_create(dg_ctx* const* ctxs, int32_t n, void* stream, dg_batch** out) {
+    if (!out) return DG_ERR_ARG;
+    *out = nullptr;
+    if (!ctxs || n < 1) return DG_ERR_ARG;
+    dg_batch* b = new dg_batch;
+    b->L.st = (cudaStream_t)stream;
+    b->L.counter = &b->launches;
+    for (int k = 0; k < n; ++k) {
+        if (!ctxs[k]) { delete b; return DG_ERR_ARG; }
+        b->ctx.push_back(ctxs[k]);
+        (ctxs[k]->P.order == 1 ? b->k1 : b->k0).push_back(k);
+    }
+    b->tradeoff = ctxs[0]->P.nf == 10;
+    for (dg_ctx* c : b->ctx)
+        if ((c->P.nf == 10) != b->tradeoff) { delete b; return DG_ERR_ARG; }   // one chemistry per batch
+    auto upload = [&](const std::vector<int2>& m, int2** d) -> cudaError_t {
+        cudaError_t e = cudaMalloc((void**)d, std::max<size_t>(1, m.size()) * sizeof(int2));
+        if (e != cudaSuccess) return e;
+        b->dev.push_back(*d);
+        return m.empty() ? cudaSuccess : cudaMemcpy(*d, m.data(), m.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    };
+    cudaError_t e = cudaSuccess;
+    std::vector<int64_t> nb1;
+    for (int k : b->k1) nb1.push_back((b->ctx[k]->P.n_cell + FUSED_VOXELS - 1) / FUSED_VOXELS);
+    for (int s = 0; s < dg_batch::N_SCHED1 && e == cudaSuccess; ++s) {
+        std::vector<int2> m = batch_map(nb1, s == 1);
+        b->nblk1 = (int)m.size();
+        e = upload(m, &b->d_map1[s]);
+    }
+    for (int q = 0; q < dg_batch::N_BS0 && e == cudaSuccess; ++q) {
+        std::vector<int64_t> nb0;
+        for (int k : b->k0) nb0.push_back((b->ctx[k]->P.n_cell + b->bs0[q] - 1) / b->bs0[q]);
+        std::vector<int2> m = batch_map(nb0, false);
+        b->nblk0[q] = (int)m.size();
+        e = upload(m, &b->d_map0[q]);
+    }
+    if (e == cudaSuccess) {
+        std::vector<int64_t> nbc;
+        for (dg_ctx* c : b->ctx) nbc.push_back((c->ndof + CONV_BLOCK_ELEMS - 1) / CONV_BLOCK_ELEMS);
+        std::vector<int2> m = batch_map(nbc, false);
+        b->nblkc = (int)m.size();
+        e = upload(m, &b->d_mapc);
+    }
+    b->sz1 = std::max(dg1_job_bytes(false), dg1_job_bytes(true));
+    auto dal = [&](void** p, size_t bytes) -> cudaError_t {
+        cudaError_t r = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (r == cudaSuccess) b->dev.push_back(*p);
+        return r;
+    };
+    auto hal = [&](void** p, size_t bytes) -> cudaError_t {
+        cudaError_t r = cudaMallocHost(p, std::max<size_t>(bytes, 16));
+        if (r == cudaSuccess) b->host.push_back(*p);
+        return r;
+    };
+    if (e == cudaSuccess) e = dal((void**)&b->d_job1, n * b->sz1);
+    if (e == cudaSuccess) e = hal((void**)&b->h_job1, n * b->sz1);
+    if (e == cudaSuccess) e = dal((void**)&b->d_job0, n * sizeof(Job0<double>));
+    if (e == cudaSuccess) e = hal((void**)&b->h_job0, n * sizeof(Job0<double>));
+    if (e == cudaSuccess) e = dal((void**)&b->d_conv, n * sizeof(ConvJob));
+    if (e == cudaSuccess) e = hal((void**)&b->h_conv, n * sizeof(ConvJob));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+    if (e == cudaSuccess && b->staged) e = cudaEventRecord(b->staged, b->L.st);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        delete b;
+        return DG_ERR_CUDA;
+    }
+    *out = b;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_batch_destroy(dg_batch* b) {
+    if (!b) return DG_ERR_ARG;
+    cudaStreamSynchronize(b->L.st);
+    batch_free(b);
+    delete b;
+    return DG_OK;
+}
+
+extern "C" const char* dg_batch_last_error(const dg_batch* b) { return b ? b->err.c_str() : "null batch"; }
+extern "C" int64_t dg_batch_launch_count(const dg_batch* b) { return b ? b->launches : 0; }
+
+// the staging buffers may be rewritten once the device has read the previous upload
+static dg_status batch_stage_wait(dg_batch* b) {
+    BCK(cudaEventSynchronize(b->staged));
+    return DG_OK;
+}
+
+static dg_status batch_upload(dg_batch* b, bool j1, bool j0, bool conv) {
+    const int n = (int)b->ctx.size();
+    if (j1) BCK(cudaMemcpyAsync(b->d_job1, b->h_job1, n * b->sz1, cudaMemcpyHostToDevice, b->L.st));
+    if (j0) BCK(cudaMemcpyAsync(b->d_job0, b->h_job0, n * sizeof(Job0<double>), cudaMemcpyHostToDevice, b->L.st));
+    if (conv) BCK(cudaMemcpyAsync(b->d_conv, b->h_conv, n * sizeof(ConvJob), cudaMemcpyHostToDevice, b->L.st));
+    BCK(cudaEventRecord(b->staged, b->L.st));
+    return DG_OK;
+}
+
+template <class S>
+static void job0_fill(dg_ctx* c, const S* z, const S* v, const double* zn, double t, double dt, S* out, Job0<S>* J) {
+    std::memset((void*)J, 0, sizeof(*J));
+    J->p = c->P;
+    J->g = c->G;
+    J->z = z;
+    J->v = v;
+    J->zn = zn;
+    const bool f32 = std::is_same<S, float>::value;
+    J->gb = f32 ? (S*)c->gb32 : (S*)c->gb;
+    J->gbd = f32 ? (S*)c->gbd32 : (S*)c->gbd;
+    J->out = out;
+    J->t = t;
+    J->dt = dt;
+    J->sc_dt = 0.0;
+    J->relax = 0;
+}
+
+// launch the products of all instances (the jobs are uploaded; sched: schedules to use)
+static dg_status batch_jvp_launch(dg_batch* b, bool f32, int s1, int s0) {
+    if (f32) BCK(to_f32_batched(b->L, b->d_conv, b->d_mapc, b->nblkc));
+    BCK(dg1_jvp_fused_batched(b->L, f32, b->tradeoff, b->d_job1, b->d_map1[s1], b->k1.empty() ? 0 : b->nblk1));
+    if (f32) BCK(dg0_batch<float>(b->L, b->tradeoff, 1, (const Job0<float>*)b->d_job0, b->d_map0[s0], b->nblk0[s0], b->bs0[s0]));
+    else BCK(dg0_batch<double>(b->L, b->tradeoff, 1, b->d_job0, b->d_map0[s0], b->nblk0[s0], b->bs0[s0]));
+    return DG_OK;
+}
+
+static dg_status batch_jvp_stage(dg_batch* b, const double* const* z, const double* t, const double* dt,
+                                 int32_t precision, const void* const* v, void* const* jv) {
+    if (!z || !t || !dt || !v || !jv) return bfail(b, DG_ERR_ARG, "dg_batch_jvp: bad argument");
+    const bool f32 = precision == DG_PREC_MIXED;
+    if (!f32 && precision != DG_PREC_FP64) return bfail(b, DG_ERR_ARG, "dg_batch_jvp: precision must be FP64 or MIXED");
+    for (size_t k = 0; k < b->ctx.size(); ++k) {
+        if (!z[k] || !v[k] || !jv[k] || !(dt[k] > 0)) return bfail(b, DG_ERR_ARG, "dg_batch_jvp: bad instance argument");
+        if (f32 && (b->ctx[k]->prm.precision != DG_PREC_MIXED || !b->ctx[k]->z32))
+            return bfail(b, DG_ERR_ARG, "dg_batch_jvp: FP32 products need contexts set up with DG_PREC_MIXED");
+    }
+    dg_status s = batch_stage_wait(b);
+    if (s != DG_OK) return s;
+    const size_t sz = dg1_job_bytes(f32);          // the kernel of this precision indexes records at its size
+    for (size_t j = 0; j < b->k1.size(); ++j) {
+        dg_ctx* c = b->ctx[b->k1[j]];
+        const int k = b->k1[j];
+        const void* zz = f32 ? (const void*)c->z32 : (const void*)z[k];
+        dg1_fused_job(f32, c->P, c->G, zz, v[k], t[k], dt[k], 0, 0.0, jv[k], b->h_job1 + j * sz);
+    }
+    for (size_t j = 0; j < b->k0.size(); ++j) {
+        const int k = b->k0[j];
+        dg_ctx* c = b->ctx[k];
+        if (f32) job0_fill<float>(c, c->z32, (const float*)v[k], nullptr, t[k], dt[k], (float*)jv[k], (Job0<float>*)(b->h_job0 + j));
+        else job0_fill<double>(c, z[k], (const double*)v[k], nullptr, t[k], dt[k], (double*)jv[k], b->h_job0 + j);
+    }
+    for (size_t k = 0; k < b->ctx.size(); ++k) b->h_conv[k] = ConvJob{z[k], b->ctx[k]->z32, b->ctx[k]->ndof};
+    return batch_upload(b, true, true, f32);
+}
+
+extern "C" dg_status dg_batch_jvp(dg_batch* b, const double* const* z, const double* t, const double* dt,
+                                  int32_t precision, const void* const* v, void* const* jv) {
+    if (!b) return DG_ERR_ARG;
+    dg_status s = batch_jvp_stage(b, z, t, dt, precision, v, jv);
+    if (s != DG_OK) return s;
+    return batch_jvp_launch(b, precision == DG_PREC_MIXED, b->sched1, b->sched0);
+}
+
+extern "C" dg_status dg_batch_residual(dg_batch* b, const double* const* z, const double* const* zold,
+                                       const double* t, const double* dt, double* const* r) {
+    if (!b) return DG_ERR_ARG;
+    if (!z || !zold || !t || !dt || !r) return bfail(b, DG_ERR_ARG, "dg_batch_residual: bad argument");
+    for (size_t k = 0; k < b->ctx.size(); ++k)
+        if (!z[k] || !zold[k] || !r[k] || !(dt[k] > 0)) return bfail(b, DG_ERR_ARG, "dg_batch_residual: bad instance argument");
+    dg_status s = batch_stage_wait(b);
+    if (s != DG_OK) return s;
+    for (size_t j = 0; j < b->k0.size(); ++j) {
+        const int k = b->k0[j];
+        job0_fill<double>(b->ctx[k], z[k], z[k], zold[k], t[k], dt[k], r[k], b->h_job0 + j);
+    }
+    s = batch_upload(b, false, true, false);
+    if (s != DG_OK) return s;
+    // 128-voxel blocks, the block size of the single-instance residual kernels
+    BCK(dg0_batch<double>(b->L, b->tradeoff, 0, b->d_job0, b->d_map0[1], b->nblk0[1], b->bs0[1]));
+    // DG1 residuals: the instances' own face-once kernels, issued on the batch stream
+    for (int k : b->k1) {
+        dg_ctx* c = b->ctx[k];
+        BCK(dg1_residual(b->L, c->P, c->G, z[k], zold[k], t[k], dt[k], 0, r[k], c->gb, c->gbd));
+    }
+    return DG_OK;
+}
+
+extern "C" dg_status dg_batch_autotune(dg_batch* b, const double* const* z, const double* t, const double* dt,
+                                       int32_t precision, const void* const* v, void* const* jv, int32_t choice[2]) {
+    if (!b) return DG_ERR_ARG;
+    dg_status s = batch_jvp_stage(b, z, t, dt, precision, v, jv);
+    if (s != DG_OK) return s;
+    const bool f32 = precision == DG_PREC_MIXED;
+    if (f32) BCK(to_f32_batched(b->L, b->d_conv, b->d_mapc, b->nblkc));
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    auto timed = [&](auto launch) -> double {
+        launch();                                   // warm-up
+        cudaEventRecord(e0, b->L.st);
+        for (int r = 0; r < 3; ++r) launch();
+        cudaEventRecord(e1, b->L.st);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    // a candidate whose launches fail is not a candidate (its time would be that of doing nothing)
+    cudaError_t trial = cudaSuccess;
+    double best = 1e30;
+    if (!b->k1.empty()) {
+        for (int q = 0; q < dg_batch::N_SCHED1; ++q) {
+            trial = cudaSuccess;
+            double ms = timed([&] {
+                cudaError_t r = dg1_jvp_fused_batched(b->L, f32, b->tradeoff, b->d_job1, b->d_map1[q], b->nblk1);
+                if (r != cudaSuccess) trial = r;
+            });
+            if (trial == cudaSuccess && ms < best) { best = ms; b->sched1 = q; }
+        }
+    }
+    best = 1e30;
+    if (!b->k0.empty()) {
+        const int maxbs = dg0_batch_max_block(b->tradeoff, f32);
+        for (int q = 0; q < dg_batch::N_BS0; ++q) {
+            if (b->bs0[q] > maxbs) continue;
+            trial = cudaSuccess;
+            double ms = timed([&] {
+                cudaError_t r = f32 ? dg0_batch<float>(b->L, b->tradeoff, 1, (const Job0<float>*)b->d_job0, b->d_map0[q],
+                                                       b->nblk0[q], b->bs0[q])
+                                    : dg0_batch<double>(b->L, b->tradeoff, 1, b->d_job0, b->d_map0[q], b->nblk0[q], b->bs0[q]);
+                if (r != cudaSuccess) trial = r;
+            });
+            if (trial == cudaSuccess && ms < best) { best = ms; b->sched0 = q; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BCK(cudaGetLastError());
+    if (choice) { choice[0] = b->sched1; choice[1] = b->bs0[b->sched0]; }
+    return DG_OK;
+}
+
+extern "C" dg_status dg_batch_step(dg_batch* b, const double* const* zn, double* const* z, const double* t,
+                                   const double* dt, dg_step_info* info, int32_t* status) {
+    if (!b || !zn || !z || !t || !dt || !status) return bfail(b, DG_ERR_ARG, "dg_batch_step: bad argument");
+    const size_t n = b->ctx.size();
+    std::vector<std::thread> th;
+    for (size_t k = 0; k < n; ++k)
+        th.emplace_back([&, k] { status[k] = dg_step(b->ctx[k], zn[k], z[k], t[k], dt[k], info ? info + k : nullptr); });
+    for (auto& x : th) x.join();
     return DG_OK;
 }

@@ -49,7 +49,26 @@ struct DevParams {
     int64_t flen[DG_MAXF];     // field lengths (per node for DG1)
     int is_struct[DG_MAXF];    // field lives on structure voxels only
     double rscale[DG_MAXF];    // Newton row scales divided by dt (per field)
+    // derived on the host, so that no kernel divides or multiplies constants in FP64 at run time
+    double icref, is8ref, ili2sref;  // 1/c_ref, 1/s8ref, 1/li2sref
+    double isqK[2];                  // 1/sqrt(K_sp) of C1, C2
+    double FU2RT[6];                 // F U0_k / (2RT)
+    double one_m_cbd;                // 1 - CBD fraction (liquid fraction of a solid-free structure voxel)
+    double eps_frozen_sum;           // sum of the frozen solid fractions (three-species chemistry)
+    // the constants of the pointwise model rounded to FP32, read by the FP32 instantiations (an FP32
+    // kernel that converted the FP64 constants would spend FP64-pipe issue slots on every conversion)
+    struct F32 {
+        float F, F_2RT, icref, visc, eps_sep, one_m_cbd, eps_frozen_sum, aV0p, is8ref, ili2sref;
+        float wS[6], kE[6], FU2RT[6], eUf[6], eUb[6], sqK[2], isqK[2], kC[2], eps_frozen[2];
+    } f;
 };
+
+// A model constant in the arithmetic type of the caller: the FP64 value for double, its FP32 copy
+// for float.
+template <class Sc> __device__ __forceinline__ Sc pv(double d, float f);
+template <> __device__ __forceinline__ double pv<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pv<float>(double, float f) { return f; }
+#define PV(Sc, name) pv<Sc>(p.name, p.f.name)
 
 // ------------------------------------------------------------------------------ dual numbers
 template <class S>
@@ -72,12 +91,15 @@ template <class S> __device__ __forceinline__ Dual<S> operator-(S a, Dual<S> b) 
 template <class S> __device__ __forceinline__ Dual<S>& operator+=(Dual<S>& a, Dual<S> b) { a.v += b.v; a.d += b.d; return a; }
 template <class S> __device__ __forceinline__ Dual<S>& operator-=(Dual<S>& a, Dual<S> b) { a.v -= b.v; a.d -= b.d; return a; }
 
+// FP32 exponential and logarithm by the hardware approximations (relative error about 2^-22 plus
+// |x| 2^-24 for the exponential): the FP32 instantiations only feed the Krylov loop of the
+// mixed-precision solver, whose FP64 Newton iteration tests the true residual
 __device__ __forceinline__ double sexp(double x) { return exp(x); }
-__device__ __forceinline__ float sexp(float x) { return expf(x); }
+__device__ __forceinline__ float sexp(float x) { return __expf(x); }
 __device__ __forceinline__ double ssqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float ssqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double slog(double x) { return log(x); }
-__device__ __forceinline__ float slog(float x) { return logf(x); }
+__device__ __forceinline__ float slog(float x) { return __logf(x); }
 __device__ __forceinline__ double scbrt(double x) { return cbrt(x); }
 __device__ __forceinline__ float scbrt(float x) { return cbrtf(x); }
 
@@ -92,10 +114,12 @@ template <class T> __device__ __forceinline__ T cst(double v) { return T(v); }
 
 template <class T> struct Make {
     static __device__ __forceinline__ T c(double v) { return T(v); }
+    static __device__ __forceinline__ T cs(T v) { return v; }   // a constant already in the scalar type
     static __device__ __forceinline__ T var(double v, double d) { return T(v); }
 };
 template <class S> struct Make<Dual<S>> {
     static __device__ __forceinline__ Dual<S> c(double v) { return mkd<S>(S(v), S(0)); }
+    static __device__ __forceinline__ Dual<S> cs(S v) { return mkd<S>(v, S(0)); }
     static __device__ __forceinline__ Dual<S> var(double v, double d) { return mkd<S>(S(v), S(d)); }
 };
 
@@ -121,9 +145,12 @@ template <class S> __device__ __forceinline__ Dual<S> act_cbrt(Dual<S> a) {
     S r = scbrt(a.v);
     return mkd(r, a.d / (S(3) * r * r));
 }
-template <class S> __device__ __forceinline__ S srcp(S a) { return S(1) / a; }
+// correctly rounded reciprocal (the same value as 1/a; in FP32 without the division's slow path)
+__device__ __forceinline__ double rcp_rn(double a) { return 1.0 / a; }
+__device__ __forceinline__ float rcp_rn(float a) { return __frcp_rn(a); }
+template <class S> __device__ __forceinline__ S srcp(S a) { return rcp_rn(a); }
 template <class S> __device__ __forceinline__ Dual<S> srcp(Dual<S> a) {
-    S r = S(1) / a.v;
+    S r = rcp_rn(a.v);
     return mkd(r, -a.d * r * r);
 }
 
@@ -138,13 +165,13 @@ template <class T> __device__ __forceinline__ T pow15(T x) {
     return Make<T>::c(0.0);
 }
 
-// log of an activity a = max(c, 0)/c_ref: -inf (with zero tangent) at a <= 0, so that
-// exp(nu log a - x) vanishes like the mass-action product a^nu does.
-template <class S> __device__ __forceinline__ S log_act(S c, double cref) {
-    return c > S(0) ? slog(c / S(cref)) : -S(INFINITY);
+// log of an activity a = max(c, 0)/c_ref (icref = 1/c_ref): -inf (with zero tangent) at a <= 0, so
+// that exp(nu log a - x) vanishes like the mass-action product a^nu does.
+template <class S> __device__ __forceinline__ S log_act(S c, S icref) {
+    return c > S(0) ? slog(c * icref) : -S(INFINITY);
 }
-template <class S> __device__ __forceinline__ Dual<S> log_act(Dual<S> c, double cref) {
-    if (c.v > S(0)) return mkd(slog(c.v / S(cref)), c.d / c.v);
+template <class S> __device__ __forceinline__ Dual<S> log_act(Dual<S> c, S icref) {
+    if (c.v > S(0)) return mkd(slog(c.v * icref), c.d * rcp_rn(c.v));
     return mkd(-S(INFINITY), S(0));
 }
 
@@ -156,7 +183,7 @@ template <class S> __device__ __forceinline__ S harm(S a, S b) {
 // dual version with one division: dH = 2 (b^2 da + a^2 db) / (a + b)^2
 template <class S> __device__ __forceinline__ Dual<S> harm(Dual<S> a, Dual<S> b) {
     if (a.v * b.v > S(0)) {
-        S r = S(1) / (a.v + b.v);
+        S r = rcp_rn(a.v + b.v);
         S h = S(2) * a.v * b.v * r;
         S d = S(2) * r * r * (b.v * b.v * a.d + a.v * a.v * b.d);
         return mkd(h, d);
@@ -184,36 +211,38 @@ struct ChemTO {
 // separator, 1 in macro-pores.
 template <class Chem, class T>
 __device__ __forceinline__ T liquid_fraction(const DevParams& p, int ph, const T* es) {
+    typedef typename Base<T>::type Sc;
     if (ph == 1) {
-        T s = Make<T>::c(1.0 - p.cbd);
+        T s = Make<T>::cs(PV(Sc, one_m_cbd));
         if (Chem::NS == 2) {
             s = s - es[0];
             s = s - es[1];
         } else {
-            s = s - Make<T>::c(p.eps_frozen[0] + p.eps_frozen[1]);
+            s = s - Make<T>::cs(PV(Sc, eps_frozen_sum));
         }
         return s;
     }
-    return Make<T>::c(ph == 2 ? p.eps_sep : 1.0);
+    return Make<T>::cs(ph == 2 ? PV(Sc, eps_sep) : Sc(1));
 }
 
 // g = max(eps_L,0)^{3/2} exp(-7.76e-4 c_S): Bruggeman (Eq. 18 final) x Stokes-Einstein (Eqs. 2-3)
 template <class Chem, class T>
 __device__ __forceinline__ T transport_factor(const DevParams& p, T epsL, const T* c) {
+    typedef typename Base<T>::type Sc;
     T cS = Make<T>::c(0.0);
 #pragma unroll
     for (int m = 0; m < Chem::NL; ++m)
-        if (p.wS[m] != 0.0) cS = cS + c[m] * (typename Base<T>::type)(p.wS[m]);
-    return pow15(epsL) * sexp(cS * (typename Base<T>::type)(-p.visc));
+        if (p.f.wS[m] != 0.0f) cS = cS + c[m] * PV(Sc, wS[m]);   // FP32 test: no FP64 compare in FP32 code
+    return pow15(epsL) * sexp(cS * (-PV(Sc, visc)));
 }
 
 // Specific surface a_V, Eq. 18 with the Eq. 57 localisation
 template <class T>
 __device__ __forceinline__ T specific_surface(const DevParams& p, T e8, T e2) {
     typedef typename Base<T>::type S;
-    T t1 = pow15(e8 * S(1.0 / p.s8ref));
-    T t2 = pow15(e2 * S(1.0 / p.li2sref));
-    return pos(Make<T>::c(1.0) - t1 - t2) * S(p.aV0p);
+    T t1 = pow15(e8 * PV(S, is8ref));
+    T t2 = pow15(e2 * PV(S, ili2sref));
+    return pos(Make<T>::c(1.0) - t1 - t2) * PV(S, aV0p);
 }
 
 // Reaction sources at a structure point (mol m^-3 s^-1 for species, A m^-3 for the charges):
@@ -221,34 +250,35 @@ __device__ __forceinline__ T specific_surface(const DevParams& p, T e8, T e2) {
 //   q_L = -F a_V sum_E k_E,k r_k,  q_S = +F a_V sum_E k_E,k r_k           (Tab. 4 rows 2 and 4)
 // with r_C = <a>_r sqrt(K) - <a>_p / sqrt(K) and r_E = <a>_r e^{-x} - <a>_p e^{x},
 // x = F (Phi^S - Phi^L - U0)/(2RT): the Butler-Volmer forms of Eqs. 19-24 at alpha = 1/2.
-template <class Chem, class T>
+template <class Chem, class T, class TH>
 __device__ __forceinline__ void sources(const DevParams& p, const T* c, const T* es, T phiL, T phiS,
-                                        double tH, T* S, T* Ss, T& qL, T& qS) {
+                                        TH tH, T* S, T* Ss, T& qL, T& qS) {
     typedef typename Base<T>::type Sc;
     const T zero = Make<T>::c(0.0);
-    T eta = (phiS - phiL) * Sc(p.F_2RT);
+    T eta = (phiS - phiL) * PV(Sc, F_2RT);
     if constexpr (Chem::NS == 0) {
         // three-species: E1 only, solids frozen
-        T aV = Make<T>::c(p.aV0p);
+        T aV;
         {
-            T e8 = Make<T>::c(p.eps_frozen[0]), e2 = Make<T>::c(p.eps_frozen[1]);
+            T e8 = Make<T>::cs(PV(Sc, eps_frozen[0])), e2 = Make<T>::cs(PV(Sc, eps_frozen[1]));
             aV = specific_surface<T>(p, e8, e2);
         }
+        const Sc icr = PV(Sc, icref);
         T r1;
         if constexpr (std::is_same<Sc, double>::value) {
             T ep = sexp(eta), em = srcp(ep);
-            T s1 = act_sqrt(pos(c[1]) * Sc(1.0 / p.cref)), s2 = act_sqrt(pos(c[2]) * Sc(1.0 / p.cref));
+            T s1 = act_sqrt(pos(c[1]) * icr), s2 = act_sqrt(pos(c[2]) * icr);
             r1 = s1 * em * Sc(p.eUf[0]) - s2 * ep * Sc(p.eUb[0]);
         } else {
-            T la1 = log_act(c[1], p.cref), la2 = log_act(c[2], p.cref);
-            T x1 = eta - Make<T>::c(p.F_2RT * p.U0[0]);
+            T la1 = log_act(c[1], icr), la2 = log_act(c[2], icr);
+            T x1 = eta - Make<T>::cs(PV(Sc, FU2RT[0]));
             r1 = sexp(la1 * Sc(0.5) - x1) - sexp(la2 * Sc(0.5) + x1);
         }
-        T w1 = aV * r1 * Sc(p.kE[0]);
+        T w1 = aV * r1 * PV(Sc, kE[0]);
         S[0] = zero;
         S[1] = w1 * Sc(-0.5);
         S[2] = w1 * Sc(0.5);
-        qS = w1 * Sc(p.F);
+        qS = w1 * PV(Sc, F);
         qL = -qS;
         return;
     } else if constexpr (std::is_same<Sc, double>::value) {
@@ -257,7 +287,7 @@ __device__ __forceinline__ void sources(const DevParams& p, const T* c, const T*
         // reciprocal, three square roots and three cube roots per point instead of six
         // logarithms and twelve exponentials.
         T aV = specific_surface<T>(p, es[0], es[1]);
-        const Sc icr = Sc(1.0 / p.cref);
+        const Sc icr = Sc(p.icref);
         T a0 = pos(c[0]) * icr, a1 = pos(c[1]) * icr, a2 = pos(c[2]) * icr;
         T a3 = pos(c[3]) * icr, a4 = pos(c[4]) * icr, a5 = pos(c[5]) * icr;
         T ep = sexp(eta), em = srcp(ep);
@@ -272,8 +302,8 @@ __device__ __forceinline__ void sources(const DevParams& p, const T* c, const T*
         T r4 = (q4 * em * Sc(p.eUf[3]) - q5 * q5 * ep * Sc(p.eUb[3])) * th;
         T r5 = s2 * em * Sc(p.eUf[4]) - a4 * ep * Sc(p.eUb[4]);
         T r6 = q4 * a0 * cLi * em * Sc(p.eUf[5]) - ep * Sc(p.eUb[5]);
-        T rc1 = Make<T>::c(p.sqK[0]) - a1 * Sc(1.0 / p.sqK[0]);
-        T rc2 = (Make<T>::c(p.sqK[1]) - a0 * a0 * a5 * Sc(1.0 / p.sqK[1])) * th;
+        T rc1 = Make<T>::c(p.sqK[0]) - a1 * Sc(p.isqK[0]);
+        T rc2 = (Make<T>::c(p.sqK[1]) - a0 * a0 * a5 * Sc(p.isqK[1])) * th;
         T wc1 = es[0] * rc1 * Sc(p.kC[0]);
         T wc2 = es[1] * rc2 * Sc(p.kC[1]);
         T w1 = aV * r1 * Sc(p.kE[0]);
@@ -296,13 +326,14 @@ __device__ __forceinline__ void sources(const DevParams& p, const T* c, const T*
         // FP32: exponents formed as differences of O(1) numbers, which cannot overflow for the
         // potentials a Newton iterate may take
         T aV = specific_surface<T>(p, es[0], es[1]);
+        const Sc icr = PV(Sc, icref);
         T la[6];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) la[m] = log_act(c[m], p.cref);
+        for (int m = 0; m < 6; ++m) la[m] = log_act(c[m], icr);
         T x[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) x[k] = eta - Make<T>::c(p.F_2RT * p.U0[k]);
-        const Sc th = Sc(p.smooth ? tH : 1.0);
+        for (int k = 0; k < 6; ++k) x[k] = eta - Make<T>::cs(PV(Sc, FU2RT[k]));
+        const Sc th = p.smooth ? Sc(tH) : Sc(1);
         // electrochemical rates, Tab. 3 rows E1..E6
         T r1 = sexp(la[1] * Sc(0.5) - x[0]) - sexp(la[2] * Sc(0.5) + x[0]);
         T r2 = sexp(la[2] * Sc(1.5) - x[1]) - sexp(la[3] * Sc(2.0) + x[1]);
@@ -311,17 +342,17 @@ __device__ __forceinline__ void sources(const DevParams& p, const T* c, const T*
         T r5 = sexp(la[2] * Sc(0.5) - x[4]) - sexp(la[4] + x[4]);
         T r6 = sexp(la[4] * Sc(1.0 / 6.0) + la[0] * Sc(4.0 / 3.0) - x[5]) - sexp(x[5]);
         // chemical rates C1, C2 (solid reactant, activity 1)
-        T a0 = pos(c[0]) * Sc(1.0 / p.cref), a1 = pos(c[1]) * Sc(1.0 / p.cref), a5 = pos(c[5]) * Sc(1.0 / p.cref);
-        T rc1 = Make<T>::c(p.sqK[0]) - a1 * Sc(1.0 / p.sqK[0]);
-        T rc2 = (Make<T>::c(p.sqK[1]) - a0 * a0 * a5 * Sc(1.0 / p.sqK[1])) * th;
-        T wc1 = es[0] * rc1 * Sc(p.kC[0]);
-        T wc2 = es[1] * rc2 * Sc(p.kC[1]);
-        T w1 = aV * r1 * Sc(p.kE[0]);
-        T w2 = aV * r2 * Sc(p.kE[1]);
-        T w3 = aV * r3 * Sc(p.kE[2]);
-        T w4 = aV * r4 * Sc(p.kE[3]);
-        T w5 = aV * r5 * Sc(p.kE[4]);
-        T w6 = aV * r6 * Sc(p.kE[5]);
+        T a0 = pos(c[0]) * icr, a1 = pos(c[1]) * icr, a5 = pos(c[5]) * icr;
+        T rc1 = Make<T>::cs(PV(Sc, sqK[0])) - a1 * PV(Sc, isqK[0]);
+        T rc2 = (Make<T>::cs(PV(Sc, sqK[1])) - a0 * a0 * a5 * PV(Sc, isqK[1])) * th;
+        T wc1 = es[0] * rc1 * PV(Sc, kC[0]);
+        T wc2 = es[1] * rc2 * PV(Sc, kC[1]);
+        T w1 = aV * r1 * PV(Sc, kE[0]);
+        T w2 = aV * r2 * PV(Sc, kE[1]);
+        T w3 = aV * r3 * PV(Sc, kE[2]);
+        T w4 = aV * r4 * PV(Sc, kE[3]);
+        T w5 = aV * r5 * PV(Sc, kE[4]);
+        T w6 = aV * r6 * PV(Sc, kE[5]);
         S[0] = wc2 * Sc(2.0) - w6 * Sc(4.0 / 3.0);
         S[1] = wc1 - w1 * Sc(0.5);
         S[2] = w1 * Sc(0.5) - w2 * Sc(1.5) - w5 * Sc(0.5);
@@ -330,7 +361,7 @@ __device__ __forceinline__ void sources(const DevParams& p, const T* c, const T*
         S[5] = wc2 + w4 * Sc(2.0 / 3.0);
         Ss[0] = -wc1;
         Ss[1] = w6 * Sc(2.0 / 3.0) - wc2;
-        qS = (w1 + w2 + w3 + w4 + w5 + w6) * Sc(p.F);
+        qS = (w1 + w2 + w3 + w4 + w5 + w6) * PV(Sc, F);
         qL = -qS;
     }
 }
@@ -339,8 +370,8 @@ __device__ __forceinline__ void sources(const DevParams& p, const T* c, const T*
 template <class T>
 __device__ __forceinline__ T anode_rate(const DevParams& p, T cLi, T phiL) {
     typedef typename Base<T>::type Sc;
-    T x = phiL * Sc(-p.F_2RT);
-    return pos(cLi) * Sc(1.0 / p.cref) * sexp(-x) - sexp(x);
+    T x = phiL * (-PV(Sc, F_2RT));
+    return pos(cLi) * PV(Sc, icref) * sexp(-x) - sexp(x);
 }
 
 }  // namespace dgls

@@ -11,6 +11,8 @@
 // field); a first pass stores g (and its tangent) per voxel so that neighbours do not
 // recompute the viscosity exponential; each thread then evaluates its own reactions once and
 // its six faces.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace dgls {
@@ -116,10 +118,8 @@ __device__ __forceinline__ void dg0_cell(const DevParams& p, int i, int j, int k
 
 // ------------------------------------------------------------------ pass 1: transport factor
 template <class Chem, class S, bool TAN>
-__global__ void __launch_bounds__(128) k_dg0_g(const DevParams p, const Geo g, const S* __restrict__ z,
-                                               const S* __restrict__ v, S* __restrict__ gb, S* __restrict__ gbd) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= p.n_cell) return;
+__device__ __forceinline__ void dg0_g_cell(const DevParams& p, const Geo& g, const S* __restrict__ z,
+                                           const S* __restrict__ v, S* __restrict__ gb, S* __restrict__ gbd, int cell) {
     int ph = g.phase[cell];
     int sidx = g.cmap[cell];
     typedef typename std::conditional<TAN, Dual<S>, S>::type T;
@@ -143,6 +143,14 @@ __global__ void __launch_bounds__(128) k_dg0_g(const DevParams p, const Geo g, c
     if (TAN) {
         if constexpr (TAN) gbd[cell] = gg.d;
     }
+}
+
+template <class Chem, class S, bool TAN>
+__global__ void __launch_bounds__(128) k_dg0_g(const DevParams p, const Geo g, const S* __restrict__ z,
+                                               const S* __restrict__ v, S* __restrict__ gb, S* __restrict__ gbd) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    dg0_g_cell<Chem, S, TAN>(p, g, z, v, gb, gbd, cell);
 }
 
 template <class Chem, class S, bool TAN, bool OWN, class T>
@@ -181,11 +189,9 @@ __device__ __forceinline__ void load_vals(const DevParams& p, const Geo& g, int 
 
 // ------------------------------------------------------------------ residual
 template <class Chem>
-__global__ void __launch_bounds__(128) k_dg0_res(const DevParams p, const Geo g, const double* __restrict__ z,
-                                                 const double* __restrict__ zn, const double* __restrict__ gb,
-                                                 double t, double dt, int relax, double* __restrict__ r) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= p.n_cell) return;
+__device__ __forceinline__ void dg0_res_cell(const DevParams& p, const Geo& g, const double* __restrict__ z,
+                                             const double* __restrict__ zn, const double* __restrict__ gb,
+                                             double t, double dt, int relax, double* __restrict__ r, int cell) {
     int i, j, k;
     cell_ijk(p, cell, i, j, k);
     CellVals<Chem, double> P;
@@ -208,14 +214,21 @@ __global__ void __launch_bounds__(128) k_dg0_res(const DevParams p, const Geo g,
     }
 }
 
-// ------------------------------------------------------------------ Jacobian-vector product
-template <class Chem, class S>
-__global__ void __launch_bounds__(128) k_dg0_jvp(const DevParams p, const Geo g, const S* __restrict__ z,
-                                                 const S* __restrict__ v, const S* __restrict__ gb,
-                                                 const S* __restrict__ gbd, double t, double dt, int relax,
-                                                 double sc_dt, S* __restrict__ out) {
+template <class Chem>
+__global__ void __launch_bounds__(128) k_dg0_res(const DevParams p, const Geo g, const double* __restrict__ z,
+                                                 const double* __restrict__ zn, const double* __restrict__ gb,
+                                                 double t, double dt, int relax, double* __restrict__ r) {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= p.n_cell) return;
+    dg0_res_cell<Chem>(p, g, z, zn, gb, t, dt, relax, r, cell);
+}
+
+// ------------------------------------------------------------------ Jacobian-vector product
+template <class Chem, class S>
+__device__ __forceinline__ void dg0_jvp_cell(const DevParams& p, const Geo& g, const S* __restrict__ z,
+                                             const S* __restrict__ v, const S* __restrict__ gb,
+                                             const S* __restrict__ gbd, double t, double dt, int relax,
+                                             double sc_dt, S* __restrict__ out, int cell) {
     typedef Dual<S> T;
     int i, j, k;
     cell_ijk(p, cell, i, j, k);
@@ -236,6 +249,16 @@ __global__ void __launch_bounds__(128) k_dg0_jvp(const DevParams p, const Geo g,
         if (!p.is_struct[f]) out[p.off[f] + cell] = o;
         else if (st) out[p.off[f] + P.sidx] = o;
     }
+}
+
+template <class Chem, class S>
+__global__ void __launch_bounds__(128) k_dg0_jvp(const DevParams p, const Geo g, const S* __restrict__ z,
+                                                 const S* __restrict__ v, const S* __restrict__ gb,
+                                                 const S* __restrict__ gbd, double t, double dt, int relax,
+                                                 double sc_dt, S* __restrict__ out) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.n_cell) return;
+    dg0_jvp_cell<Chem, S>(p, g, z, v, gb, gbd, t, dt, relax, sc_dt, out, cell);
 }
 
 // ------------------------------------------------------------------ diagonal blocks of S J
@@ -339,5 +362,92 @@ cudaError_t dg0_gfactor(const LaunchCtx& L, const DevParams& p, const Geo& g, co
     *L.counter += 1;
     return cudaGetLastError();
 }
+
+// ------------------------------------------------------------------ batched instances
+// One launch over the voxels of several DG0 instances (each its own grid, parameters and buffers):
+// the batch's block range is the concatenation of the instances' ranges, every block belongs to
+// one instance (map), and the block copies that instance's job record into shared memory.
+// Every voxel goes through the same device functions as in the single-instance kernels, so the
+// results are those of the instances run alone.
+template <class S>
+__device__ __forceinline__ const Job0<S>& stage_job0(const Job0<S>* jobs, const int2* map, Job0<S>* sj) {
+    const int j = map[blockIdx.x].x;
+    const int4* src = reinterpret_cast<const int4*>(jobs + j);
+    int4* dst = reinterpret_cast<int4*>(sj);
+    for (int w = threadIdx.x; w < (int)(sizeof(Job0<S>) / 16); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    return *sj;
+}
+
+template <class Chem, class S, bool TAN>
+__global__ void k_batch_dg0_g(const Job0<S>* __restrict__ jobs, const int2* __restrict__ map) {
+    __shared__ __align__(16) Job0<S> sj;
+    const Job0<S>& J = stage_job0(jobs, map, &sj);
+    const int cell = map[blockIdx.x].y * blockDim.x + threadIdx.x;
+    if (cell >= J.p.n_cell) return;
+    dg0_g_cell<Chem, S, TAN>(J.p, J.g, J.z, TAN ? J.v : J.z, J.gb, J.gbd, cell);
+}
+
+template <class Chem>
+__global__ void k_batch_dg0_res(const Job0<double>* __restrict__ jobs, const int2* __restrict__ map) {
+    __shared__ __align__(16) Job0<double> sj;
+    const Job0<double>& J = stage_job0(jobs, map, &sj);
+    const int cell = map[blockIdx.x].y * blockDim.x + threadIdx.x;
+    if (cell >= J.p.n_cell) return;
+    dg0_res_cell<Chem>(J.p, J.g, J.z, J.zn, J.gb, J.t, J.dt, J.relax, J.out, cell);
+}
+
+template <class Chem, class S>
+__global__ void k_batch_dg0_jvp(const Job0<S>* __restrict__ jobs, const int2* __restrict__ map) {
+    __shared__ __align__(16) Job0<S> sj;
+    const Job0<S>& J = stage_job0(jobs, map, &sj);
+    const int cell = map[blockIdx.x].y * blockDim.x + threadIdx.x;
+    if (cell >= J.p.n_cell) return;
+    dg0_jvp_cell<Chem, S>(J.p, J.g, J.z, J.v, J.gb, J.gbd, J.t, J.dt, J.relax, J.sc_dt, J.out, cell);
+}
+
+// mode 0: residual (S = double), 1: Jacobian-vector product; two launches (transport factors, voxels)
+template <class S>
+cudaError_t dg0_batch(const LaunchCtx& L, bool tradeoff, int mode, const Job0<S>* d_jobs, const int2* d_map,
+                      int nblk, int bs) {
+    if (nblk <= 0) return cudaSuccess;
+    if (mode == 0) {
+        if constexpr (std::is_same<S, double>::value) {
+            if (tradeoff) {
+                k_batch_dg0_g<ChemTO, double, false><<<nblk, bs, 0, L.st>>>(d_jobs, d_map);
+                k_batch_dg0_res<ChemTO><<<nblk, bs, 0, L.st>>>(d_jobs, d_map);
+            } else {
+                k_batch_dg0_g<ChemR3, double, false><<<nblk, bs, 0, L.st>>>(d_jobs, d_map);
+                k_batch_dg0_res<ChemR3><<<nblk, bs, 0, L.st>>>(d_jobs, d_map);
+            }
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    } else if (tradeoff) {
+        k_batch_dg0_g<ChemTO, S, true><<<nblk, bs, 0, L.st>>>(d_jobs, d_map);
+        k_batch_dg0_jvp<ChemTO, S><<<nblk, bs, 0, L.st>>>(d_jobs, d_map);
+    } else {
+        k_batch_dg0_g<ChemR3, S, true><<<nblk, bs, 0, L.st>>>(d_jobs, d_map);
+        k_batch_dg0_jvp<ChemR3, S><<<nblk, bs, 0, L.st>>>(d_jobs, d_map);
+    }
+    *L.counter += 2;
+    return cudaGetLastError();
+}
+
+template <class Chem, class S>
+static int max_block_of() {
+    cudaFuncAttributes a, b;
+    if (cudaFuncGetAttributes(&a, k_batch_dg0_g<Chem, S, true>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&b, k_batch_dg0_jvp<Chem, S>) != cudaSuccess) return 0;
+    return std::min(a.maxThreadsPerBlock, b.maxThreadsPerBlock);
+}
+
+int dg0_batch_max_block(bool tradeoff, bool f32) {
+    if (tradeoff) return f32 ? max_block_of<ChemTO, float>() : max_block_of<ChemTO, double>();
+    return f32 ? max_block_of<ChemR3, float>() : max_block_of<ChemR3, double>();
+}
+
+template cudaError_t dg0_batch<double>(const LaunchCtx&, bool, int, const Job0<double>*, const int2*, int, int);
+template cudaError_t dg0_batch<float>(const LaunchCtx&, bool, int, const Job0<float>*, const int2*, int, int);
 
 }  // namespace dgls

@@ -31,6 +31,23 @@ struct MGLevel {
     double* dense; // coarsest level only: [2n][4n] Gauss-Jordan workspace, right half = A^{-1}
 };
 
+// Workspace carved from one caller-owned device buffer instead of cudaMalloc (a server keeps such
+// buffers and reuses them across requests); with base == nullptr the allocations are only counted,
+// which sizes the buffer exactly.  Every allocation starts on a 256-byte boundary.
+struct DevArena {
+    char* base = nullptr;
+    int64_t size = 0;
+    int64_t used = 0;
+    bool active = false;
+};
+inline cudaError_t arena_alloc(DevArena* a, size_t bytes, void** p) {
+    const int64_t off = (a->used + 255) / 256 * 256;
+    if (a->base && off + (int64_t)bytes > a->size) return cudaErrorMemoryAllocation;
+    *p = a->base ? (void*)(a->base + off) : (void*)(uintptr_t)(off + 256);   // counting: a distinct dummy address
+    a->used = off + (int64_t)bytes;
+    return cudaSuccess;
+}
+
 // Launch counter increment hook (owned by the context).
 struct LaunchCtx {
     cudaStream_t st;
@@ -84,11 +101,44 @@ template <class S>
 cudaError_t dg1_lin_apply(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v,
                           double t, double dt, int relax, double sc_dt, S* out, const DG1Lin& lin);
 
-// Fused matrix-free DG1 product (jvp1.cu): out = J(z) v (times dt rscale per row when sc_dt > 0)
-// in one launch, forward-mode dual numbers in the arithmetic type S; nothing cached.
+// ------------------------------------------------------------------ batched instances
+// One record per instance of a batch (device memory); the batched kernels launch once over the
+// block ranges of all instances of one kind, and launch block b runs block map[b].y of instance
+// map[b].x with the same device functions as the single-instance kernels (map: the schedule).
 template <class S>
-cudaError_t dg1_jvp_fused(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v, double t,
-                          double dt, int relax, double sc_dt, S* out);
+struct alignas(16) Job0 {          // DG0: transport factors, then the residual or the product
+    DevParams p;
+    Geo g;
+    const S* z;
+    const S* v;
+    const double* zn;
+    S* gb;
+    S* gbd;
+    S* out;
+    double t, dt, sc_dt;
+    int relax;
+};
+template <class S>
+cudaError_t dg0_batch(const LaunchCtx& L, bool tradeoff, int mode, const Job0<S>* d_jobs, const int2* d_map,
+                      int nblk, int bs);
+// largest block size every batched DG0 product kernel of this chemistry and precision can launch with
+int dg0_batch_max_block(bool tradeoff, bool f32);
+// DG1 fused product: job records are opaque bytes of dg1_job_bytes(f32), filled on the host
+size_t dg1_job_bytes(bool f32);
+void dg1_fused_job(bool f32, const DevParams& p, const Geo& g, const void* z, const void* v, double t, double dt,
+                   int relax, double sc_dt, void* out, void* job);
+cudaError_t dg1_jvp_fused_batched(const LaunchCtx& L, bool f32, bool tradeoff, const void* d_jobs, const int2* d_map,
+                                  int nblk);
+// FP64 -> FP32 copies of several vectors in one launch (blocks of 256 x 4 elements)
+struct ConvJob {
+    const double* src;
+    float* dst;
+    int64_t n;
+};
+cudaError_t to_f32_batched(const LaunchCtx& L, const ConvJob* d_jobs, const int2* d_map, int nblk);
+constexpr int CONV_BLOCK_ELEMS = 1024;
+constexpr int FUSED_VOXELS = 32;   // voxels per block of the fused DG1 product
+constexpr size_t JOB_SLOT = 4096;  // bytes of one job-record slot (every job record fits)
 
 // ------------------------------------------------------------------ linear algebra (la.cu)
 // Block-Jacobi: invert nblk blocks of nf x nf (row-major) in place; identity rows for absent
@@ -125,7 +175,7 @@ cudaError_t ledger(const LaunchCtx& L, const DevParams& p, const Geo& g, const d
 
 // ------------------------------------------------------------------ potential multigrid (mg.cu)
 cudaError_t mg_levels_alloc(std::vector<MGLevel>& lv, int nx, int ny, int nz, std::vector<void*>& allocs,
-                            int64_t* bytes);
+                            int64_t* bytes, DevArena* arena = nullptr);
 cudaError_t mg_setup(const LaunchCtx& L, const DevParams& p, const Geo& g, const double* z, const double* gb,
                      double t, double dt, int relax, std::vector<MGLevel>& lv);
 template <class S>

@@ -20,6 +20,13 @@
 //   phase 3  each node adds its own face flux (trace weight ALPHA) and its line partner's (BETA)
 //            from shared memory and stores its row-scaled outputs.
 // Each interior face point is evaluated by the voxels on both of its sides.
+//
+// The kernel always runs from a table of job records (one per instance: parameters, geometry,
+// buffers, per-call constants) and a block map: a batch of many instances and a single instance
+// (a one-job table) use the same compiled kernel, so an instance's product is bitwise the same
+// alone and in a batch.
+#include <cstring>
+
 #include "dg1_shared.cuh"
 
 namespace dgls {
@@ -35,6 +42,8 @@ struct FusedK {
     S kSv, kS;                      // Phi^S: 2 kappa_s vol in the volume, kappa_s at faces
     S aLi, aL;                      // anode: k_Ano on the Li+ row (zero while relaxing), F k_Ano on Phi^L
     S rs[DG_MAXF];                  // row scales of the outputs (Newton rows) or 1
+    S M, Mdt, Msdt[2];              // node volume h^3/8, M/dt, M rho_s/(M_s dt) of the two solids
+    S tH;                           // T_H(t) of Eq. 56 (the smoothed reactions)
     int charged;                    // bit m: species m carries charge
 };
 
@@ -49,30 +58,74 @@ __host__ __device__ constexpr bool struct_field(int f) {
     return (f >= Chem::NL && f < Chem::NL + Chem::NS) || f == Chem::PHIS;
 }
 
+// Tangent of the node terms of one DG1 node (mass M = h^3/8): storage of Eq. 50 (or the d_t Phi
+// terms of the relaxation of Sec. 2.8) minus the reaction sources of structure points (Tab. 4);
+// the previous time level enters the node terms as constants only, so it drops out.
 template <class Chem, class S>
-constexpr size_t fused_smem() {
-    return (size_t)(2 * Chem::NF * 8 * FT + 2 * 32 * FT + 8 * 3 * (Chem::NL + 2) * FT) * sizeof(S) + 2 * FT * sizeof(int);
+__device__ __forceinline__ void node_tangent(const DevParams& p, const FusedK<S>& K, int ph, const Dual<S>* c,
+                                             const Dual<S>* es, Dual<S> phiL, Dual<S> phiS, int relax, S* out) {
+    typedef Dual<S> T;
+    constexpr int NL = Chem::NL, NS = Chem::NS, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
+    const bool st = ph == 1;
+    const T epsL = liquid_fraction<Chem, T>(p, ph, es);
+#pragma unroll
+    for (int m = 0; m < NL; ++m) out[m] = (relax ? c[m].d : (epsL * c[m]).d) * K.Mdt;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) out[NL + q] = st ? es[q].d * K.Msdt[q] : S(0);
+    out[PHIL] = relax ? phiL.d * K.Mdt : S(0);
+    out[PHIS] = relax && st ? phiS.d * K.Mdt : S(0);
+    if (st) {
+        T Sv[NL], Ss[2], qL, qS;
+        sources<Chem, T>(p, c, es, phiL, phiS, K.tH, Sv, Ss, qL, qS);
+        if (!relax) {
+#pragma unroll
+            for (int m = 0; m < NL; ++m) out[m] -= Sv[m].d * K.M;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) out[NL + q] -= Ss[q].d * K.M;
+        }
+        out[PHIL] -= qL.d * K.M;
+        out[PHIS] -= qS.d * K.M;
+    }
 }
-}  // namespace
 
 template <class Chem, class S>
-__global__ void __launch_bounds__(256) k_jvp1_fused(const DevParams p, const Geo g, const S* __restrict__ z,
-                                                    const S* __restrict__ v, const FusedK<S> K, double tH,
-                                                    double dt, int relax, S* __restrict__ out) {
+__host__ __device__ constexpr size_t fused_smem() {
+    return (size_t)(2 * Chem::NF * 8 * FT + 2 * 32 * FT + 8 * 3 * (Chem::NL + 2) * FT) * sizeof(S) + 2 * FT * sizeof(int);
+}
+
+// one instance of a batched product
+template <class S>
+struct alignas(16) Job1 {
+    DevParams p;
+    Geo g;
+    FusedK<S> K;
+    const S* z;
+    const S* v;
+    S* out;
+    int relax;
+};
+static_assert(FT == FUSED_VOXELS, "block width");
+}  // namespace
+
+// The product over one block of 32 voxels (block index `blk` of the instance); the calling kernel
+// provides the dynamic shared memory (fused_smem bytes) and 256 threads.
+template <class Chem, class S>
+__device__ __forceinline__ void jvp1_block(const DevParams& p, const Geo& g, const S* __restrict__ z,
+                                           const S* __restrict__ v, const FusedK<S>& K, int relax,
+                                           S* __restrict__ out, int blk, unsigned char* smem_raw) {
     typedef Dual<S> T;
     constexpr int NL = Chem::NL, NS = Chem::NS, NF = Chem::NF, PHIL = Chem::PHIL, PHIS = Chem::PHIS;
     constexpr int NE = NL + 2;   // transport equations: the species, Phi^L, Phi^S
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* sZ = reinterpret_cast<S*>(smem_raw);   // [NF][8][FT]
-    S* sV = sZ + NF * 8 * FT;                 // [NF][8][FT]
-    S* sG = sV + NF * 8 * FT;                 // [32 slots][FT] transport factors (value)
+    typedef typename std::conditional<std::is_same<S, float>::value, float2, double2>::type S2;
+    S2* sZV = reinterpret_cast<S2*>(smem_raw);   // [NF][8][FT] (z, v) pairs: one shared load per value and tangent
+    S* sG = reinterpret_cast<S*>(sZV + NF * 8 * FT);   // [32 slots][FT] transport factors (value)
     S* sGd = sG + 32 * FT;                    // [32 slots][FT] (tangent)
     S* sF = sGd + 32 * FT;                    // [8 nodes][3 dirs][NE][FT] near-face flux tangents, signed and weighted
     int* sPh = reinterpret_cast<int*>(sF + 8 * 3 * NE * FT);
     int* sSi = sPh + FT;
 
     const int n = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * FT + lane;
+    const int c = blk * FT + lane;
     const bool active = c < p.n_cell;
     const S al = S(ALPHA), be = S(BETA);
 
@@ -94,11 +147,16 @@ __global__ void __launch_bounds__(256) k_jvp1_fused(const DevParams p, const Geo
             zz = z[o];
             vv = v[o];
         }
-        sZ[(f * 8 + n) * FT + lane] = zz;
-        sV[(f * 8 + n) * FT + lane] = vv;
+        S2 w;
+        w.x = zz;
+        w.y = vv;
+        sZV[(f * 8 + n) * FT + lane] = w;
     }
     __syncthreads();
-    auto zv = [&](int f, int node, int l) -> T { return mkd(sZ[(f * 8 + node) * FT + l], sV[(f * 8 + node) * FT + l]); };
+    auto zv = [&](int f, int node, int l) -> T {
+        const S2 w = sZV[(f * 8 + node) * FT + l];
+        return mkd(w.x, w.y);
+    };
 
     // ---- phase 1: transport factors at the node and its three face points; node terms
     S acc[NF];
@@ -133,23 +191,17 @@ __global__ void __launch_bounds__(256) k_jvp1_fused(const DevParams p, const Geo
             sG[slot * FT + lane] = gg.v;
             sGd[slot * FT + lane] = gg.d;
         }
-        // storage and sources of this node (the previous time level enters only as constants)
+        // storage and sources of this node
         const T phiL = zv(PHIL, n, lane);
         const T phiS = ph == 1 ? zv(PHIS, n, lane) : Make<T>::c(0.0);
-        double old[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) old[f] = 0.0;
-        T R[NF];
-        node_terms<Chem, T>(p, ph, cn, es, phiL, phiS, old, tH, dt, relax, R);
-#pragma unroll
-        for (int f = 0; f < NF; ++f) acc[f] = R[f].d;
+        node_tangent<Chem, S>(p, K, ph, cn, es, phiL, phiS, relax, acc);
     }
     __syncthreads();
 
     // ---- phase 2: per direction, the line's volume term and the flux through this node's face point
     int ci = 0, cj = 0, ck = 0;
     if (active) cell_ijk(p, c, ci, cj, ck);
-#pragma unroll
+#pragma unroll 1   // one copy of the direction body: the kernel is large, and instruction fetch stalled it
     for (int d = 0; d < 3; ++d) {
         const int pn = n ^ (1 << d);
         const int mc = (n >> d) & 1;         // this node's coordinate along d (1: next to the +d face)
@@ -175,7 +227,7 @@ __global__ void __launch_bounds__(256) k_jvp1_fused(const DevParams p, const Geo
                 acc[m] += sgn * K.vol * fl;
             }
             acc[PHIL] += sgn * K.vol * accL;
-            if (ph == 1) acc[PHIS] += sgn * K.kSv * (sV[(PHIS * 8 + n1) * FT + lane] - sV[(PHIS * 8 + n0) * FT + lane]);
+            if (ph == 1) acc[PHIS] += sgn * K.kSv * (zv(PHIS, n1, lane).d - zv(PHIS, n0, lane).d);
         }
         // flux through the face point on this node's side of the line
         S Fe[NE];
@@ -245,7 +297,7 @@ __global__ void __launch_bounds__(256) k_jvp1_fused(const DevParams p, const Geo
             }
             Fe[NL] = fL;
             if (ph == 1 && qph == 1) {
-                const S jn = sV[(PHIS * 8 + n) * FT + lane], jf = sV[(PHIS * 8 + pn) * FT + lane];
+                const S jn = zv(PHIS, n, lane).d, jf = zv(PHIS, pn, lane).d;
                 const S qn = nb(PHIS, pn).d, qf = nb(PHIS, n).d;
                 const S to = jn * al + jf * be, tn = qn * al + qf * be;
                 const S jump = mc ? to - tn : tn - to;
@@ -286,10 +338,25 @@ __global__ void __launch_bounds__(256) k_jvp1_fused(const DevParams p, const Geo
     }
 }
 
+// Batched product: launch block b runs block map[b].y of instance map[b].x, whose job record is
+// staged in shared memory behind the product's own arrays.
 template <class Chem, class S>
-static cudaError_t fused_impl(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v, double t,
-                              double dt, int relax, double sc_dt, S* out) {
-    FusedK<S> K;
+__global__ void __launch_bounds__(256, sizeof(S) == 4 ? 4 : 1) k_jvp1_batched(const Job1<S>* __restrict__ jobs,
+                                                                             const int2* __restrict__ map) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr size_t off = (fused_smem<Chem, S>() + 15) / 16 * 16;
+    Job1<S>* sj = reinterpret_cast<Job1<S>*>(smem_raw + off);
+    {
+        const int4* src = reinterpret_cast<const int4*>(jobs + map[blockIdx.x].x);
+        int4* dst = reinterpret_cast<int4*>(sj);
+        for (int w = threadIdx.x; w < (int)(sizeof(Job1<S>) / 16); w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    jvp1_block<Chem, S>(sj->p, sj->g, sj->z, sj->v, sj->K, sj->relax, sj->out, map[blockIdx.x].y, smem_raw);
+}
+
+template <class S>
+static void fill_K(const DevParams& p, int nl, int nf, double t, double dt, int relax, double sc_dt, FusedK<S>& K) {
     const double h = p.h;
     K.wf = S(0.25 * h * h);
     K.vol = S(3.0 * h / 8.0);
@@ -297,7 +364,7 @@ static cudaError_t fused_impl(const LaunchCtx& L, const DevParams& p, const Geo&
     K.gq2 = S(0.5 * 1.7320508075688772935 / h);
     K.charged = 0;
     for (int m = 0; m < 6; ++m) {
-        const bool on = m < Chem::NL;
+        const bool on = m < nl;
         K.D0[m] = S(on && !relax ? p.D0[m] : 0.0);
         K.km[m] = S(on && !relax ? p.kappa_m[m] : 0.0);
         K.Kd[m] = S(on ? p.Kd[m] : 0.0);
@@ -308,28 +375,56 @@ static cudaError_t fused_impl(const LaunchCtx& L, const DevParams& p, const Geo&
     K.kS = S(p.kappa_s);
     K.aLi = S(relax ? 0.0 : p.kAno);
     K.aL = S(p.F * p.kAno);
-    for (int f = 0; f < DG_MAXF; ++f) K.rs[f] = S(f < Chem::NF && sc_dt > 0.0 ? sc_dt * p.rscale[f] : 1.0);
-    const size_t smem = fused_smem<Chem, S>();
-    // more than 48 KB of dynamic shared memory needs an opt-in, which belongs to the current device
-    cudaError_t e = cudaFuncSetAttribute(k_jvp1_fused<Chem, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int f = 0; f < DG_MAXF; ++f) K.rs[f] = S(f < nf && sc_dt > 0.0 ? sc_dt * p.rscale[f] : 1.0);
+    const double M = p.V / 8.0;
+    K.M = S(M);
+    K.Mdt = S(M / dt);
+    K.Msdt[0] = S(M * p.rhoM[0] / dt);
+    K.Msdt[1] = S(M * p.rhoM[1] / dt);
+    K.tH = S(smooth_step(t));
+}
+
+static_assert(sizeof(Job1<double>) <= JOB_SLOT && sizeof(Job1<float>) <= JOB_SLOT, "job record slot");
+size_t dg1_job_bytes(bool f32) { return f32 ? sizeof(Job1<float>) : sizeof(Job1<double>); }
+
+template <class S>
+static void fill_job(const DevParams& p, const Geo& g, const void* z, const void* v, double t, double dt, int relax,
+                     double sc_dt, void* out, void* job) {
+    Job1<S> J;
+    std::memset(&J, 0, sizeof(J));
+    J.p = p;
+    J.g = g;
+    fill_K<S>(p, p.nl, p.nf, t, dt, relax, sc_dt, J.K);
+    J.z = (const S*)z;
+    J.v = (const S*)v;
+    J.out = (S*)out;
+    J.relax = relax;
+    std::memcpy(job, &J, sizeof(J));
+}
+
+void dg1_fused_job(bool f32, const DevParams& p, const Geo& g, const void* z, const void* v, double t, double dt,
+                   int relax, double sc_dt, void* out, void* job) {
+    if (f32) fill_job<float>(p, g, z, v, t, dt, relax, sc_dt, out, job);
+    else fill_job<double>(p, g, z, v, t, dt, relax, sc_dt, out, job);
+}
+
+template <class Chem, class S>
+static cudaError_t batched_impl(const LaunchCtx& L, const void* d_jobs, const int2* d_map, int nblk) {
+    const size_t smem = (fused_smem<Chem, S>() + 15) / 16 * 16 + sizeof(Job1<S>);
+    cudaError_t e = cudaFuncSetAttribute(k_jvp1_batched<Chem, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int blocks = (p.n_cell + FT - 1) / FT;
-    k_jvp1_fused<Chem, S><<<blocks, 8 * FT, smem, L.st>>>(p, g, z, v, K, smooth_step(t), dt, relax, out);
+    k_jvp1_batched<Chem, S><<<nblk, 8 * FT, smem, L.st>>>((const Job1<S>*)d_jobs, d_map);
     *L.counter += 1;
     return cudaGetLastError();
 }
 
-template <class S>
-cudaError_t dg1_jvp_fused(const LaunchCtx& L, const DevParams& p, const Geo& g, const S* z, const S* v, double t,
-                          double dt, int relax, double sc_dt, S* out) {
-    if (p.order != 1) return cudaErrorInvalidValue;
-    return p.nf == 10 ? fused_impl<ChemTO, S>(L, p, g, z, v, t, dt, relax, sc_dt, out)
-                      : fused_impl<ChemR3, S>(L, p, g, z, v, t, dt, relax, sc_dt, out);
+cudaError_t dg1_jvp_fused_batched(const LaunchCtx& L, bool f32, bool tradeoff, const void* d_jobs, const int2* d_map,
+                                  int nblk) {
+    if (nblk <= 0) return cudaSuccess;
+    if (f32) return tradeoff ? batched_impl<ChemTO, float>(L, d_jobs, d_map, nblk)
+                             : batched_impl<ChemR3, float>(L, d_jobs, d_map, nblk);
+    return tradeoff ? batched_impl<ChemTO, double>(L, d_jobs, d_map, nblk)
+                    : batched_impl<ChemR3, double>(L, d_jobs, d_map, nblk);
 }
-
-template cudaError_t dg1_jvp_fused<double>(const LaunchCtx&, const DevParams&, const Geo&, const double*,
-                                           const double*, double, double, int, double, double*);
-template cudaError_t dg1_jvp_fused<float>(const LaunchCtx&, const DevParams&, const Geo&, const float*, const float*,
-                                          double, double, int, double, float*);
 
 }  // namespace dgls

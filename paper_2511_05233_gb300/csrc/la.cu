@@ -506,4 +506,22 @@ cudaError_t ledger(const LaunchCtx& L, const DevParams& p, const Geo& g, const d
     return cudaGetLastError();
 }
 
+// FP64 -> FP32 copies of several vectors in one launch: launch block b converts elements
+// [map[b].y * CONV_BLOCK_ELEMS, +CONV_BLOCK_ELEMS) of vector map[b].x
+__global__ void __launch_bounds__(256) k_to_f32_batched(const ConvJob* __restrict__ jobs, const int2* __restrict__ map) {
+    const ConvJob J = jobs[map[blockIdx.x].x];
+    const int64_t base = (int64_t)map[blockIdx.x].y * CONV_BLOCK_ELEMS;
+    for (int e = threadIdx.x; e < CONV_BLOCK_ELEMS; e += blockDim.x) {
+        const int64_t i = base + e;
+        if (i < J.n) J.dst[i] = (float)J.src[i];
+    }
+}
+
+cudaError_t to_f32_batched(const LaunchCtx& L, const ConvJob* d_jobs, const int2* d_map, int nblk) {
+    if (nblk <= 0) return cudaSuccess;
+    k_to_f32_batched<<<nblk, 256, 0, L.st>>>(d_jobs, d_map);
+    *L.counter += 1;
+    return cudaGetLastError();
+}
+
 }  // namespace dgls

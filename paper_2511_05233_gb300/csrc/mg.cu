@@ -580,7 +580,7 @@ __global__ void k_sp_prolong_add(const DevParams p, MGLevel L, int m0, int m1, S
 
 // ------------------------------------------------------------------ host drivers
 cudaError_t mg_levels_alloc(std::vector<MGLevel>& lv, int nx, int ny, int nz, std::vector<void*>& allocs,
-                            int64_t* bytes) {
+                            int64_t* bytes, DevArena* arena) {
     lv.clear();
     int x = nx, y = ny, zz = nz;
     for (;;) {
@@ -590,9 +590,11 @@ cudaError_t mg_levels_alloc(std::vector<MGLevel>& lv, int nx, int ny, int nz, st
         L.n = x * y * zz;
         auto al = [&](auto** ptr, int64_t cnt) -> cudaError_t {
             void* q = nullptr;
-            cudaError_t e = cudaMalloc(&q, (size_t)cnt * sizeof(**ptr));
+            const bool from_arena = arena && arena->active;
+            cudaError_t e = from_arena ? arena_alloc(arena, (size_t)cnt * sizeof(**ptr), &q)
+                                       : cudaMalloc(&q, (size_t)cnt * sizeof(**ptr));
             if (e != cudaSuccess) return e;
-            allocs.push_back(q);
+            if (!from_arena) allocs.push_back(q);
             *bytes += cnt * (int64_t)sizeof(**ptr);
             *ptr = (std::remove_reference_t<decltype(*ptr)>)q;
             return cudaSuccess;

@@ -86,6 +86,8 @@ def lib():
         sig = {
             "dg_params_default": (C.c_int, [C.POINTER(Params), C.c_int32, C.c_int32]),
             "dg_setup": (C.c_int, [C.POINTER(Structure), C.POINTER(Params), _P, C.POINTER(_P)]),
+            "dg_setup_in": (C.c_int, [C.POINTER(Structure), C.POINTER(Params), _P, _P, C.c_int64, C.POINTER(_P)]),
+            "dg_workspace_estimate": (C.c_int, [C.POINTER(Structure), C.POINTER(Params), C.POINTER(C.c_int64)]),
             "dg_destroy": (C.c_int, [_P]),
             "dg_last_error": (C.c_char_p, [_P]),
             "dg_layout": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
@@ -109,6 +111,18 @@ def lib():
             "dg_limit": (C.c_int, [_P, _P]),
             "dg_reorth_count": (C.c_int64, [_P]),
             "dg_workspace_bytes": (C.c_int64, [_P]),
+            "dg_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, _P, C.POINTER(_P)]),
+            "dg_batch_destroy": (C.c_int, [_P]),
+            "dg_batch_last_error": (C.c_char_p, [_P]),
+            "dg_batch_launch_count": (C.c_int64, [_P]),
+            "dg_batch_jvp": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32,
+                                       C.POINTER(_P), C.POINTER(_P)]),
+            "dg_batch_residual": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double), C.POINTER(_P)]),
+            "dg_batch_autotune": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32,
+                                            C.POINTER(_P), C.POINTER(_P), C.POINTER(C.c_int32)]),
+            "dg_batch_step": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(StepInfo), C.POINTER(C.c_int32)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -145,24 +159,46 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-class Context:
-    """One discretised cell (structure + parameters) with its device workspaces."""
+def _structure(phase, h):
+    ph = np.ascontiguousarray(phase, dtype=np.uint8)
+    if ph.ndim != 3:
+        raise ValueError("phase must be (nz, ny, nx)")
+    nz, ny, nx = ph.shape
+    return ph, Structure(nx, ny, nz, float(h), ph.ctypes.data_as(C.POINTER(C.c_uint8)))
 
-    def __init__(self, phase, h, params, stream=None):
+
+def workspace_estimate(phase, h, params):
+    """dg_workspace_estimate: device bytes a context for this structure and parameters needs."""
+    ph, s = _structure(phase, h)
+    n = C.c_int64()
+    st = lib().dg_workspace_estimate(C.byref(s), C.byref(params), C.byref(n))
+    if st != OK:
+        raise DGError(st, "dg_workspace_estimate")
+    return int(n.value)
+
+
+class Context:
+    """One discretised cell (structure + parameters) with its device workspaces (its own cudaMalloc
+    allocations, or carved from `workspace`, a CUDA uint8 tensor the caller keeps and may reuse)."""
+
+    def __init__(self, phase, h, params, stream=None, workspace=None):
         import torch
 
         self._lib = lib()
-        ph = np.ascontiguousarray(phase, dtype=np.uint8)
-        if ph.ndim != 3:
-            raise ValueError("phase must be (nz, ny, nx)")
-        nz, ny, nx = ph.shape
+        ph, s = _structure(phase, h)
         self._phase = ph
-        s = Structure(nx, ny, nz, float(h), ph.ctypes.data_as(C.POINTER(C.c_uint8)))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
+        self.workspace = workspace
         h_ = C.c_void_p()
-        st = self._lib.dg_setup(C.byref(s), C.byref(params), C.c_void_p(stream.cuda_stream), C.byref(h_))
+        if workspace is not None:
+            if not (workspace.is_cuda and workspace.dtype == torch.uint8 and workspace.is_contiguous()):
+                raise TypeError("workspace must be a contiguous uint8 CUDA tensor")
+            st = self._lib.dg_setup_in(C.byref(s), C.byref(params), C.c_void_p(stream.cuda_stream),
+                                       C.c_void_p(workspace.data_ptr()), workspace.numel(), C.byref(h_))
+        else:
+            st = self._lib.dg_setup(C.byref(s), C.byref(params), C.c_void_p(stream.cuda_stream), C.byref(h_))
         if st != OK:
             raise DGError(st, "dg_setup (no structure voxel at x = 0, bad arguments or out of memory)")
         self._h = h_
@@ -328,3 +364,97 @@ class Context:
 
     def workspace_bytes(self):
         return int(self._lib.dg_workspace_bytes(self._h))
+
+
+def _dev_ptr(t, dtypes=("float64",)):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or str(t.dtype)[6:] not in dtypes:
+        raise TypeError("expected contiguous CUDA tensors of " + "/".join(dtypes))
+    return t.data_ptr()
+
+
+class Batch:
+    """dg_batch: several contexts (uneven grids, DG0 and DG1, one chemistry) evaluated together --
+    one launch per kind of kernel over all instances -- and stepped concurrently."""
+
+    def __init__(self, contexts, stream=None):
+        import torch
+
+        self._lib = lib()
+        self.contexts = list(contexts)          # keeps the contexts alive as long as the batch
+        n = len(self.contexts)
+        arr = (_P * n)(*[c._h.value for c in self.contexts])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = _P()
+        st = self._lib.dg_batch_create(arr, n, _P(stream.cuda_stream), C.byref(h))
+        if st != OK:
+            raise DGError(st, "dg_batch_create (contexts of different chemistries, or out of memory)")
+        self._h = h
+        self.n = n
+
+    def _check(self, st):
+        if st != OK:
+            raise DGError(st, self._lib.dg_batch_last_error(self._h).decode())
+
+    def _ptrs(self, tensors, dtypes=("float64",)):
+        if len(tensors) != self.n:
+            raise ValueError("one tensor per instance")
+        return (_P * self.n)(*[_dev_ptr(t, dtypes) for t in tensors])
+
+    def _dbl(self, xs):
+        xs = list(xs)
+        if len(xs) != self.n:
+            raise ValueError("one value per instance")
+        return (C.c_double * self.n)(*[float(x) for x in xs])
+
+    @staticmethod
+    def _prec(vs):
+        import torch
+
+        return MIXED if vs[0].dtype == torch.float32 else FP64
+
+    def jvp(self, zs, ts, dts, vs, outs):
+        prec = self._prec(vs)
+        dt = ("float32",) if prec == MIXED else ("float64",)
+        self._check(self._lib.dg_batch_jvp(self._h, self._ptrs(zs), self._dbl(ts), self._dbl(dts), prec,
+                                           self._ptrs(vs, dt), self._ptrs(outs, dt)))
+        return outs
+
+    def residual(self, zs, zns, ts, dts, rs):
+        self._check(self._lib.dg_batch_residual(self._h, self._ptrs(zs), self._ptrs(zns), self._dbl(ts),
+                                                self._dbl(dts), self._ptrs(rs)))
+        return rs
+
+    def autotune(self, zs, ts, dts, vs, outs):
+        """Choose the schedules by timed trials; returns (DG1 block order, DG0 block size)."""
+        prec = self._prec(vs)
+        dt = ("float32",) if prec == MIXED else ("float64",)
+        ch = (C.c_int32 * 2)()
+        self._check(self._lib.dg_batch_autotune(self._h, self._ptrs(zs), self._dbl(ts), self._dbl(dts), prec,
+                                                self._ptrs(vs, dt), self._ptrs(outs, dt), ch))
+        return int(ch[0]), int(ch[1])
+
+    def step(self, zns, zs, ts, dts):
+        """One implicit step of every instance; returns (statuses, step infos)."""
+        infos = (StepInfo * self.n)()
+        sts = (C.c_int32 * self.n)()
+        self._check(self._lib.dg_batch_step(self._h, self._ptrs(zns), self._ptrs(zs), self._dbl(ts), self._dbl(dts),
+                                            infos, sts))
+        return [int(x) for x in sts], [infos[k] for k in range(self.n)]
+
+    def launch_count(self):
+        return int(self._lib.dg_batch_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -22,6 +22,7 @@ def main():
     ap.add_argument("--op", default="jvp", choices=["residual", "jvp", "jvp_fused", "step"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--no-warm", action="store_true", help="no untimed call first (launch lists of exactly reps calls)")
     a = ap.parse_args()
     import torch
 
@@ -58,7 +59,8 @@ def main():
         else:
             ctx.step(z, out, 0.0, 1e-3, check=False)
 
-    call()
+    if not a.no_warm:
+        call()
     torch.cuda.synchronize()
     e0.record(st)
     for _ in range(a.reps):

@@ -53,32 +53,56 @@ def make_requests(n, rate_hz, seed, side_range=(16, 40), n_steps=6, orders=(0, 1
     return out
 
 
-def workspace_estimate(req):
-    """Device bytes of one context (state, Newton, Krylov, blocks) before it is created."""
-    n = req.side ** 3
-    nn = 8 if req.order == 1 else 1
-    dof = int(n * nn * (7 + 3 * (1 - req.porosity)))
-    return dof * 8 * (31 + 20) + n * nn * 100 * 8 + (64 << 20)
+_STRUCTURES = {}
 
 
-def run_one(req, stream=None, precision=None, keep_state=False):
-    """Set up the cell, take the Tab. 6 equilibrium state and run the naive controller for
-    req.n_steps accepted steps; returns the curve and a checksum of the final state (and the state
-    itself with keep_state).  precision: dgls.FP64 (default) or dgls.MIXED."""
-    import torch
+def request_structure(req):
+    """The request's structure: the seeded random field (the first seed that keeps a collector
+    voxel); generated once per request and kept, so that a served request carries its structure as a
+    client would send it."""
+    from . import inputs
 
-    from . import dgls, inputs
+    key = (req.side, req.porosity, req.corr_len, req.seed)
+    if key not in _STRUCTURES:
+        for s in range(req.seed, req.seed + 50):
+            ph = inputs.make_structure(req.side, req.porosity, req.corr_len, s)
+            if np.any(ph[:, :, 0] == inputs.STRUCT):
+                _STRUCTURES[key] = ph
+                break
+    return _STRUCTURES[key]
 
-    phase = None
-    for s in range(req.seed, req.seed + 50):
-        ph = inputs.make_structure(req.side, req.porosity, req.corr_len, s)
-        if np.any(ph[:, :, 0] == inputs.STRUCT):
-            phase = ph
-            break
+
+def request_cell(req, precision=None):
+    """The request's structure and its library parameters."""
+    from . import dgls
+
+    phase = request_structure(req)
     prm = dgls.default_params(dgls.TRADEOFF, req.order, f_C=req.f_C, eps_struct=1 - req.porosity,
                               precision=dgls.FP64 if precision is None else precision)
+    return phase, prm
+
+
+def workspace_estimate(req, precision=None):
+    """Device bytes of the request's context, from the library (dg_workspace_estimate), plus its
+    state vector."""
+    from . import dgls
+
+    phase, prm = request_cell(req, precision)
+    return dgls.workspace_estimate(phase, 1e-6, prm) + (1 << 20)
+
+
+def run_one(req, stream=None, precision=None, keep_state=False, workspace=None):
+    """Set up the cell (inside `workspace`, a device uint8 buffer the caller reuses, when given),
+    take the Tab. 6 equilibrium state and run the naive controller for req.n_steps accepted steps;
+    returns the curve and a checksum of the final state (and the state itself with keep_state).
+    precision: dgls.FP64 (default) or dgls.MIXED."""
+    import torch
+
+    from . import dgls
+
+    phase, prm = request_cell(req, precision)
     with torch.cuda.stream(stream) if stream is not None else _null():
-        ctx = dgls.Context(phase, 1e-6, prm, stream=stream or torch.cuda.current_stream())
+        ctx = dgls.Context(phase, 1e-6, prm, stream=stream or torch.cuda.current_stream(), workspace=workspace)
         z = ctx.new_state()
         ctx.equilibrium_state(z)
         res = ctx.discharge(z, controller=dgls.NAIVE, dt0=1e-3, max_steps=req.n_steps)
@@ -93,41 +117,61 @@ def run_one(req, stream=None, precision=None, keep_state=False):
 
 
 class Admission:
-    """Host-side admission of the serving loop: first come, first served into free slots while the
-    request's workspace fits in what is left of the HBM budget.  A request that could never fit
-    (its workspace alone exceeds the whole budget) is rejected when it arrives, so it cannot block
+    """Host-side admission of the serving loop.  Every slot keeps a device workspace buffer across
+    requests (a context is set up inside it, no allocation per request); the HBM budget covers the
+    buffers the slots hold together.  Requests are taken first come, first served: the head of the
+    queue goes to a free slot whose buffer already fits it (the smallest such), else to the free slot
+    with the largest buffer, grown to the request's workspace if the budget allows the growth.  A
+    request whose workspace alone exceeds the budget is rejected when it arrives, so it cannot block
     the queue behind it."""
 
     def __init__(self, slots, budget, size_of):
-        self.free_slots = slots
+        self.buf = [0] * slots          # bytes of each slot's workspace buffer
+        self.busy = [False] * slots
         self.budget = budget
-        self.total = budget
         self.size_of = size_of
         self.queue = []
         self.rejected = []
 
+    @property
+    def free_slots(self):
+        return self.busy.count(False)
+
+    def held(self):
+        return sum(self.buf)
+
     def arrive(self, req):
         need = self.size_of(req)
-        if need > self.total:
-            req.result = {"status": f"rejected: workspace {need} B exceeds the HBM budget {self.total} B"}
+        if need > self.budget:
+            req.result = {"status": f"rejected: workspace {need} B exceeds the HBM budget {self.budget} B"}
             self.rejected.append(req)
             return False
         heapq.heappush(self.queue, (req.arrival, req.rid, req, need))
         return True
 
     def admit(self):
-        """Pop every request that fits now: [(req, need)]."""
+        """Pop every request that fits now: [(req, need, slot, new buffer bytes)]."""
         out = []
-        while self.queue and self.free_slots > 0 and self.queue[0][3] <= self.budget:
-            _, _, req, need = heapq.heappop(self.queue)
-            self.free_slots -= 1
-            self.budget -= need
-            out.append((req, need))
+        while self.queue:
+            _, _, req, need = self.queue[0]
+            free = [k for k in range(len(self.buf)) if not self.busy[k]]
+            if not free:
+                break
+            fit = [k for k in free if self.buf[k] >= need]
+            if fit:
+                k = min(fit, key=lambda q: self.buf[q])
+            else:
+                k = max(free, key=lambda q: self.buf[q])
+                if self.held() - self.buf[k] + need > self.budget:
+                    break
+                self.buf[k] = need
+            heapq.heappop(self.queue)
+            self.busy[k] = True
+            out.append((req, need, k, self.buf[k]))
         return out
 
-    def release(self, need):
-        self.free_slots += 1
-        self.budget += need
+    def release(self, slot):
+        self.busy[slot] = False
 
     def idle(self):
         return not self.queue
@@ -148,21 +192,20 @@ def serve(requests, slots=4, hbm_budget=150 << 30, time_scale=1.0, precision=Non
     t0 = time.perf_counter()
     pending = sorted(requests, key=lambda r: r.arrival)
     lock = threading.Condition()
-    adm = Admission(slots, hbm_budget, workspace_estimate)
+    adm = Admission(slots, hbm_budget, lambda r: workspace_estimate(r, precision))
     streams = [torch.cuda.Stream() for _ in range(slots)]
-    free_streams = list(range(slots))
+    buffers = [None] * slots           # each slot's workspace buffer, kept across requests
     threads = []
 
-    def worker(req, sidx, need):
+    def worker(req, slot, need):
         req.start = time.perf_counter() - t0
         try:
-            req.result = run_one(req, streams[sidx], precision, keep_state)
+            req.result = run_one(req, streams[slot], precision, keep_state, workspace=buffers[slot])
         except Exception as e:  # a failed request is reported, not fatal to the server
             req.result = {"status": f"error: {e}"}
         req.end = time.perf_counter() - t0
         with lock:
-            adm.release(need)
-            free_streams.append(sidx)
+            adm.release(slot)
             lock.notify_all()
 
     i = 0
@@ -174,9 +217,11 @@ def serve(requests, slots=4, hbm_budget=150 << 30, time_scale=1.0, precision=Non
                     pending[i].start = pending[i].end = now
                 i += 1
             started = adm.admit()
-            for req, need in started:
-                sidx = free_streams.pop()
-                th = threading.Thread(target=worker, args=(req, sidx, need), daemon=True)
+            for req, need, slot, nbytes in started:
+                if buffers[slot] is None or buffers[slot].numel() < nbytes:
+                    buffers[slot] = None          # the old buffer goes back to torch's cache first
+                    buffers[slot] = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+                th = threading.Thread(target=worker, args=(req, slot, need), daemon=True)
                 threads.append(th)
                 th.start()
             if not started:
@@ -186,7 +231,13 @@ def serve(requests, slots=4, hbm_budget=150 << 30, time_scale=1.0, precision=Non
                 lock.wait(timeout=wait if wait > 0 else 0.001)
     for th in threads:
         th.join()
-    return requests, time.perf_counter() - t0
+    wall = time.perf_counter() - t0
+    # hand the slot buffers back to the device, not only to torch's cache: contexts set up after the
+    # server allocate with cudaMalloc
+    buffers.clear()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return requests, wall
 
 
 def sequential(requests, time_scale=1.0, precision=None, keep_state=False):

@@ -74,7 +74,7 @@ def test_dg1_128_sampled_residual_and_jvp():
     """Interior voxels (structure and pore), collector-face structure voxels (x = 0) and anode-face
     voxels (x = nx - 1): residual (1e-12 of the terms' size), the FP64 product of dg_jvp and of the
     fused kernel (1e-12 |J||v|), and the fused FP32 product of the mixed-precision Krylov loop
-    (1e-5 |J||v|, the bound derived in test_gpu_fused_jvp)."""
+    (2e-5 |J||v|, the bound derived in test_gpu_fused_jvp)."""
     import torch
 
     from paper_2511_05233_gb300 import dgls
@@ -134,4 +134,4 @@ def test_dg1_128_sampled_residual_and_jvp():
         mag_jv = _centre(m, g, mag_jv, centre)
         assert np.all(np.abs(pick(JV) - ref_jv) <= 1e-12 * mag_jv + 1e-300), (k, j, i)
         assert np.all(np.abs(pick(JF) - ref_jv) <= 1e-12 * mag_jv + 1e-300), (k, j, i)
-        assert np.all(np.abs(pick(J32) - ref_jv) <= 1e-5 * mag_jv + 1e-30), (k, j, i)
+        assert np.all(np.abs(pick(J32) - ref_jv) <= 2e-5 * mag_jv + 1e-30), (k, j, i)

@@ -44,3 +44,35 @@ def test_mixed_precision_serving_matches_fp64():
         assert r.result["sha256"] == by_id[r.rid].result["sha256"]
     err = serve.max_rel_diff(served, ref)
     assert err is not None and err["U_cell"] <= 1e-8 and err["state"] <= 1e-8, err
+
+
+def test_context_in_caller_workspace_equals_own_allocations():
+    """dg_setup_in: a context carved from a caller buffer of exactly dg_workspace_estimate bytes steps
+    bitwise as one with its own allocations (and the buffer can be reused by the next context); a
+    buffer 256 bytes short is refused with DG_ERR_OOM."""
+    import numpy as np
+    import torch
+
+    from paper_2511_05233_gb300 import dgls
+    from tests.gpu_helpers import make_case, to_dev
+
+    for order in (0, 1):
+        model, grid, phase, z0, z = make_case("tradeoff", order, (8, 5, 4))
+        p = dgls.default_params(dgls.TRADEOFF, order, f_C=model.f_C, eps_struct=model.eps_struct)
+        need = dgls.workspace_estimate(phase, 1e-6, p)
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        outs = []
+        for trial in range(2):                     # the second context reuses the first one's buffer
+            c = dgls.Context(phase, 1e-6, p, workspace=ws)
+            o = to_dev(np.zeros_like(z))
+            st, info = c.step(to_dev(z), o, 0.0, 1e-3)
+            assert info.converged
+            outs.append(o.cpu().numpy())
+            c.close()
+        ref = dgls.Context(phase, 1e-6, p)
+        o = to_dev(np.zeros_like(z))
+        ref.step(to_dev(z), o, 0.0, 1e-3)
+        assert np.array_equal(outs[0], o.cpu().numpy()) and np.array_equal(outs[1], outs[0])
+        with pytest.raises(dgls.DGError) as e:
+            dgls.Context(phase, 1e-6, p, workspace=ws[: need - 256])
+        assert e.value.status == dgls.ERR_OOM
