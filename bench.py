@@ -43,9 +43,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--batch", type=int, default=64, help="instances of the batched workload (0: skip)")
-    ap.add_argument("--serve", type=int, default=24, help="requests of the serving workload (0: skip)")
-    ap.add_argument("--serve-steps", type=int, default=3)
+    # the default batch and stream are smaller than the full-size runs (64 instances; 24 requests of
+    # 3 steps, sides 32-128) so that the whole bench ends within minutes
+    ap.add_argument("--batch", type=int, default=32, help="instances of the batched workload (0: skip)")
+    ap.add_argument("--serve", type=int, default=12, help="requests of the serving workload (0: skip)")
+    ap.add_argument("--serve-steps", type=int, default=2)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrivals per second")
     return ap.parse_args()

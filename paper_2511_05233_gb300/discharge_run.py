@@ -19,7 +19,7 @@ import numpy as np
 
 
 def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, species_mg=2, t_end=0.0, h=1e-6,
-        stall_rtol=None, single_cluster=False):
+        stall_rtol=None, single_cluster=True, wall_limit=0.0, chunk=25):
     import torch
 
     from . import dgls, inputs
@@ -41,8 +41,24 @@ def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, 
     ctx.relax(z, 0.1, 40)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    res = ctx.discharge(z, controller=dgls.NAIVE, dt0=1e-3, dt_min=1e-6, dt_max=10.0, cutoff_V=1.9,
-                        t_end=t_end, max_steps=max_steps, limiter=limiter)
+    # the discharge in chunks of accepted steps, each resumed from the previous chunk's controller state
+    # (bitwise the same curve as one call), so that a wall-clock limit can end it between chunks
+    parts, ck = [], None
+    while True:
+        n_left = max_steps - sum(len(q["t"]) for q in parts)
+        if n_left <= 0:
+            break
+        r = ctx.discharge(z, controller=dgls.NAIVE, dt0=1e-3, dt_min=1e-6, dt_max=10.0, cutoff_V=1.9,
+                          t_end=t_end, max_steps=min(chunk, n_left), limiter=limiter, resume=ck)
+        parts.append(r)
+        ck = r["checkpoint"]
+        done = r["status"] != "DG_OK" or len(r["t"]) < min(chunk, n_left) or \
+            (len(r["U_cell"]) and r["U_cell"][-1] <= 1.9) or (t_end > 0 and ck["t"] >= t_end)
+        if done or (wall_limit > 0 and time.perf_counter() - t1 > wall_limit):
+            break
+    res = {k: np.concatenate([q[k] for q in parts]) for k in ("t", "dt", "U_cell", "c_m", "newton_its", "gmres_its")}
+    res.update(status=parts[-1]["status"], attempts=sum(q["attempts"] for q in parts),
+               failures=sum(q["failures"] for q in parts))
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     out = {"n": n, "order": order, "porosity": porosity, "corr_len": corr_len, "f_C": f_C, "precision": precision,
@@ -55,7 +71,8 @@ def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, 
            "newton_total": int(np.sum(res["newton_its"])), "gmres_total": int(np.sum(res["gmres_its"])),
            "U_end": float(res["U_cell"][-1]) if len(res["U_cell"]) else None,
            "dt_max_reached": float(res["dt"].max()) if len(res["dt"]) else 0.0,
-           "wall_relax_s": t1 - t0, "wall_discharge_s": t2 - t1,
+           "wall_relax_s": t1 - t0, "wall_discharge_s": t2 - t1, "wall_limit_s": wall_limit,
+           "stopped_by_wall_limit": bool(wall_limit > 0 and t2 - t1 > wall_limit and not (len(res["U_cell"]) and res["U_cell"][-1] <= 1.9)),
            "curve": {"t": res["t"].tolist(), "U_cell": res["U_cell"].tolist(), "c_m": res["c_m"].tolist()}}
     ctx.close()
     return out
@@ -91,18 +108,20 @@ def main():
                          "scaled residual (1e-7 here, one decade above the rounding level measured on DG1 "
                          "mid-discharge states; the library default is 1e-8)")
     ap.add_argument("--no-curve", action="store_true", help="print the summary without the curve arrays")
-    ap.add_argument("--single-cluster", action="store_true",
-                    help="keep only the largest structure cluster touching the current collector")
+    ap.add_argument("--multi-cluster", action="store_true",
+                    help="keep every structure cluster touching the current collector (default: only the largest, "
+                         "so that no collector voxel is isolated)")
+    ap.add_argument("--wall-limit", type=float, default=0.0, help="stop the discharge after this many seconds (0: none)")
     ap.add_argument("--compare", action="store_true", help="also run the other precision and compare")
     a = ap.parse_args()
     lim = a.order == 1 and not a.no_limiter
-    r = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, a.precision, a.seed, a.max_steps, lim, a.species_mg, a.t_end, stall_rtol=a.stall_rtol,
-            single_cluster=a.single_cluster)
+    r = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, a.precision, a.seed, a.max_steps, lim, a.species_mg, a.t_end,
+            stall_rtol=a.stall_rtol, single_cluster=not a.multi_cluster, wall_limit=a.wall_limit)
     out = {"run": r}
     if a.compare:
         other = "mixed" if a.precision == "fp64" else "fp64"
-        r2 = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, other, a.seed, a.max_steps, lim, a.species_mg, a.t_end, stall_rtol=a.stall_rtol,
-            single_cluster=a.single_cluster)
+        r2 = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, other, a.seed, a.max_steps, lim, a.species_mg, a.t_end,
+                 stall_rtol=a.stall_rtol, single_cluster=not a.multi_cluster, wall_limit=a.wall_limit)
         out["other"] = r2
         out["comparison"] = curve_diff(r, r2)
     if a.no_curve:

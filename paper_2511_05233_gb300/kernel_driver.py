@@ -19,6 +19,9 @@ def main():
     ap.add_argument("--order", type=int, default=1)
     ap.add_argument("--chem", default="tradeoff")
     ap.add_argument("--porosity", type=float, default=0.5)
+    ap.add_argument("--corr", type=float, default=4.0, help="correlation length of the structure, voxels")
+    ap.add_argument("--seed", type=int, default=3, help="structure seed")
+    ap.add_argument("--noise-seed", type=int, default=4)
     ap.add_argument("--op", default="jvp", choices=["residual", "jvp", "jvp_fused", "step"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=5)
@@ -28,7 +31,7 @@ def main():
 
     from . import dgls, inputs
 
-    phase = inputs.make_structure(a.n, a.porosity, 4.0, 3)
+    phase = inputs.make_structure(a.n, a.porosity, a.corr, a.seed)
     chem = dgls.TRADEOFF if a.chem == "tradeoff" else dgls.REDUCED3
     prm = dgls.default_params(chem, a.order, eps_struct=1 - a.porosity,
                               precision=dgls.MIXED if a.precision == "mixed" else dgls.FP64)
@@ -36,7 +39,7 @@ def main():
     N = ctx.n_dof
     z0 = ctx.new_state()
     ctx.equilibrium_state(z0)
-    noise = torch.from_numpy(inputs.uniform_noise(N, 4)).cuda()
+    noise = torch.from_numpy(inputs.uniform_noise(N, a.noise_seed)).cuda()
     nl = 6 if a.chem == "tradeoff" else 3
     z = z0.clone()
     z[: ctx.offsets[nl]] *= 1.0 + 0.01 * noise[: ctx.offsets[nl]]

@@ -58,14 +58,15 @@ _STRUCTURES = {}
 
 def request_structure(req):
     """The request's structure: the seeded random field (the first seed that keeps a collector
-    voxel); generated once per request and kept, so that a served request carries its structure as a
-    client would send it."""
+    voxel), its single structure cluster on the collector kept; generated once per request and kept,
+    so that a served request carries its structure as a client would send it."""
     from . import inputs
 
     key = (req.side, req.porosity, req.corr_len, req.seed)
     if key not in _STRUCTURES:
         for s in range(req.seed, req.seed + 50):
-            ph = inputs.make_structure(req.side, req.porosity, req.corr_len, s)
+            # one structure cluster on the collector: no isolated collector voxel can passivate
+            ph = inputs.make_structure(req.side, req.porosity, req.corr_len, s, single_cluster=True)
             if np.any(ph[:, :, 0] == inputs.STRUCT):
                 _STRUCTURES[key] = ph
                 break
