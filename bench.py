@@ -84,7 +84,7 @@ LIN_JVP_DG1_DRAM_BYTES_PER_DOF = 263.8
 # kernels behind the profiled "jvp" category of each precision (the Krylov-loop products)
 JVP_KERNELS = {"fp64": "jvp (linearised DG1 apply: k_lin_g, k_lin_nodes_apply, k_lin_nodes_diag, "
                        "k_lin_face_flux, k_lin_line_gather)",
-               "mixed": "jvp (fused matrix-free FP32 DG1 product: k_jvp1_fused)"}
+               "mixed": "jvp (fused matrix-free FP32 DG1 product: k_jvp1_batched, one-job table)"}
 # DRAM bytes per unknown of one fused FP32 product (ncu dram__bytes_read.sum + write.sum at 64^3 /
 # unknowns), or None when the kernel has changed since the counters were taken
 FUSED_F32_DRAM_BYTES_PER_DOF = None

@@ -86,10 +86,11 @@ typedef struct {
                                   starts from the current iterate of the finest level */
     int32_t precond_every;     /* rebuild the preconditioner every k-th Newton iteration of a step
                                   (0: once per step, at its first iteration) */
-    double newton_stall_rtol;  /* a Newton solve whose line search can no longer reduce ||S R|| counts as
-                                  converged if ||S R|| <= newton_stall_rtol ||S R(z^n)|| (1e-8, PETSc's
-                                  default relative tolerance): at large dt the FP64 rounding level of
-                                  the scaled residual lies above newton_rtol ||S R(z^n)|| */
+    double newton_stall_rtol;  /* a Newton solve whose line search can no longer reduce ||S R||, or whose
+                                  last iteration reduced it by less than half, counts as converged if
+                                  ||S R|| <= newton_stall_rtol ||S R(z^n)|| (1e-8, PETSc's default
+                                  relative tolerance): at large dt the FP64 rounding level of the
+                                  scaled residual lies above newton_rtol ||S R(z^n)|| */
     int32_t reorth;            /* classical Gram-Schmidt in GMRES: 2 = one pass (PETSc's default GMRES
                                   orthogonalisation, the solver of Sec. 2.7; default); 0 = a second
                                   pass when the first cancelled, ||w'|| < ||w|| / sqrt(2)

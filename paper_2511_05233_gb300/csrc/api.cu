@@ -1047,6 +1047,11 @@ static dg_status newton_(dg_ctx* ctx, const double* zn, double t1, double dt, in
         }
         std::swap(ctx->zc, ctx->zt);
         std::swap(ctx->R, ctx->Rt);
+        // stagnation at the rounding level: within the stall tolerance, an iteration that no longer
+        // halves ||S R|| has met the floor that rounding puts under the scaled residual (above it
+        // the inexact Newton iteration contracts by its forcing term, at most eta_max), so the
+        // solve ends here, certified to the same level as a stalled line search
+        const bool stagnant = nt <= ctx->prm.newton_stall_rtol * n0 && nt > 0.5 * nrm;
         // Eisenstat-Walker choice 2 (gamma 0.9, alpha 2) with the usual safeguard
         double eta_new = 0.9 * (nt / nrm) * (nt / nrm);
         double safe = 0.9 * eta * eta;
@@ -1054,6 +1059,7 @@ static dg_status newton_(dg_ctx* ctx, const double* zn, double t1, double dt, in
         eta = std::min(ctx->prm.eta_max, std::max(ctx->prm.eta_min, eta_new));
         nrm = nt;
         ++it;
+        if (stagnant) break;
     }
     if (info) {
         info->converged = result == DG_OK;

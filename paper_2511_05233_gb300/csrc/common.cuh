@@ -97,7 +97,12 @@ template <class S> __device__ __forceinline__ Dual<S>& operator-=(Dual<S>& a, Du
 __device__ __forceinline__ double sexp(double x) { return exp(x); }
 __device__ __forceinline__ float sexp(float x) { return __expf(x); }
 __device__ __forceinline__ double ssqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float ssqrt(float x) { return sqrtf(x); }
+// FP32 square root by the hardware approximation (sqrt.approx, relative error about 2^-23)
+__device__ __forceinline__ float ssqrt(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double slog(double x) { return log(x); }
 __device__ __forceinline__ float slog(float x) { return __logf(x); }
 __device__ __forceinline__ double scbrt(double x) { return cbrt(x); }
@@ -145,24 +150,38 @@ template <class S> __device__ __forceinline__ Dual<S> act_cbrt(Dual<S> a) {
     S r = scbrt(a.v);
     return mkd(r, a.d / (S(3) * r * r));
 }
-// correctly rounded reciprocal (the same value as 1/a; in FP32 without the division's slow path)
-__device__ __forceinline__ double rcp_rn(double a) { return 1.0 / a; }
-__device__ __forceinline__ float rcp_rn(float a) { return __frcp_rn(a); }
-template <class S> __device__ __forceinline__ S srcp(S a) { return rcp_rn(a); }
+// reciprocal: correctly rounded in FP64 (the same value as 1/a); in FP32 the hardware approximation
+// (rcp.approx, relative error about 2^-23), which is all the Krylov-loop products need
+__device__ __forceinline__ double rcp_k(double a) { return 1.0 / a; }
+__device__ __forceinline__ float rcp_k(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+template <class S> __device__ __forceinline__ S srcp(S a) { return rcp_k(a); }
 template <class S> __device__ __forceinline__ Dual<S> srcp(Dual<S> a) {
-    S r = rcp_rn(a.v);
+    S r = rcp_k(a.v);
     return mkd(r, -a.d * r * r);
 }
+// a product rounded on its own (never contracted into a neighbouring addition)
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 
 // max(x, 0) with the branch taken on the value
 template <class S> __device__ __forceinline__ S pos(S x) { return x > S(0) ? x : S(0); }
 template <class S> __device__ __forceinline__ Dual<S> pos(Dual<S> x) { return x.v > S(0) ? x : mkd(S(0), S(0)); }
 
-// x^{3/2} of max(x, 0)
-template <class T> __device__ __forceinline__ T pow15(T x) {
-    typedef typename Base<T>::type S;
-    if (val(x) > S(0)) return x * ssqrt(x);
-    return Make<T>::c(0.0);
+// x^{3/2} of max(x, 0); the tangent is (3/2) x^{1/2} dx, which needs no division
+template <class S> __device__ __forceinline__ S pow15(S x) {
+    if (x > S(0)) return x * ssqrt(x);
+    return S(0);
+}
+template <class S> __device__ __forceinline__ Dual<S> pow15(Dual<S> x) {
+    if (x.v > S(0)) {
+        const S r = ssqrt(x.v);
+        return mkd(x.v * r, S(1.5) * r * x.d);
+    }
+    return mkd(S(0), S(0));
 }
 
 // log of an activity a = max(c, 0)/c_ref (icref = 1/c_ref): -inf (with zero tangent) at a <= 0, so
@@ -171,7 +190,7 @@ template <class S> __device__ __forceinline__ S log_act(S c, S icref) {
     return c > S(0) ? slog(c * icref) : -S(INFINITY);
 }
 template <class S> __device__ __forceinline__ Dual<S> log_act(Dual<S> c, S icref) {
-    if (c.v > S(0)) return mkd(slog(c.v * icref), c.d * rcp_rn(c.v));
+    if (c.v > S(0)) return mkd(slog(c.v * icref), c.d * rcp_k(c.v));
     return mkd(-S(INFINITY), S(0));
 }
 
@@ -180,12 +199,14 @@ template <class S> __device__ __forceinline__ S harm(S a, S b) {
     if (a * b > S(0)) return (S(2) * a * b) / (a + b);
     return S(0);
 }
-// dual version with one division: dH = 2 (b^2 da + a^2 db) / (a + b)^2
+// dual version with one reciprocal: dH = 2 (b^2 da + a^2 db) / (a + b)^2.  Symmetric to the last
+// bit (harm(a, b) == harm(b, a)): the two terms of dH are rounded separately before their sum, so
+// the two voxels of a face that each evaluate its flux get the same value with opposite signs.
 template <class S> __device__ __forceinline__ Dual<S> harm(Dual<S> a, Dual<S> b) {
     if (a.v * b.v > S(0)) {
-        S r = rcp_rn(a.v + b.v);
-        S h = S(2) * a.v * b.v * r;
-        S d = S(2) * r * r * (b.v * b.v * a.d + a.v * a.v * b.d);
+        S r = rcp_k(a.v + b.v);
+        S h = S(2) * (a.v * b.v) * r;
+        S d = S(2) * r * r * (mul_rn(b.v * b.v, a.d) + mul_rn(a.v * a.v, b.d));
         return mkd(h, d);
     }
     return mkd(S(0), S(0));

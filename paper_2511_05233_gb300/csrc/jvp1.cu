@@ -243,13 +243,28 @@ __device__ __forceinline__ void jvp1_block(const DevParams& p, const Geo& g, con
             const bool local = d == 0 && ql >= 0 && ql < FT;
             const int qph = local ? sPh[ql] : g.phase[qc];
             const int qsi = local ? sSi[ql] : g.cmap[qc];
-            // neighbour values at its node `node` (its near node is pn, its far node n)
-            auto nb = [&](int f, int node) -> T {
-                if (local) return zv(f, node, ql);
-                if (struct_field<Chem>(f) && qph != 1) return Make<T>::c(0.0);
-                const int64_t o = p.off[f] + (int64_t)node * p.flen[f] + (struct_field<Chem>(f) ? qsi : qc);
-                return mkd(z[o], v[o]);
-            };
+            // the neighbour's values at its near node (pn) and its far node (n), all loads issued
+            // together so that one L2 round trip covers them
+            T qN[NF], qF[NF];
+            if (local) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    qN[f] = zv(f, pn, ql);
+                    qF[f] = zv(f, n, ql);
+                }
+            } else {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    if (struct_field<Chem>(f) && qph != 1) {
+                        qN[f] = qF[f] = Make<T>::c(0.0);
+                    } else {
+                        const int64_t b = p.off[f] + (struct_field<Chem>(f) ? qsi : qc);
+                        const int64_t o0 = b + (int64_t)pn * p.flen[f], o1 = b + (int64_t)n * p.flen[f];
+                        qN[f] = mkd(z[o0], v[o0]);
+                        qF[f] = mkd(z[o1], v[o1]);
+                    }
+                }
+            }
             const int q = line_of(d, n);
             const int slotP = face_slot(d, mc ? 1 : -1, q);
             const T gP = mkd(sG[slotP * FT + lane], sGd[slotP * FT + lane]);
@@ -260,36 +275,38 @@ __device__ __forceinline__ void jvp1_block(const DevParams& p, const Geo& g, con
             } else {
                 T ct[NL], et[2];
 #pragma unroll
-                for (int m = 0; m < NL; ++m) ct[m] = nb(m, pn) * al + nb(m, n) * be;
+                for (int m = 0; m < NL; ++m) ct[m] = qN[m] * al + qF[m] * be;
                 et[0] = et[1] = Make<T>::c(0.0);
                 if (NS == 2 && qph == 1) {
-                    et[0] = nb(NL, pn) * al + nb(NL, n) * be;
-                    et[1] = nb(NL + 1, pn) * al + nb(NL + 1, n) * be;
+                    et[0] = qN[NL] * al + qF[NL] * be;
+                    et[1] = qN[NL + 1] * al + qF[NL + 1] * be;
                 }
                 gQ = transport_factor<Chem, T>(p, liquid_fraction<Chem, T>(p, qph, et), ct);
             }
-            const T gl = mc ? gP : gQ, gr = mc ? gQ : gP;
-            const T Hg = harm(gl, gr);
-            // jump (left minus right) and mean normal derivative of a field across the face
+            // Everything below is taken from this voxel's side: the bracket with the own trace first
+            // is the left-minus-right bracket times sgn = +1 (this voxel left of the face) or -1, and
+            // the flux is linear in the brackets, so the flux from this side is sgn times the face
+            // flux, exactly (negation is exact and the harmonic means are symmetric to the last
+            // bit); the stored value (flux from this side) x wf is then +f for the left voxel and -f
+            // for the right one, with no selects on the side.
+            const T Hg = harm(gP, gQ);
             auto bracket = [&](T own_n, T own_f, T nb_n, T nb_f, T& t_own, T& t_nb) -> T {
                 t_own = own_n * al + own_f * be;
                 t_nb = nb_n * al + nb_f * be;
-                const T jump = mc ? t_own - t_nb : t_nb - t_own;
-                const T dn = ((mc ? own_n - own_f : own_f - own_n) + (mc ? nb_f - nb_n : nb_n - nb_f)) * K.gq2;
-                return jump * K.pen - dn;
+                const T dn = ((own_n - own_f) + (nb_f - nb_n)) * K.gq2;
+                return (t_own - t_nb) * K.pen - dn;
             };
             T tPo, tPn;
-            const T bL = bracket(zv(PHIL, n, lane), zv(PHIL, pn, lane), nb(PHIL, pn), nb(PHIL, n), tPo, tPn);
+            const T bL = bracket(zv(PHIL, n, lane), zv(PHIL, pn, lane), qN[PHIL], qF[PHIL], tPo, tPn);
             S fL = S(0);
 #pragma unroll
             for (int m = 0; m < NL; ++m) {
                 T to, tn;
-                const T b = bracket(zv(m, n, lane), zv(m, pn, lane), nb(m, pn), nb(m, n), to, tn);
+                const T b = bracket(zv(m, n, lane), zv(m, pn, lane), qN[m], qF[m], to, tn);
                 const T dterm = b * Hg;
                 S f = (dterm * K.D0[m]).d;
                 if ((K.charged >> m) & 1) {
-                    const T cl = mc ? to : tn, cr = mc ? tn : to;
-                    const T mterm = bL * harm(gl * cl, gr * cr);
+                    const T mterm = bL * harm(gP * to, gQ * tn);
                     f += (mterm * K.km[m]).d;
                     fL += (dterm * K.Kd[m] + mterm * K.Km[m]).d;
                 }
@@ -298,11 +315,10 @@ __device__ __forceinline__ void jvp1_block(const DevParams& p, const Geo& g, con
             Fe[NL] = fL;
             if (ph == 1 && qph == 1) {
                 const S jn = zv(PHIS, n, lane).d, jf = zv(PHIS, pn, lane).d;
-                const S qn = nb(PHIS, pn).d, qf = nb(PHIS, n).d;
+                const S qn = qN[PHIS].d, qf = qF[PHIS].d;
                 const S to = jn * al + jf * be, tn = qn * al + qf * be;
-                const S jump = mc ? to - tn : tn - to;
-                const S dn = ((mc ? jn - jf : jf - jn) + (mc ? qf - qn : qn - qf)) * K.gq2;
-                Fe[NL + 1] = (jump * K.pen - dn) * K.kS;
+                const S dn = ((jn - jf) + (qf - qn)) * K.gq2;
+                Fe[NL + 1] = ((to - tn) * K.pen - dn) * K.kS;
             }
         } else if (active && d == 0 && mc && ci == p.nx - 1) {
             // anode face (Eqs. 26-27): exchange rate at the face trace of c_Li and Phi^L
@@ -312,10 +328,10 @@ __device__ __forceinline__ void jvp1_block(const DevParams& p, const Geo& g, con
             Fe[0] = rA * K.aLi;
             Fe[NL] = rA * K.aL;
         }
-        // the left voxel of a face gets +f, the right one -f (face weight folded in)
-        const S sw = mc ? K.wf : -K.wf;
+        // flux from this side x the face weight: +f for the left voxel of the face, -f for the right
+        // one (the anode face has its voxel on the left)
 #pragma unroll
-        for (int e = 0; e < NE; ++e) sF[((n * 3 + d) * NE + e) * FT + lane] = Fe[e] * sw;
+        for (int e = 0; e < NE; ++e) sF[((n * 3 + d) * NE + e) * FT + lane] = Fe[e] * K.wf;
     }
     __syncthreads();
 
@@ -341,7 +357,7 @@ __device__ __forceinline__ void jvp1_block(const DevParams& p, const Geo& g, con
 // Batched product: launch block b runs block map[b].y of instance map[b].x, whose job record is
 // staged in shared memory behind the product's own arrays.
 template <class Chem, class S>
-__global__ void __launch_bounds__(256, sizeof(S) == 4 ? 4 : 1) k_jvp1_batched(const Job1<S>* __restrict__ jobs,
+__global__ void __launch_bounds__(256, sizeof(S) == 4 ? 3 : 1) k_jvp1_batched(const Job1<S>* __restrict__ jobs,
                                                                              const int2* __restrict__ map) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr size_t off = (fused_smem<Chem, S>() + 15) / 16 * 16;
