@@ -13,13 +13,14 @@ from __future__ import annotations
 
 import argparse
 import json
+import sys
 import time
 
 import numpy as np
 
 
 def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, species_mg=2, t_end=0.0, h=1e-6,
-        stall_rtol=None, single_cluster=True, wall_limit=0.0, chunk=25):
+        stall_rtol=None, single_cluster=True, wall_limit=0.0, chunk=25, progress=False):
     import torch
 
     from . import dgls, inputs
@@ -52,6 +53,12 @@ def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, 
                           t_end=t_end, max_steps=min(chunk, n_left), limiter=limiter, resume=ck)
         parts.append(r)
         ck = r["checkpoint"]
+        if progress:
+            sys.stderr.write(json.dumps({"chunk": len(parts), "t": ck["t"], "dt": ck["dt"],
+                                         "U_cell": float(r["U_cell"][-1]) if len(r["U_cell"]) else None,
+                                         "steps": sum(len(q["t"]) for q in parts), "status": r["status"],
+                                         "wall_s": time.perf_counter() - t1}) + "\n")
+            sys.stderr.flush()
         done = r["status"] != "DG_OK" or len(r["t"]) < min(chunk, n_left) or \
             (len(r["U_cell"]) and r["U_cell"][-1] <= 1.9) or (t_end > 0 and ck["t"] >= t_end)
         if done or (wall_limit > 0 and time.perf_counter() - t1 > wall_limit):
@@ -112,16 +119,19 @@ def main():
                     help="keep every structure cluster touching the current collector (default: only the largest, "
                          "so that no collector voxel is isolated)")
     ap.add_argument("--wall-limit", type=float, default=0.0, help="stop the discharge after this many seconds (0: none)")
+    ap.add_argument("--progress", action="store_true", help="one JSON line per chunk of accepted steps on stderr")
     ap.add_argument("--compare", action="store_true", help="also run the other precision and compare")
     a = ap.parse_args()
     lim = a.order == 1 and not a.no_limiter
     r = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, a.precision, a.seed, a.max_steps, lim, a.species_mg, a.t_end,
-            stall_rtol=a.stall_rtol, single_cluster=not a.multi_cluster, wall_limit=a.wall_limit)
+            stall_rtol=a.stall_rtol, single_cluster=not a.multi_cluster, wall_limit=a.wall_limit,
+            progress=a.progress)
     out = {"run": r}
     if a.compare:
         other = "mixed" if a.precision == "fp64" else "fp64"
         r2 = run(a.n, a.order, a.porosity, a.corr_len, a.f_C, other, a.seed, a.max_steps, lim, a.species_mg, a.t_end,
-                 stall_rtol=a.stall_rtol, single_cluster=not a.multi_cluster, wall_limit=a.wall_limit)
+                 stall_rtol=a.stall_rtol, single_cluster=not a.multi_cluster, wall_limit=a.wall_limit,
+                 progress=a.progress)
         out["other"] = r2
         out["comparison"] = curve_diff(r, r2)
     if a.no_curve:

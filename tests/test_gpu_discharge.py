@@ -195,3 +195,35 @@ def test_full_discharge_free_running_reaches_cutoff():
     assert res["status"] == "DG_OK"
     assert res["U_cell"][-1] <= 1.9 < res["U_cell"][-2]
     assert abs(res["t"][-1] / gd["t"][-1] - 1.0) <= 0.02
+
+
+def test_large_dg1_step_ends_at_the_rounding_floor():
+    """Newton at large dt from a DG1 mid-discharge state: the scaled residual stops at its rounding
+    floor, which at large dt lies above rtol ||S R0||; the solve ends there within a few iterations,
+    certified to the stall tolerance, instead of trading rounding noise up to the iteration limit."""
+    import torch
+
+    from paper_2511_05233_gb300 import dgls, inputs
+
+    phase = None
+    for s in range(3, 53):
+        ph = inputs.make_structure(16, 0.5, 4.0, s, single_cluster=True)
+        if np.any(ph[:, :, 0] == inputs.STRUCT):
+            phase = ph
+            break
+    prm = dgls.default_params(dgls.TRADEOFF, 1, f_C=0.5, eps_struct=0.5, newton_stall_rtol=1e-7)
+    ctx = dgls.Context(phase, 1e-6, prm)
+    z = ctx.new_state()
+    ctx.equilibrium_state(z)
+    ctx.relax(z, 0.1, 40)
+    r = ctx.discharge(z, controller=dgls.NAIVE, dt0=1e-3, dt_min=1e-6, dt_max=10.0, cutoff_V=1.9, t_end=3.0,
+                      max_steps=2000, limiter=True)
+    assert r["status"] == "DG_OK"
+    t = r["checkpoint"]["t"]
+    out = torch.empty_like(z)
+    for dt in (0.4, 1.6):
+        st, info = ctx.step(z, out, t, dt, check=False)
+        assert st == dgls.OK and info.converged, (dt, st)
+        assert info.norm <= 1e-7 * info.norm0, (dt, info.norm, info.norm0)
+        assert info.newton_iterations <= 10, (dt, info.newton_iterations)
+    ctx.close()
