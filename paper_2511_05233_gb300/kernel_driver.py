@@ -22,7 +22,9 @@ def main():
     ap.add_argument("--corr", type=float, default=4.0, help="correlation length of the structure, voxels")
     ap.add_argument("--seed", type=int, default=3, help="structure seed")
     ap.add_argument("--noise-seed", type=int, default=4)
-    ap.add_argument("--op", default="jvp", choices=["residual", "jvp", "jvp_fused", "step"])
+    ap.add_argument("--op", default="jvp",
+                    help="residual, jvp, jvp_fused or step; several separated by commas run one after the other "
+                         "on the same context")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--no-warm", action="store_true", help="no untimed call first (launch lists of exactly reps calls)")
@@ -49,12 +51,17 @@ def main():
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def call():
-        if a.op == "residual":
+    ops = a.op.split(",")
+    for op in ops:
+        if op not in ("residual", "jvp", "jvp_fused", "step"):
+            raise SystemExit(f"unknown op {op}")
+
+    def call(op):
+        if op == "residual":
             ctx.residual(z, z0, 1e-3, 1e-3, out)
-        elif a.op == "jvp":
+        elif op == "jvp":
             ctx.jvp(z, 1e-3, 1e-3, v, out)
-        elif a.op == "jvp_fused":
+        elif op == "jvp_fused":
             if a.precision == "mixed":
                 ctx.jvp_fused(z, 1e-3, 1e-3, v32, o32)
             else:
@@ -62,19 +69,20 @@ def main():
         else:
             ctx.step(z, out, 0.0, 1e-3, check=False)
 
-    if not a.no_warm:
-        call()
-    torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(a.reps):
-        call()
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / a.reps
-    print(json.dumps({"op": a.op, "n": a.n, "order": a.order, "chem": a.chem, "precision": a.precision,
-                      "n_dof": N, "ms_per_call": ms, "gdof_per_s": N / (ms / 1e3) / 1e9,
-                      "finite": bool(np.isfinite((o32 if a.op == "jvp_fused" and a.precision == "mixed" else out)
-                                                 .cpu().numpy()).all())}))
+    for op in ops:
+        if not a.no_warm:
+            call(op)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(a.reps):
+            call(op)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.reps
+        res = o32 if op == "jvp_fused" and a.precision == "mixed" else out
+        print(json.dumps({"op": op, "n": a.n, "order": a.order, "chem": a.chem, "precision": a.precision,
+                          "n_dof": N, "ms_per_call": ms, "gdof_per_s": N / (ms / 1e3) / 1e9,
+                          "finite": bool(np.isfinite(res.cpu().numpy()).all())}), flush=True)
 
 
 if __name__ == "__main__":
