@@ -85,9 +85,10 @@ LIN_JVP_DG1_DRAM_BYTES_PER_DOF = 263.8
 JVP_KERNELS = {"fp64": "jvp (linearised DG1 apply: k_lin_g, k_lin_nodes_apply, k_lin_nodes_diag, "
                        "k_lin_face_flux, k_lin_line_gather)",
                "mixed": "jvp (fused matrix-free FP32 DG1 product: k_jvp1_batched, one-job table)"}
-# DRAM bytes per unknown of one fused FP32 product (ncu dram__bytes_read.sum + write.sum at 64^3 /
-# unknowns), or None when the kernel has changed since the counters were taken
-FUSED_F32_DRAM_BYTES_PER_DOF = None
+# DRAM bytes per unknown of one fused FP32 product: ncu dram__bytes_read.sum + dram__bytes_write.sum of
+# one launch at this workload's size (128^3, 139,463,920 unknowns; 1.13 GB + 537.0 MB, a 1-pass
+# capture) / unknowns; None when the kernel has changed since the counters were taken
+FUSED_F32_DRAM_BYTES_PER_DOF = 11.95
 
 
 def kernel_rates(prof, N, n_pot, hbm, precision):
