@@ -15,11 +15,13 @@
 //   phase 2  per direction, the volume term of the thread's line (both nodes of a line are in the
 //            block) and the interior-penalty flux (Eq. 46) through the face point on its side, from
 //            its own traces and the neighbour voxel's: the x-neighbour of an inner lane is read
-//            from shared memory, other neighbours from global memory (L1/L2: the neighbouring
-//            blocks read the same lines);
+//            from shared memory, other neighbours from global memory (in practice from L2: the
+//            blocks that own them, mostly on other SMs, read the same values), all twenty (z, v)
+//            pairs of a face loaded together;
 //   phase 3  each node adds its own face flux (trace weight ALPHA) and its line partner's (BETA)
 //            from shared memory and stores its row-scaled outputs.
-// Each interior face point is evaluated by the voxels on both of its sides.
+// Each interior face point is evaluated by the voxels on both of its sides; the two results are
+// exact negatives of each other (see phase 2), so the discrete fluxes cancel exactly.
 //
 // The kernel always runs from a table of job records (one per instance: parameters, geometry,
 // buffers, per-call constants) and a block map: a batch of many instances and a single instance
