@@ -6,7 +6,7 @@ import pytest
 
 from oracle import chemistry as ch, init, lis
 from paper_2511_05233_gb300 import inputs
-from tests.gpu_helpers import ensure_built, structure_with_collector, to_dev, to_host
+from tests.gpu_helpers import ensure_built, structure_with_collector, to_dev
 
 pytestmark = pytest.mark.gpu
 

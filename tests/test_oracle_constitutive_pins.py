@@ -7,8 +7,7 @@ exponent, sign, factor, species weight or localisation.  No CUDA code is used.
 import numpy as np
 import pytest
 
-from oracle import chemistry as ch, constants as K, dg, init, lis
-from paper_2511_05233_gb300 import inputs
+from oracle import chemistry as ch, constants as K, init, lis
 
 LIQ = ["Li", "S8L", "S8_2", "S6_2", "S4_2", "S_2"]
 

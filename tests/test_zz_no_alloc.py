@@ -3,7 +3,6 @@ call (for example inside CUDA stream capture) and must not use the context's wor
 its scratch in a static device array; its result must equal dg_residual's, call after call.
 
 Collected last (file name), so that a run stopping at the first failure has run everything else."""
-import ctypes as C
 
 import numpy as np
 import pytest
