@@ -19,6 +19,39 @@ import time
 import numpy as np
 
 
+def discharge_in_chunks(ctx, z, controller, t_end, max_steps, limiter, wall_limit=0.0, chunk=25, progress=False,
+                        clock=time.perf_counter, log=None):
+    """The discharge in chunks of accepted steps, each resumed from the previous chunk's controller state
+    (bitwise the same curve as one call), so that a wall-clock limit can end it between chunks.  Stops
+    at the cut-off (U_cell <= 1.9 V), at t_end, at max_steps, on a failed status, or once wall_limit
+    seconds have passed since the call.  Returns the concatenated curve and step statistics."""
+    log = log if log is not None else sys.stderr
+    t1 = clock()
+    parts, ck = [], None
+    while True:
+        n_left = max_steps - sum(len(q["t"]) for q in parts)
+        if n_left <= 0:
+            break
+        r = ctx.discharge(z, controller=controller, dt0=1e-3, dt_min=1e-6, dt_max=10.0, cutoff_V=1.9,
+                          t_end=t_end, max_steps=min(chunk, n_left), limiter=limiter, resume=ck)
+        parts.append(r)
+        ck = r["checkpoint"]
+        if progress:
+            log.write(json.dumps({"chunk": len(parts), "t": ck["t"], "dt": ck["dt"],
+                                  "U_cell": float(r["U_cell"][-1]) if len(r["U_cell"]) else None,
+                                  "steps": sum(len(q["t"]) for q in parts), "status": r["status"],
+                                  "wall_s": clock() - t1}) + "\n")
+            log.flush()
+        done = r["status"] != "DG_OK" or len(r["t"]) < min(chunk, n_left) or \
+            (len(r["U_cell"]) and r["U_cell"][-1] <= 1.9) or (t_end > 0 and ck["t"] >= t_end)
+        if done or (wall_limit > 0 and clock() - t1 > wall_limit):
+            break
+    res = {k: np.concatenate([q[k] for q in parts]) for k in ("t", "dt", "U_cell", "c_m", "newton_its", "gmres_its")}
+    res.update(status=parts[-1]["status"], attempts=sum(q["attempts"] for q in parts),
+               failures=sum(q["failures"] for q in parts))
+    return res
+
+
 def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, species_mg=2, t_end=0.0, h=1e-6,
         stall_rtol=None, single_cluster=True, wall_limit=0.0, chunk=25, progress=False):
     import torch
@@ -42,30 +75,8 @@ def run(n, order, porosity, corr_len, f_C, precision, seed, max_steps, limiter, 
     ctx.relax(z, 0.1, 40)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    # the discharge in chunks of accepted steps, each resumed from the previous chunk's controller state
-    # (bitwise the same curve as one call), so that a wall-clock limit can end it between chunks
-    parts, ck = [], None
-    while True:
-        n_left = max_steps - sum(len(q["t"]) for q in parts)
-        if n_left <= 0:
-            break
-        r = ctx.discharge(z, controller=dgls.NAIVE, dt0=1e-3, dt_min=1e-6, dt_max=10.0, cutoff_V=1.9,
-                          t_end=t_end, max_steps=min(chunk, n_left), limiter=limiter, resume=ck)
-        parts.append(r)
-        ck = r["checkpoint"]
-        if progress:
-            sys.stderr.write(json.dumps({"chunk": len(parts), "t": ck["t"], "dt": ck["dt"],
-                                         "U_cell": float(r["U_cell"][-1]) if len(r["U_cell"]) else None,
-                                         "steps": sum(len(q["t"]) for q in parts), "status": r["status"],
-                                         "wall_s": time.perf_counter() - t1}) + "\n")
-            sys.stderr.flush()
-        done = r["status"] != "DG_OK" or len(r["t"]) < min(chunk, n_left) or \
-            (len(r["U_cell"]) and r["U_cell"][-1] <= 1.9) or (t_end > 0 and ck["t"] >= t_end)
-        if done or (wall_limit > 0 and time.perf_counter() - t1 > wall_limit):
-            break
-    res = {k: np.concatenate([q[k] for q in parts]) for k in ("t", "dt", "U_cell", "c_m", "newton_its", "gmres_its")}
-    res.update(status=parts[-1]["status"], attempts=sum(q["attempts"] for q in parts),
-               failures=sum(q["failures"] for q in parts))
+    res = discharge_in_chunks(ctx, z, dgls.NAIVE, t_end, max_steps, limiter, wall_limit=wall_limit, chunk=chunk,
+                              progress=progress)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     out = {"n": n, "order": order, "porosity": porosity, "corr_len": corr_len, "f_C": f_C, "precision": precision,
