@@ -233,7 +233,9 @@ dg_status dg_jvp(dg_ctx* ctx, const double* z_dev, double t, double dt,
  * for DG0 the two-launch product (transport factors, then voxels).  precision DG_PREC_FP64: v_dev
  * and jv_dev are n_dof doubles and the arithmetic is FP64; DG_PREC_MIXED: they are n_dof floats, z
  * is rounded to FP32 on the device and the arithmetic is FP32 (the context must have been set up
- * with precision DG_PREC_MIXED, which holds the FP32 copy of z).  Rows unscaled, as dg_jvp.
+ * with precision DG_PREC_MIXED, which holds the FP32 copy of z).  The FP32 arithmetic uses the
+ * hardware exponential, logarithm, reciprocal and square root; its element-wise error against the
+ * exact product stays below 2e-5 |J||v| (the tested bound).  Rows unscaled, as dg_jvp.
  * Asynchronous. */
 dg_status dg_jvp_fused(dg_ctx* ctx, const double* z_dev, double t, double dt, int32_t precision,
                        const void* v_dev, void* jv_dev);
