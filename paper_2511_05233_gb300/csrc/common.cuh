@@ -201,7 +201,8 @@ template <class S> __device__ __forceinline__ S harm(S a, S b) {
 }
 // dual version with one reciprocal: dH = 2 (b^2 da + a^2 db) / (a + b)^2.  Symmetric to the last
 // bit (harm(a, b) == harm(b, a)): the two terms of dH are rounded separately before their sum, so
-// the two voxels of a face that each evaluate its flux get the same value with opposite signs.
+// the two voxels of a face that each evaluate its flux from the same inputs get the same value with
+// opposite signs.
 template <class S> __device__ __forceinline__ Dual<S> harm(Dual<S> a, Dual<S> b) {
     if (a.v * b.v > S(0)) {
         S r = rcp_k(a.v + b.v);

@@ -20,8 +20,10 @@
 //            pairs of a face loaded together;
 //   phase 3  each node adds its own face flux (trace weight ALPHA) and its line partner's (BETA)
 //            from shared memory and stores its row-scaled outputs.
-// Each interior face point is evaluated by the voxels on both of its sides; the two results are
-// exact negatives of each other (see phase 2), so the discrete fluxes cancel exactly.
+// Each interior face point is evaluated by the voxels on both of its sides; from the same inputs
+// the two results are exact negatives of each other (see phase 2), and the inputs agree bit for bit
+// except for the neighbour's face-point transport factor, which a side whose neighbour is in
+// another block recomputes.
 //
 // The kernel always runs from a table of job records (one per instance: parameters, geometry,
 // buffers, per-call constants) and a block map: a batch of many instances and a single instance
